@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable splatting rasterizer GEVO optimises through.
+
+Metric: forward + backward Gaussian-pixel evaluations per second (and views per
+second) over 16 batched keyframe views of a 500k-Gaussian SH-3 room scene, 12
+views at 640x480 and 4 at 320x240 (the rendered past keyframes of Eq. 6, at the
+TUM image size of Section III-A1), against the unbatched plain path on the same
+GPU.  One step = projection of all views, tile binning and sort, blending, the
+L1 photometric + depth loss against stop-gradient targets, the reverse walk and
+the projection backward with se(3) pose gradients.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs independent replicas, one per GPU (the path has no exchange step).
+Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
+METRIC = "fwd+bwd Gaussian-pixel evals/s & views/s at 640x480, 500k Gaussians vs plain"
+WORKLOAD = "16 keyframe views (12x640x480 + 4x320x240), 500k Gaussians, SH degree 3"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--plain-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on the host cores (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(views=(12,)):
+    """Forward + backward of the given views of the workload through the oracle.
+    Returns (seconds, evaluations, description)."""
+    import numpy as np
+
+    import oracle
+    from paper_2409_09295_gb300 import scenes
+    w = scenes.workload(2)
+    cams = [w["cams"][v] for v in views]
+    t0 = time.perf_counter()
+    outs, projs, b = oracle.render_views(w["scene"], cams)
+    gC = [np.sign(o["rgb"] - 0.5) / o["rgb"].size for o in outs]
+    gD = [np.sign(o["depth"] - 3.0) / o["depth"].size for o in outs]
+    oracle.backward_views(w["scene"], cams, projs, b, gC, gD, None)
+    dt = time.perf_counter() - t0
+    E = sum(int(o["n_eval"].sum()) + int(o["n_contrib"].sum()) for o in outs)
+    sizes = "+".join(f"{c['W']}x{c['H']}" for c in cams)
+    return dt, E, f"views {list(views)} ({sizes}) of the 16-view 500k workload, fwd+bwd, FP64"
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    total_s, total_e = 0.0, 0
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        dt, E, desc = oracle_sample()
+        if i >= args.warmup:
+            total_s += dt
+            total_e += E
+    v = total_e / total_s
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle, one view per step"},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_2409_09295_gb300 import _abi, raster, scenes
+    from paper_2409_09295_gb300.batch import BatchedReplay, PlainReplay
+    _abi.load()
+
+    dev = torch.device("cuda", local)
+    w = scenes.workload(2)
+    scene, cams = w["scene"], w["cams"]
+    g = raster.gaussians_to_device(scene, dev)
+    # stop-gradient targets: renders of the previous map (the jittered scene)
+    gt = raster.gaussians_to_device(w["target_scene"], dev)
+    zero_rgb = None
+    tgt = BatchedReplay(gt, cams, zero_rgb, autotune=False, tuning_fwd=dict(
+        threads_per_tile=256, persistent=0, blocks_per_sm=0), tuning_bwd=dict(
+        threads_per_tile=256, persistent=0, blocks_per_sm=0))
+    tgt.pipe.forward(gt, tgt.camt)
+    target_rgb = tgt.pipe.rgb.clone()
+    target_depth = tgt.pipe.depth.clone()
+    del tgt
+    torch.cuda.empty_cache()
+
+    rep = BatchedReplay(g, cams, target_rgb, target_depth, lambda_depth=1.0)
+    E_fwd, E_bwd = rep.eval_counts()
+    rep.capture()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    nst = len(rep.stages())
+
+    for _ in range(args.warmup):
+        rep.replay()
+    torch.cuda.synchronize()
+    assert rep.pipe.last_error() == 0, "duplicate capacity exceeded"
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
+           for _ in range(args.steps)]
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                      # L2 flushed between timed steps
+        rep.replay(evs[k])
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    assert rep.pipe.last_error() == 0, "duplicate capacity exceeded"
+    step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
+    stage_ms = {name: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps
+                for i, (name, _) in enumerate(rep.graphs)}
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    V = len(cams)
+    evals = (E_fwd + E_bwd) * args.steps * world
+    value = evals / (total_ms / 1e3)
+    views_per_s = V * args.steps * world / (total_ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ---------------------------------
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).pin_memory()
+               for k in ("means", "scales", "quats", "opacities", "sh")}
+    host_cams = rep.camt.cpu().pin_memory()
+    host_tr = target_rgb.cpu().pin_memory()
+    host_td = target_depth.cpu().pin_memory()
+    out_loss = torch.empty(V, dtype=torch.float32).pin_memory()
+    out_dxi = torch.empty(V, 6, dtype=torch.float32).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host_in.values()) + host_cams.numel() * 4 + \
+        host_tr.numel() * 4 + host_td.numel() * 4
+    d2h = out_loss.numel() * 4 + out_dxi.numel() * 4
+
+    def e2e_step():
+        for k, t in host_in.items():
+            g[k].copy_(t, non_blocking=True)
+        rep.camt.copy_(host_cams, non_blocking=True)
+        target_rgb.copy_(host_tr, non_blocking=True)
+        target_depth.copy_(host_td, non_blocking=True)
+        rep.replay()
+        out_loss.copy_(rep.pipe.loss, non_blocking=True)
+        out_dxi.copy_(rep.pipe.dxi, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        e2e_step()
+        e.record()
+        e.synchronize()
+        e2e_ms += s.elapsed_time(e)
+    e2e_value = (E_fwd + E_bwd) * args.steps * world / (e2e_ms / 1e3)
+
+    # ---- the plain (unbatched) path on the same GPU --------------------------------------
+    plain = PlainReplay(g, cams, target_rgb, target_depth, lambda_depth=1.0)
+    plain.step()
+    torch.cuda.synchronize()
+    pms = 0.0
+    for _ in range(args.plain_steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        plain.step()
+        e.record()
+        e.synchronize()
+        pms += s.elapsed_time(e)
+    pms /= args.plain_steps
+    plain_line = {"evals_per_s": (E_fwd + E_bwd) / (pms / 1e3), "views_per_s": V / (pms / 1e3),
+                  "ms_per_step": pms}
+
+    # ---- roofline of the dominant stage ------------------------------------------------
+    pk = peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_peak = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * 128 * 2 * clk_peak * 1e6 / 1e12   # TFLOP/s, FMA = 2
+    FLOP_FWD, FLOP_BWD = 24, 71                 # per evaluated entry (design notes)
+    if dom == "render_bwd":
+        flops = FLOP_BWD * E_bwd
+    else:
+        flops = FLOP_FWD * E_fwd
+    achieved = flops / (stage_ms[dom] / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": {"render_bwd": "k_render_bwd",
+                                         "forward": "k_render_fwd (forward graph)",
+                                         "project_bwd": "k_project_bwd"}[dom],
+            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {clk_peak:.0f} MHz"}
+
+    line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "views": V, "gaussians": int(g["means"].shape[0]),
+                       "duplicates": rep.n_dup, "evals_fwd": E_fwd, "evals_bwd": E_bwd,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "tuning_fwd": rep.tuning_fwd, "tuning_bwd": rep.tuning_bwd,
+                       "graphs": "3 CUDA graphs per step"},
+            "views_per_s": views_per_s, "stage_ms": stage_ms,
+            "plain": plain_line, "speedup_vs_plain": value / plain_line["evals_per_s"],
+            "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": None, "roofline": roof, "clocks": clk,
+            "wall_s_timed": wall1 - wall0}
+    line["gpu_launches"] = launches_per_step(rep) * args.steps
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, E, desc = oracle_sample()
+        line["cpu_baseline"] = {"value": E / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                                "sample": desc + f", {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def launches_per_step(rep) -> int:
+    """Kernels of ours launched per step: project (1), bin_sort (count, scan,
+    scatter, segsort = 4), render_fwd (1), loss (1), render_bwd (zero + walk = 2),
+    project_bwd (1)."""
+    return 1 + 4 + 1 + 1 + 2 + 1
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,286 @@
+/*
+ * gevo.h -- C ABI of the GB300 (sm_103a) differentiable Gaussian-splatting
+ * rasterizer behind GEVO's map optimisation, tracking and rendered keyframes.
+ *
+ * The paper (GEVO, arXiv 2409.09295) renders with the 3DGS rasterizer it cites
+ * in Section I ("GS") and optimises the map and the camera pose T_k through it
+ * (Section III-B, Eq. 2 local stage and Eq. 3 global stage); Eq. 6 (E_pc)
+ * compares renders R(M'_t, T_kl) of four past keyframes against stop-gradient
+ * renders of the previous map, which is what the batched multi-view calls are
+ * for.  Every operation below is one stage of that renderer:
+ *
+ *   gevo_project      projection: 3-D covariance, EWA 2-D conic, depth, radius,
+ *                     colour, tiles touched                          (stage a1)
+ *   gevo_bin_sort     (tile, depth) keys, bit-exact sort, tile ranges (a2-a4)
+ *   gevo_render_fwd   front-to-back alpha blending: RGB, depth, final T (a5)
+ *   gevo_render_bwd   reverse walk: gradients of the 2-D records     (a6)
+ *   gevo_project_bwd  gradients of the Gaussian parameters and of the camera
+ *                     pose as an se(3) twist                          (a7)
+ *   gevo_loss_l1      L1 photometric (+ depth) loss and its gradient  (a8)
+ *
+ * Conventions shared by every call
+ *  - Device pointers are caller-owned device memory (for example torch
+ *    tensors); the library never allocates, frees or synchronises inside these
+ *    calls, and launches only on the given stream.  Host pointers are read
+ *    before the call returns.
+ *  - float arrays are IEEE binary32, row-major, tightly packed, 16-byte
+ *    aligned unless stated otherwise.
+ *  - A call returns GEVO_ERR_INVALID without launching anything on host-
+ *    detectable misuse (NULL where a pointer is required, negative sizes,
+ *    sh_degree outside 0..3, a layout with no views, misaligned pointers).
+ *    GEVO_ERR_CUDA means a launch failed (cudaGetLastError after the launch).
+ *  - Conditions only the device can see (duplicate count above capacity)
+ *    set a sticky error word in the workspace; outputs that depend on them are
+ *    then defined as stated per call.  gevo_last_error() reads and clears it.
+ *  - No kernel waits on another kernel or block: there are no spin-waits.
+ *
+ * Numerical constants of the formulation (3DGS defaults; the paper gives none):
+ *   near plane z > 0.2, 2-D dilation 0.3 px^2, Jacobian guard band 1.3x the
+ *   half field of view, alpha clamp 0.99, skip alpha < 1/255, stop before
+ *   T < 1e-4, 16 x 16 pixel tiles, radius ceil(3 sqrt(lambda_max)).
+ */
+#ifndef GEVO_H
+#define GEVO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GEVO_VERSION 1
+#define GEVO_MAX_VIEWS 64
+#define GEVO_TILE 16
+
+typedef enum {
+    GEVO_OK = 0,
+    GEVO_ERR_INVALID = 1,   /* bad argument, nothing launched                    */
+    GEVO_ERR_CAPACITY = 2,  /* device: duplicate count exceeded dup_capacity     */
+    GEVO_ERR_CUDA = 3,      /* a CUDA runtime call or launch failed              */
+    GEVO_ERR_TIMEOUT = 4,   /* reserved: no call waits on the device             */
+    GEVO_ERR_NONFINITE = 5  /* device: a non-finite projected value was culled   */
+} gevo_status;
+
+/* Pinhole camera of one view, world -> camera: p_c = R * p_w + t, camera x
+ * right, y down, z forward.  Pixel i is sampled at coordinate i, so the image
+ * mean of a point is (fx X/Z + cx - 0.5, fy Y/Z + cy - 0.5).  An array of these
+ * lives in DEVICE memory (16 floats = 64 bytes each) so that poses can change
+ * between replays of a captured graph. */
+typedef struct {
+    float R[9];   /* row-major */
+    float t[3];
+    float fx, fy, cx, cy;
+} gevo_camera;
+
+/* Image geometry of a batch of views (HOST memory, fixed for a captured graph).
+ * Tiles are numbered view-major: global tile = tile_base[v] + ty * tiles_x[v]
+ * + tx.  Per-pixel outputs are view-major planes: view v's pixel (x, y) is
+ * element pix_base[v] + y * width[v] + x of a [total_pixels] plane; an RGB
+ * output holds three such planes per view, R then G then B, starting at
+ * 3 * pix_base[v]. */
+typedef struct {
+    int32_t n_views;
+    int32_t total_tiles;
+    int64_t total_pixels;
+    int32_t width[GEVO_MAX_VIEWS];
+    int32_t height[GEVO_MAX_VIEWS];
+    int32_t tiles_x[GEVO_MAX_VIEWS];
+    int32_t tiles_y[GEVO_MAX_VIEWS];
+    int32_t tile_base[GEVO_MAX_VIEWS + 1];
+    int64_t pix_base[GEVO_MAX_VIEWS + 1];
+} gevo_layout;
+
+/* Gaussian parameters, DEVICE memory, structure of arrays over n Gaussians.
+ * Exactly one of sh / rgb is non-NULL.  rgb colours are used as given; SH
+ * colours are max(0, sum_k Y_k(d) sh[k] + 0.5) with d the unit direction from
+ * the camera centre to the mean and Y the real SH basis up to sh_degree. */
+typedef struct {
+    const float* means;      /* [n][3] world position                            */
+    const float* scales;     /* [n][3] activated (positive) standard deviations  */
+    const float* quats;      /* [n][4] rotation (w, x, y, z), any non-zero norm  */
+    const float* opacities;  /* [n]    activated opacity in (0, 1)               */
+    const float* sh;         /* [n][(sh_degree+1)^2][3] or NULL                  */
+    const float* rgb;        /* [n][3] or NULL                                   */
+    int32_t n;
+    int32_t sh_degree;       /* 0..3, used with sh                               */
+} gevo_gaussians;
+
+/* Gradients w.r.t. gevo_gaussians, same shapes, DEVICE memory, written (not
+ * accumulated) by gevo_project_bwd.  sh must be non-NULL iff the parameters
+ * have sh, rgb iff they have rgb. */
+typedef struct {
+    float* means;
+    float* scales;
+    float* quats;
+    float* opacities;
+    float* sh;
+    float* rgb;
+} gevo_gaussian_grads;
+
+/* Per (view, Gaussian) projection records, DEVICE memory, entry v * n + g. */
+typedef struct {
+    float* xy;             /* [V*n][2] image-space mean                          */
+    float* conic_opacity;  /* [V*n][4] inverse 2-D covariance (a, b, c), opacity */
+    float* rgb_depth;      /* [V*n][4] colour, camera-frame depth                 */
+    int32_t* radius;       /* [V*n]    pixel radius, 0 = culled                   */
+    uint32_t* tiles_touched; /* [V*n]  tiles in the rectangle, 0 if culled        */
+} gevo_proj;
+
+/* Gradients of a scalar loss w.r.t. the records, DEVICE memory, entry v*n+g. */
+typedef struct {
+    float* xy;             /* [V*n][2]                                           */
+    float* conic_opacity;  /* [V*n][4] d/da, d/db, d/dc (as in the power), d/do  */
+    float* rgb_depth;      /* [V*n][4] d/dr, d/dg, d/db, d/ddepth                 */
+} gevo_grad2d;
+
+/* Launch shape for the per-tile kernels (chosen by the autotuner).
+ * threads_per_tile in {64, 128, 256}: each thread owns 256 / threads pixels of
+ * its 16 x 16 tile.  persistent != 0: one grid of blocks_per_sm * SMs blocks
+ * pulls (view, tile) work items heaviest first from a device counter; 0: one
+ * block per tile.  NULL = {256, 0, 0}. */
+typedef struct {
+    int32_t threads_per_tile;
+    int32_t persistent;
+    int32_t blocks_per_sm;   /* 0 = as many as fit */
+} gevo_tuning;
+
+/* ---------------------------------------------------------------------- */
+/* Set-up (host only; no device work)                                      */
+/* ---------------------------------------------------------------------- */
+
+/* Fills *layout for n_views views of the given pixel sizes (host arrays).
+ * Returns GEVO_ERR_INVALID if n_views is not in 1..GEVO_MAX_VIEWS or a size is
+ * not positive or the totals overflow 32-bit tile / 31-bit list indices. */
+gevo_status gevo_layout_init(gevo_layout* layout, int32_t n_views, const int32_t* width,
+                             const int32_t* height);
+
+/* Bytes of device workspace the calls below need for n Gaussians, this layout
+ * and a duplicate capacity of dup_capacity (Gaussian, tile) pairs.  The
+ * workspace must be 256-byte aligned, is owned by the caller, and carries
+ * state between calls of one pipeline (tile counts, the heaviest-first tile
+ * order and the sticky error word): use one workspace per pipeline and do not
+ * run two pipelines on it concurrently.  It must be zero-filled once before
+ * its first use (cudaMemset). */
+size_t gevo_workspace_bytes(const gevo_layout* layout, int32_t n, uint64_t dup_capacity);
+
+/* ---------------------------------------------------------------------- */
+/* Stage a1: projection (Section I "GS"; Section III-B Eq. 2/3 render R(M,T)) */
+/* ---------------------------------------------------------------------- */
+
+/* For every view v and Gaussian g: p = R mu + t; cull if p.z <= 0.2;
+ * Sigma3 = Rq diag(s)^2 Rq^T; J = EWA Jacobian of the pinhole map at p (x/z and
+ * y/z clamped to 1.3x the half field of view); Sigma2 = J R Sigma3 R^T J^T +
+ * 0.3 I; cull if det <= 0; conic = Sigma2^-1; radius = ceil(3 sqrt(lambda_max))
+ * with lambda_max = mid + sqrt(max(0.1, mid^2 - det)); tile rectangle (see
+ * gevo_bin_sort); cull if it is empty; colour from rgb or SH.  Culled entries
+ * get radius = 0 and tiles_touched = 0 (other fields undefined).
+ * Each Gaussian is read once for all views.  cams: DEVICE array [n_views]. */
+gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,
+                         const gevo_camera* cams, gevo_proj* out, void* workspace,
+                         void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Stages a2-a4: keys, bit-exact sort, tile ranges                          */
+/* ---------------------------------------------------------------------- */
+
+/* Tile rectangle of entry (v, g), in binary32: per axis
+ * [floor((m - r) / 16), floor((m + r + 15) / 16)) clamped to the tile grid.
+ * Every tile t of it yields one duplicate with key = (tile_base[v] + t) << 32 |
+ * bit pattern of the binary32 depth, value = g.  Output: keys / vals sorted by
+ * key, equal keys by value, of length D = sum tiles_touched; ranges[2 t],
+ * ranges[2 t + 1] = [start, end) of global tile t in that order, (0, 0) for an
+ * empty tile.  *d_n_dup (DEVICE uint64) receives D.
+ * If D > dup_capacity: the error word gets GEVO_ERR_CAPACITY, *d_n_dup still
+ * receives the true D, every range is (0, 0) and keys / vals are undefined.
+ * keys: [dup_capacity] uint64, vals: [dup_capacity] uint32, ranges:
+ * [total_tiles][2] uint32 (DEVICE). */
+gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                          uint64_t dup_capacity, uint64_t* keys, uint32_t* vals,
+                          uint32_t* ranges, uint64_t* d_n_dup, void* workspace, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Stage a5: front-to-back blending (R(M, T) of Eq. 2, 3 and 6)             */
+/* ---------------------------------------------------------------------- */
+
+/* Per pixel (x, y) of view v, walk its tile's list in order: d = xy - (x, y);
+ * power = -1/2 (a dx^2 + c dy^2) - b dx dy; skip if power > 0;
+ * alpha = min(0.99, o exp(power)); skip if alpha < 1/255; stop (without
+ * blending) if T (1 - alpha) < 1e-4; else C += alpha T c, D += alpha T z,
+ * T *= 1 - alpha.  Finally C += T bg.
+ * Outputs (DEVICE planes, see gevo_layout): rgb [3 * total_pixels], depth,
+ * T_final [total_pixels] float; n_contrib [total_pixels] uint32 = 1 + list
+ * position of the last blended entry (0 if none); n_eval (nullable) = list
+ * entries examined including skips and the stopping entry.
+ * bg: HOST float[3].  workspace: the one gevo_bin_sort used (persistent mode
+ * reads its tile order). */
+gevo_status gevo_render_fwd(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                            const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                            float* rgb, float* depth, float* T_final, uint32_t* n_contrib,
+                            uint32_t* n_eval, const gevo_tuning* tuning, void* workspace,
+                            void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Stage a6: reverse walk                                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Gradients of a scalar loss L w.r.t. every record that gevo_render_fwd
+ * blended, given dL/drgb [3 * total_pixels], dL/ddepth [total_pixels] and
+ * dL/dT_final [total_pixels] (dL_ddepth and dL_dT nullable = 0).  Walks each
+ * pixel's list from n_contrib - 1 down to 0, recomputing alpha and recovering
+ * T by T / (1 - alpha) from T_final; per-Gaussian sums are warp-reduced and
+ * added with FP32 atomics (summation order is not deterministic).
+ * out: rows of entries with radius > 0 are zeroed and then accumulated; rows
+ * of culled entries are left untouched. */
+gevo_status gevo_render_bwd(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                            const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                            const float* T_final, const uint32_t* n_contrib,
+                            const float* dL_drgb, const float* dL_ddepth, const float* dL_dT,
+                            gevo_grad2d* out, const gevo_tuning* tuning, void* workspace,
+                            void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Stage a7: projection derivative incl. the se(3) pose gradient            */
+/* ---------------------------------------------------------------------- */
+
+/* Chains dL/d(records) back to the Gaussian parameters (summed over views,
+ * written to *out) and, if dxi != NULL, to a left se(3) perturbation
+ * xi = (rho, phi) of each view's world->camera transform, T <- Exp(xi) T at
+ * xi = 0 (dxi: DEVICE float [n_views][6], written).  The pose enters through
+ * the camera-frame mean, through R in Sigma2 and through the camera centre in
+ * the SH view direction.  Clamped SH channels and clamped Jacobian directions
+ * get zero gradient. */
+gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
+                             const gevo_camera* cams, const gevo_proj* proj,
+                             const gevo_grad2d* grad2d, gevo_gaussian_grads* out, float* dxi,
+                             void* workspace, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Stage a8: L1 loss with stop-gradient targets (E_pho of Eq. 2, E_pc of Eq. 6) */
+/* ---------------------------------------------------------------------- */
+
+/* L = sum_v [ mean_px,ch |rgb - target_rgb| + lambda_depth mean_px |depth -
+ * target_depth| ] over the views of the layout; dL_drgb = sign(.) / (3 P_v),
+ * dL_ddepth = lambda_depth sign(.) / P_v, sign(0) = 0.  depth / target_depth /
+ * dL_ddepth may be NULL when lambda_depth == 0 (dL_ddepth is then untouched).
+ * loss: DEVICE float[n_views] per-view terms (written).  All DEVICE. */
+gevo_status gevo_loss_l1(const gevo_layout* layout, const float* rgb, const float* target_rgb,
+                         const float* depth, const float* target_depth, float lambda_depth,
+                         float* dL_drgb, float* dL_ddepth, float* loss, void* workspace,
+                         void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Status                                                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Synchronises the stream, returns the sticky device error word (GEVO_OK if
+ * clear) and clears it.  Not capturable (it copies to the host). */
+gevo_status gevo_last_error(void* workspace, void* stream);
+
+const char* gevo_status_str(gevo_status s);
+int32_t gevo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GEVO_H */

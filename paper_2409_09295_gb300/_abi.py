@@ -1,0 +1,259 @@
+"""ctypes binding of libgevo.so (include/gevo.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does nothing
+but turn torch tensors into device pointers and the current CUDA stream into a
+handle; all arithmetic runs in the library's kernels.  If the library cannot be
+loaded the import fails loudly -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+MAX_VIEWS = 64
+TILE = 16
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "duplicate capacity exceeded", 3: "CUDA error",
+          4: "device wait timed out", 5: "non-finite value culled"}
+
+
+class GevoError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} failed: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int32), ("total_tiles", ctypes.c_int32),
+                ("total_pixels", ctypes.c_int64),
+                ("width", ctypes.c_int32 * MAX_VIEWS), ("height", ctypes.c_int32 * MAX_VIEWS),
+                ("tiles_x", ctypes.c_int32 * MAX_VIEWS), ("tiles_y", ctypes.c_int32 * MAX_VIEWS),
+                ("tile_base", ctypes.c_int32 * (MAX_VIEWS + 1)),
+                ("pix_base", ctypes.c_int64 * (MAX_VIEWS + 1))]
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacities", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p), ("rgb", ctypes.c_void_p),
+                ("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32)]
+
+
+class GaussianGrads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacities", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p), ("rgb", ctypes.c_void_p)]
+
+
+class Proj(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("conic_opacity", ctypes.c_void_p),
+                ("rgb_depth", ctypes.c_void_p), ("radius", ctypes.c_void_p),
+                ("tiles_touched", ctypes.c_void_p)]
+
+
+class Grad2d(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("conic_opacity", ctypes.c_void_p),
+                ("rgb_depth", ctypes.c_void_p)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("threads_per_tile", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
+# Every symbol include/gevo.h declares (checked by the CPU test-suite).
+EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin_sort",
+           "gevo_render_fwd", "gevo_render_bwd", "gevo_project_bwd", "gevo_loss_l1",
+           "gevo_last_error", "gevo_status_str", "gevo_version"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgevo.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or (build_if_missing and not _build.up_to_date()):
+        if not build_if_missing:
+            raise OSError(f"{path} is missing: run paper_2409_09295_gb300/build.py")
+        _build.build()
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, i32, i64, u64, f32 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                              ctypes.c_float)
+    L.gevo_layout_init.argtypes = [P(Layout), i32, P(i32), P(i32)]
+    L.gevo_layout_init.restype = ctypes.c_int
+    L.gevo_workspace_bytes.argtypes = [P(Layout), i32, u64]
+    L.gevo_workspace_bytes.restype = ctypes.c_size_t
+    L.gevo_project.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), vp, vp]
+    L.gevo_bin_sort.argtypes = [P(Layout), i32, P(Proj), u64, vp, vp, vp, vp, vp, vp]
+    L.gevo_render_fwd.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp, vp,
+                                  P(Tuning), vp, vp]
+    L.gevo_render_bwd.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp, vp,
+                                  P(Grad2d), P(Tuning), vp, vp]
+    L.gevo_project_bwd.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d),
+                                   P(GaussianGrads), vp, vp, vp]
+    L.gevo_loss_l1.argtypes = [P(Layout), vp, vp, vp, vp, f32, vp, vp, vp, vp, vp]
+    L.gevo_last_error.argtypes = [vp, vp]
+    L.gevo_status_str.argtypes = [ctypes.c_int]
+    L.gevo_status_str.restype = ctypes.c_char_p
+    L.gevo_version.restype = i32
+    for name in ("gevo_project", "gevo_bin_sort", "gevo_render_fwd", "gevo_render_bwd",
+                 "gevo_project_bwd", "gevo_loss_l1", "gevo_last_error"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _p(t):
+    """Device pointer of a tensor (None -> NULL)."""
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(fn, code):
+    if code != 0:
+        raise GevoError(fn, code)
+
+
+# ---------------------------------------------------------------------------
+# Host-side set-up
+# ---------------------------------------------------------------------------
+def gevo_layout_init(widths, heights) -> Layout:
+    L = Layout()
+    V = len(widths)
+    W = (ctypes.c_int32 * V)(*[int(w) for w in widths])
+    H = (ctypes.c_int32 * V)(*[int(h) for h in heights])
+    _check("gevo_layout_init", load().gevo_layout_init(ctypes.byref(L), V, W, H))
+    return L
+
+
+def gevo_workspace_bytes(layout: Layout, n: int, dup_capacity: int) -> int:
+    return int(load().gevo_workspace_bytes(ctypes.byref(layout), int(n), int(dup_capacity)))
+
+
+def gaussians_struct(g: dict) -> Gaussians:
+    s = Gaussians()
+    s.means, s.scales, s.quats, s.opacities = (_p(g["means"]), _p(g["scales"]), _p(g["quats"]),
+                                              _p(g["opacities"]))
+    s.sh = _p(g.get("sh"))
+    s.rgb = _p(g.get("rgb"))
+    s.n = int(g["means"].shape[0])
+    s.sh_degree = int(g.get("sh_degree", 0))
+    return s
+
+
+def proj_struct(p: dict) -> Proj:
+    s = Proj()
+    s.xy, s.conic_opacity, s.rgb_depth, s.radius, s.tiles_touched = (
+        _p(p["xy"]), _p(p["conic_opacity"]), _p(p["rgb_depth"]), _p(p["radius"]),
+        _p(p["tiles_touched"]))
+    return s
+
+
+def grad2d_struct(g: dict) -> Grad2d:
+    s = Grad2d()
+    s.xy, s.conic_opacity, s.rgb_depth = _p(g["xy"]), _p(g["conic_opacity"]), _p(g["rgb_depth"])
+    return s
+
+
+def tuning_struct(t) -> Tuning | None:
+    if t is None:
+        return None
+    s = Tuning()
+    s.threads_per_tile = int(t.get("threads_per_tile", 256))
+    s.persistent = int(t.get("persistent", 0))
+    s.blocks_per_sm = int(t.get("blocks_per_sm", 0))
+    return s
+
+
+# ---------------------------------------------------------------------------
+# The entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def gevo_project(layout, g: dict, cams: torch.Tensor, proj: dict, ws: torch.Tensor, stream=None):
+    G = gaussians_struct(g)
+    P_ = proj_struct(proj)
+    _check("gevo_project", load().gevo_project(ctypes.byref(layout), ctypes.byref(G), _p(cams),
+                                               ctypes.byref(P_), _p(ws), _stream(stream)))
+
+
+def gevo_bin_sort(layout, n, proj: dict, dup_capacity, keys, vals, ranges, d_n_dup, ws,
+                  stream=None):
+    P_ = proj_struct(proj)
+    _check("gevo_bin_sort", load().gevo_bin_sort(
+        ctypes.byref(layout), int(n), ctypes.byref(P_), int(dup_capacity), _p(keys), _p(vals),
+        _p(ranges), _p(d_n_dup), _p(ws), _stream(stream)))
+
+
+def gevo_render_fwd(layout, n, proj: dict, vals, ranges, bg, rgb, depth, T_final, n_contrib,
+                    n_eval, ws, tuning=None, stream=None):
+    P_ = proj_struct(proj)
+    bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    tu = tuning_struct(tuning)
+    _check("gevo_render_fwd", load().gevo_render_fwd(
+        ctypes.byref(layout), int(n), ctypes.byref(P_), _p(vals), _p(ranges), bgv, _p(rgb),
+        _p(depth), _p(T_final), _p(n_contrib), _p(n_eval),
+        ctypes.byref(tu) if tu is not None else None, _p(ws), _stream(stream)))
+
+
+def gevo_render_bwd(layout, n, proj: dict, vals, ranges, bg, T_final, n_contrib, dL_drgb,
+                    dL_ddepth, dL_dT, grad2d: dict, ws, tuning=None, stream=None):
+    P_ = proj_struct(proj)
+    G2 = grad2d_struct(grad2d)
+    bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    tu = tuning_struct(tuning)
+    _check("gevo_render_bwd", load().gevo_render_bwd(
+        ctypes.byref(layout), int(n), ctypes.byref(P_), _p(vals), _p(ranges), bgv, _p(T_final),
+        _p(n_contrib), _p(dL_drgb), _p(dL_ddepth), _p(dL_dT), ctypes.byref(G2),
+        ctypes.byref(tu) if tu is not None else None, _p(ws), _stream(stream)))
+
+
+def gevo_project_bwd(layout, g: dict, cams, proj: dict, grad2d: dict, out: dict, dxi, ws,
+                     stream=None):
+    G = gaussians_struct(g)
+    P_ = proj_struct(proj)
+    G2 = grad2d_struct(grad2d)
+    O = GaussianGrads()
+    O.means, O.scales, O.quats, O.opacities = (_p(out["means"]), _p(out["scales"]),
+                                               _p(out["quats"]), _p(out["opacities"]))
+    O.sh = _p(out.get("sh"))
+    O.rgb = _p(out.get("rgb"))
+    _check("gevo_project_bwd", load().gevo_project_bwd(
+        ctypes.byref(layout), ctypes.byref(G), _p(cams), ctypes.byref(P_), ctypes.byref(G2),
+        ctypes.byref(O), _p(dxi), _p(ws), _stream(stream)))
+
+
+def gevo_loss_l1(layout, rgb, target_rgb, depth, target_depth, lambda_depth, dL_drgb, dL_ddepth,
+                 loss, ws=None, stream=None):
+    _check("gevo_loss_l1", load().gevo_loss_l1(
+        ctypes.byref(layout), _p(rgb), _p(target_rgb), _p(depth), _p(target_depth),
+        float(lambda_depth), _p(dL_drgb), _p(dL_ddepth), _p(loss), _p(ws), _stream(stream)))
+
+
+def gevo_last_error(ws, stream=None) -> int:
+    return int(load().gevo_last_error(_p(ws), _stream(stream)))
+
+
+def gevo_status_str(code: int) -> str:
+    return load().gevo_status_str(int(code)).decode()
+
+
+def gevo_version() -> int:
+    return int(load().gevo_version())

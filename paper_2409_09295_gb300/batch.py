@@ -1,0 +1,215 @@
+"""Batched keyframe replay: many views of uneven resolution rendered and
+back-propagated together, captured into CUDA graphs, launch shapes autotuned.
+
+GEVO replaces stored past keyframes by renders of the map (Section I; Section
+III-B2): the consistency loss E_pc of Eq. 6 compares R(M'_t, T_kl) with the
+stop-gradient render R(M_{t-1}, T_kl) over four past views, and the local stage
+(Eq. 2) optimises over the sliding window.  `BatchedReplay` runs that forward +
+L1 + backward over all views at once:
+  - projection reads each Gaussian once and evaluates every view;
+  - keys of all views share one global (view, tile) numbering, so one sort and
+    one set of ranges serve every view;
+  - blending and its reverse walk run as one persistent grid over (view, tile)
+    work items, heaviest tile first;
+  - every stage is captured into a CUDA graph once; replays need no host sync
+    (the duplicate capacity is sized by one untimed pass plus slack, and an
+    overflow is reported through the sticky error word).
+`PlainReplay` is the unbatched reference point: one single-view pipeline per
+view, a host sync to size each sort, default launch shapes, no graph.
+"""
+from __future__ import annotations
+
+import itertools
+
+import torch
+
+from .raster import Pipeline, camera_tensor
+
+CANDIDATES = [dict(threads_per_tile=t, persistent=p, blocks_per_sm=0)
+              for t, p in itertools.product((256, 128, 64), (0, 1))]
+
+
+def _time(fn, reps=3):
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        s.record()
+        fn()
+        e.record()
+        e.synchronize()
+        best = min(best, s.elapsed_time(e))
+    return best
+
+
+class BatchedReplay:
+    def __init__(self, g: dict, cams, target_rgb, target_depth=None, lambda_depth=0.0,
+                 bg=(0.0, 0.0, 0.0), slack=1.3, tuning_fwd=None, tuning_bwd=None,
+                 want_dxi=True, autotune=True):
+        self.g = g
+        self.cams = cams
+        self.sizes = [(int(c["W"]), int(c["H"])) for c in cams]
+        self.camt = camera_tensor(cams, g["means"].device)
+        self.target_rgb, self.target_depth = target_rgb, target_depth
+        self.lambda_depth = float(lambda_depth)
+        self.bg = bg
+        self.want_dxi = want_dxi
+        n = int(g["means"].shape[0])
+        colour = "rgb" if "rgb" in g else "sh"
+        self.pipe = Pipeline(n, self.sizes, 1 << 20, colour=colour,
+                             sh_degree=g.get("sh_degree", 0), device=g["means"].device)
+        D = self.pipe.ensure_capacity(g, self.camt, slack)
+        if self.pipe.capacity < D * slack:
+            self.pipe.alloc_capacity(int(D * slack) + 1024)
+        self.n_dup = D
+        self.tuning_fwd = tuning_fwd or dict(threads_per_tile=256, persistent=1, blocks_per_sm=0)
+        self.tuning_bwd = tuning_bwd or dict(threads_per_tile=256, persistent=1, blocks_per_sm=0)
+        self.tune_log = []
+        if autotune and (tuning_fwd is None or tuning_bwd is None):
+            self.autotune(fwd=tuning_fwd is None, bwd=tuning_bwd is None)
+        self.graphs = None
+
+    # ---- stages with the chosen shapes ------------------------------------------------
+    def _forward(self):
+        p = self.pipe
+        p.project(self.g, self.camt)
+        p.bin_sort()
+        p.render_fwd(self.bg, tuning=self.tuning_fwd)
+        p.loss_l1(self.target_rgb, self.target_depth, self.lambda_depth)
+
+    def _render_bwd(self):
+        p = self.pipe
+        p.render_bwd(p.dL_drgb, p.dL_ddepth if self.lambda_depth else None, None, self.bg,
+                     tuning=self.tuning_bwd)
+
+    def _project_bwd(self):
+        self.pipe.project_bwd(self.g, self.camt, self.want_dxi)
+
+    def stages(self):
+        return [("forward", self._forward), ("render_bwd", self._render_bwd),
+                ("project_bwd", self._project_bwd)]
+
+    def step_eager(self):
+        for _, f in self.stages():
+            f()
+
+    # ---- autotuner ---------------------------------------------------------------------
+    def autotune(self, fwd=True, bwd=True, reps=3):
+        """Times every candidate launch shape of the blend and of its reverse walk
+        on this workload (outputs are bitwise identical across shapes) and keeps
+        the fastest of each."""
+        p = self.pipe
+        self._forward()
+        torch.cuda.synchronize()
+        if fwd:
+            best = None
+            for c in CANDIDATES:
+                t = _time(lambda: p.render_fwd(self.bg, tuning=c), reps)
+                self.tune_log.append(("render_fwd", c, t))
+                if best is None or t < best[0]:
+                    best = (t, c)
+            self.tuning_fwd = dict(best[1])
+            p.render_fwd(self.bg, tuning=self.tuning_fwd)
+            p.loss_l1(self.target_rgb, self.target_depth, self.lambda_depth)
+        if bwd:
+            best = None
+            for c in CANDIDATES:
+                t = _time(lambda: p.render_bwd(p.dL_drgb, p.dL_ddepth if self.lambda_depth else None,
+                                               None, self.bg, tuning=c), reps)
+                self.tune_log.append(("render_bwd", c, t))
+                if best is None or t < best[0]:
+                    best = (t, c)
+            self.tuning_bwd = dict(best[1])
+        torch.cuda.synchronize()
+
+    # ---- graphs ------------------------------------------------------------------------
+    def capture(self):
+        """Captures each stage into its own CUDA graph (three graphs per step, so
+        a stage can be timed with events between graph launches)."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                self.step_eager()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.graphs = []
+        for name, f in self.stages():
+            gph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gph):
+                f()
+            self.graphs.append((name, gph))
+        torch.cuda.synchronize()
+
+    def replay(self, events=None):
+        """One step.  events: optional list of len(stages) + 1 timing events
+        recorded between the stage graphs on the current stream."""
+        if self.graphs is None:
+            self.capture()
+        if events is not None:
+            events[0].record()
+        for i, (_, gph) in enumerate(self.graphs):
+            gph.replay()
+            if events is not None:
+                events[i + 1].record()
+
+    def eval_counts(self):
+        """(E_fwd, E_bwd): list entries examined by the blend (including skips and
+        the stopping entry) and entries walked by the backward (sum of n_contrib)."""
+        p = self.pipe
+        p.project(self.g, self.camt)
+        p.bin_sort()
+        p.render_fwd(self.bg, n_eval=True, tuning=self.tuning_fwd)
+        torch.cuda.synchronize()
+        return int(p.n_eval.sum(dtype=torch.int64)), int(p.n_contrib.sum(dtype=torch.int64))
+
+
+class PlainReplay:
+    """The unbatched path: one single-view pipeline per view, host-synchronised
+    sizing of each sort, default launch shapes, no graph; gradients summed over
+    views afterwards."""
+
+    def __init__(self, g: dict, cams, target_rgb, target_depth=None, lambda_depth=0.0,
+                 bg=(0.0, 0.0, 0.0), slack=1.3, want_dxi=True):
+        self.g = g
+        self.bg = bg
+        self.lambda_depth = float(lambda_depth)
+        self.want_dxi = want_dxi
+        n = int(g["means"].shape[0])
+        colour = "rgb" if "rgb" in g else "sh"
+        dev = g["means"].device
+        self.views = []
+        base = 0
+        for c in cams:
+            W, H = int(c["W"]), int(c["H"])
+            P = W * H
+            pipe = Pipeline(n, [(W, H)], 1 << 20, colour=colour, sh_degree=g.get("sh_degree", 0),
+                            device=dev)
+            camt = camera_tensor([c], dev)
+            D = pipe.ensure_capacity(g, camt, slack)
+            tr = target_rgb[3 * base:3 * (base + P)]
+            td = target_depth[base:base + P] if target_depth is not None else None
+            self.views.append((pipe, camt, tr, td))
+            base += P
+        self.grads = {k: torch.zeros_like(v) for k, v in self.views[0][0].grads.items()}
+
+    def step(self):
+        for k in self.grads:
+            self.grads[k].zero_()
+        for pipe, camt, tr, td in self.views:
+            pipe.project(self.g, camt)
+            pipe.bin_sort()
+            D = int(pipe.n_dup.item())            # host sync sizes the sort
+            if D > pipe.capacity:
+                pipe.last_error()
+                pipe.alloc_capacity(int(D * 1.3) + 1024)
+                pipe.bin_sort()
+            pipe.render_fwd(self.bg)
+            pipe.loss_l1(tr, td, self.lambda_depth)
+            pipe.render_bwd(pipe.dL_drgb, pipe.dL_ddepth if self.lambda_depth else None, None,
+                            self.bg)
+            pipe.project_bwd(self.g, camt, self.want_dxi)
+            for k in self.grads:
+                self.grads[k].add_(pipe.grads[k])

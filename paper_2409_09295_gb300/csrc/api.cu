@@ -1,0 +1,122 @@
+// Host-side set-up, workspace sizing and status calls of the C ABI.
+#include <string.h>
+
+#include "gevo_internal.cuh"
+
+namespace gevo {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap)
+{
+    (void)n;
+    WsLayout w;
+    size_t T = (size_t)L.total_tiles;
+    size_t o = 0;
+    w.err = o;          o = align256(o + 64);
+    w.tile_count = o;   o = align256(o + 4 * T);
+    w.tile_cursor = o;  o = align256(o + 4 * T);
+    w.tile_order = o;   o = align256(o + 4 * T);
+    w.tile_start = o;   o = align256(o + 4 * (T + 1));
+    w.dup_tmp = o;      o = align256(o + 8 * (size_t)cap);
+    w.dup_tmp2 = o;     o = align256(o + 8 * (size_t)cap);
+    w.dxi_acc = o;      o = align256(o + 4 * 6 * (size_t)GEVO_MAX_VIEWS);
+    w.total = o;
+    return w;
+}
+
+int sm_count()
+{
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached = v > 0 ? v : 1;
+    }
+    return cached;
+}
+
+int device_max_smem_optin()
+{
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cached = v > 0 ? v : 48 * 1024;
+    }
+    return cached;
+}
+
+}  // namespace gevo
+
+extern "C" {
+
+gevo_status gevo_layout_init(gevo_layout* layout, int32_t n_views, const int32_t* width,
+                             const int32_t* height)
+{
+    if (!layout || !width || !height || n_views < 1 || n_views > GEVO_MAX_VIEWS)
+        return GEVO_ERR_INVALID;
+    memset(layout, 0, sizeof(*layout));
+    layout->n_views = n_views;
+    int64_t tiles = 0, pix = 0;
+    for (int v = 0; v < n_views; v++) {
+        if (width[v] <= 0 || height[v] <= 0 || width[v] > 65536 || height[v] > 65536)
+            return GEVO_ERR_INVALID;
+        layout->width[v] = width[v];
+        layout->height[v] = height[v];
+        layout->tiles_x[v] = (width[v] + GEVO_TILE - 1) / GEVO_TILE;
+        layout->tiles_y[v] = (height[v] + GEVO_TILE - 1) / GEVO_TILE;
+        layout->tile_base[v] = (int32_t)tiles;
+        layout->pix_base[v] = pix;
+        tiles += (int64_t)layout->tiles_x[v] * layout->tiles_y[v];
+        pix += (int64_t)width[v] * height[v];
+        if (tiles > (1 << 30)) return GEVO_ERR_INVALID;
+    }
+    layout->tile_base[n_views] = (int32_t)tiles;
+    layout->pix_base[n_views] = pix;
+    layout->total_tiles = (int32_t)tiles;
+    layout->total_pixels = pix;
+    return GEVO_OK;
+}
+
+size_t gevo_workspace_bytes(const gevo_layout* layout, int32_t n, uint64_t dup_capacity)
+{
+    if (!layout || layout->n_views < 1) return 0;
+    return gevo::ws_layout(*layout, n, dup_capacity).total;
+}
+
+gevo_status gevo_last_error(void* workspace, void* stream)
+{
+    if (!workspace) return GEVO_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t word = 0;
+    if (cudaMemcpyAsync(&word, workspace, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return GEVO_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return GEVO_ERR_CUDA;
+    if (word) {
+        if (cudaMemsetAsync(workspace, 0, 4, s) != cudaSuccess) return GEVO_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return GEVO_ERR_CUDA;
+    }
+    if (word & gevo::kErrCapacity) return GEVO_ERR_CAPACITY;
+    if (word & gevo::kErrNonFinite) return GEVO_ERR_NONFINITE;
+    return GEVO_OK;
+}
+
+const char* gevo_status_str(gevo_status s)
+{
+    switch (s) {
+    case GEVO_OK: return "ok";
+    case GEVO_ERR_INVALID: return "invalid argument";
+    case GEVO_ERR_CAPACITY: return "duplicate capacity exceeded";
+    case GEVO_ERR_CUDA: return "CUDA error";
+    case GEVO_ERR_TIMEOUT: return "device wait timed out";
+    case GEVO_ERR_NONFINITE: return "non-finite value culled";
+    }
+    return "unknown status";
+}
+
+int32_t gevo_version(void) { return GEVO_VERSION; }
+
+}  // extern "C"

@@ -1,0 +1,343 @@
+// Stages a2-a4 of the splatting renderer GEVO uses (Section I "GS"): emit one
+// (tile, depth) key per (Gaussian, tile) pair, sort the keys bit-exactly and
+// find each tile's range.
+//
+// GB300 design (instead of one 64-bit radix sort over all duplicates):
+//   1. k_count   : per-tile duplicate counts (one L2 atomic per duplicate);
+//   2. k_scan    : one block scans the counts -> tile starts, the ranges, the
+//                  total D and a heaviest-first tile order for later kernels;
+//   3. k_scatter : each duplicate (depth bits << 32 | id) goes into its tile's
+//                  bucket (8 bytes written per duplicate);
+//   4. k_segsort : one block per tile sorts its bucket in shared memory (stable
+//                  LSD radix over the varying depth bytes, then equal depths by
+//                  id) and writes the final 64-bit keys and 32-bit values.
+// The tile is handled by counting, so the sort only moves the depth half; the
+// result is the unique (tile, depth bits, id) order, identical to a full sort.
+#include "gevo_internal.cuh"
+
+namespace gevo {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortSmemItems = 2048;   // longer tiles sort through global memory (L2)
+
+__global__ void __launch_bounds__(256)
+k_count(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restrict__ radius,
+        uint32_t* __restrict__ tile_count)
+{
+    const size_t total = (size_t)L.n_views * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int r = radius[i];
+        if (r <= 0) continue;
+        const int v = (int)(i / n);
+        const float2 m = xy[i];
+        int x0, y0, x1, y1;
+        tile_rect(m.x, m.y, r, L.tiles_x[v], L.tiles_y[v], x0, y0, x1, y1);
+        const int base = L.tile_base[v];
+        const int tx = L.tiles_x[v];
+        for (int y = y0; y < y1; y++)
+            for (int x = x0; x < x1; x++) atomicAdd(tile_count + base + y * tx + x, 1u);
+    }
+}
+
+// One block of 1024 threads.
+__global__ void __launch_bounds__(1024)
+k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* __restrict__ tile_start,
+       uint32_t* __restrict__ tile_cursor, uint32_t* __restrict__ tile_order,
+       uint32_t* __restrict__ ranges, uint64_t* __restrict__ d_n_dup, uint32_t* err)
+{
+    __shared__ unsigned long long s_warp[32];
+    __shared__ uint32_t s_bucket[34];
+    __shared__ uint32_t s_bucket_base[34];
+    __shared__ unsigned long long s_total;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (T + blockDim.x - 1) / blockDim.x;
+    const int lo = min(T, tid * per), hi = min(T, lo + per);
+    if (tid < 34) s_bucket[tid] = 0;
+    unsigned long long mine = 0;
+    for (int t = lo; t < hi; t++) mine += tile_count[t];
+    // block exclusive scan of `mine`
+    unsigned long long incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0ull;
+        unsigned long long wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        s_warp[lane] = wi - w;
+        if (lane == 31) s_total = wi;
+    }
+    __syncthreads();
+    const unsigned long long D = s_total;
+    const bool overflow = D > cap;
+    unsigned long long run = s_warp[warp] + incl - mine;
+    for (int t = lo; t < hi; t++) {
+        const uint32_t c = tile_count[t];
+        tile_start[t] = (uint32_t)run;
+        tile_cursor[t] = 0u;
+        const bool empty = overflow || c == 0;
+        ranges[2 * t] = empty ? 0u : (uint32_t)run;
+        ranges[2 * t + 1] = empty ? 0u : (uint32_t)(run + c);
+        run += c;
+        const int b = c == 0 ? 0 : 32 - __clz(c);
+        atomicAdd(&s_bucket[b], 1u);
+    }
+    if (tid == 0) {
+        *d_n_dup = D;
+        if (overflow) atomicOr(err, kErrCapacity);
+    }
+    __syncthreads();
+    if (tid == 0) {  // heaviest bucket first, empty tiles last
+        uint32_t acc = 0;
+        for (int b = 33; b >= 0; b--) { s_bucket_base[b] = acc; acc += s_bucket[b]; }
+    }
+    __syncthreads();
+    for (int t = lo; t < hi; t++) {
+        const uint32_t c = tile_count[t];
+        const int b = c == 0 ? 0 : 32 - __clz(c);
+        const uint32_t pos = atomicAdd(&s_bucket_base[b], 1u);
+        tile_order[pos] = (uint32_t)t;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_scatter(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restrict__ radius,
+          const float4* __restrict__ rgbz, const uint32_t* __restrict__ tile_start,
+          uint32_t* __restrict__ tile_cursor, const uint64_t* __restrict__ d_n_dup, uint64_t cap,
+          unsigned long long* __restrict__ bucket)
+{
+    if (*d_n_dup > cap) return;
+    const size_t total = (size_t)L.n_views * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int r = radius[i];
+        if (r <= 0) continue;
+        const int v = (int)(i / n);
+        const uint32_t g = (uint32_t)(i - (size_t)v * n);
+        const float2 m = xy[i];
+        const uint32_t dbits = __float_as_uint(rgbz[i].w);
+        const unsigned long long item = ((unsigned long long)dbits << 32) | g;
+        int x0, y0, x1, y1;
+        tile_rect(m.x, m.y, r, L.tiles_x[v], L.tiles_y[v], x0, y0, x1, y1);
+        const int base = L.tile_base[v];
+        const int tx = L.tiles_x[v];
+        for (int y = y0; y < y1; y++)
+            for (int x = x0; x < x1; x++) {
+                const int t = base + y * tx + x;
+                const uint32_t slot = tile_start[t] + atomicAdd(tile_cursor + t, 1u);
+                bucket[slot] = item;
+            }
+    }
+}
+
+// Exclusive scan of 256 values held one per thread (blockDim == 256).
+__device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t* s_tmp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_tmp[warp] = incl;
+    __syncthreads();
+    uint32_t off = 0;
+    for (int w = 0; w < warp; w++) off += s_tmp[w];
+    __syncthreads();
+    return off + incl - v;
+}
+
+// One stable LSD pass over the byte of `a` at bit `shift`, a -> b.
+__device__ void radix_pass(const unsigned long long* a, unsigned long long* b, int L, int shift,
+                           uint32_t* s_base, uint32_t (*s_cnt)[256], uint32_t (*s_off)[256],
+                           uint32_t* s_tmp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    s_base[tid] = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) s_cnt[w][tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < L; i += kSortThreads) atomicAdd(&s_base[(a[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    const uint32_t h = s_base[tid];
+    const uint32_t ex = block_exscan256(h, s_tmp);
+    s_base[tid] = ex;
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int r = 0; r < L; r += kSortThreads) {
+        const int i = r + tid;
+        const bool valid = i < L;
+        const unsigned long long key = valid ? a[i] : 0ull;
+        const uint32_t dg = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && (__ffs(peers) - 1) == lane) s_cnt[warp][dg] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t run = s_base[tid];
+#pragma unroll
+            for (int w = 0; w < kSortWarps; w++) {
+                const uint32_t c = s_cnt[w][tid];
+                s_off[w][tid] = run;
+                run += c;
+                s_cnt[w][tid] = 0;
+            }
+            s_base[tid] = run;
+        }
+        __syncthreads();
+        if (valid) b[s_off[warp][dg] + rank] = key;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ tile_start,
+          const uint32_t* __restrict__ tile_count, const uint64_t* __restrict__ d_n_dup,
+          uint64_t cap, unsigned long long* __restrict__ bucket,
+          unsigned long long* __restrict__ bucket2, unsigned long long* __restrict__ keys_out,
+          uint32_t* __restrict__ vals_out)
+{
+    extern __shared__ unsigned long long s_items[];   // 2 * kSortSmemItems
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_cnt[kSortWarps][256];
+    __shared__ uint32_t s_off[kSortWarps][256];
+    __shared__ uint32_t s_tmp[kSortWarps];
+    __shared__ uint32_t s_or[kSortWarps], s_and[kSortWarps];
+    if (*d_n_dup > cap) return;
+    const uint32_t tile = tile_order[blockIdx.x];
+    const int L = (int)tile_count[tile];
+    if (L == 0) return;
+    const uint32_t s0 = tile_start[tile];
+    const int tid = threadIdx.x;
+    unsigned long long* a;
+    unsigned long long* b;
+    if (L <= kSortSmemItems) {
+        a = s_items;
+        b = s_items + kSortSmemItems;
+        for (int i = tid; i < L; i += kSortThreads) a[i] = bucket[s0 + i];
+    } else {
+        a = bucket + s0;
+        b = bucket2 + s0;
+    }
+    // which depth bytes vary inside this tile
+    uint32_t o = 0u, an = 0xffffffffu;
+    for (int i = tid; i < L; i += kSortThreads) {
+        const uint32_t hi = (uint32_t)(a[i] >> 32);
+        o |= hi;
+        an &= hi;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        o |= __shfl_xor_sync(0xffffffffu, o, d);
+        an &= __shfl_xor_sync(0xffffffffu, an, d);
+    }
+    if ((tid & 31) == 0) { s_or[tid >> 5] = o; s_and[tid >> 5] = an; }
+    __syncthreads();
+    uint32_t vary = 0u;
+    {
+        uint32_t oo = 0u, aa = 0xffffffffu;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; w++) { oo |= s_or[w]; aa &= s_and[w]; }
+        vary = oo ^ aa;
+    }
+    if (L > 1) {
+        for (int d = 0; d < 4; d++) {
+            if (((vary >> (8 * d)) & 255u) == 0u) continue;
+            radix_pass(a, b, L, 32 + 8 * d, s_base, s_cnt, s_off, s_tmp);
+            unsigned long long* t = a;
+            a = b;
+            b = t;
+        }
+        // equal depth bits: order by id (runs are rare and short)
+        for (int i = tid; i < L; i += kSortThreads) {
+            const uint32_t hi = (uint32_t)(a[i] >> 32);
+            const bool start = (i == 0 || (uint32_t)(a[i - 1] >> 32) != hi);
+            if (start && i + 1 < L && (uint32_t)(a[i + 1] >> 32) == hi) {
+                int e = i + 1;
+                while (e < L && (uint32_t)(a[e] >> 32) == hi) e++;
+                for (int j = i + 1; j < e; j++) {
+                    const unsigned long long k = a[j];
+                    int m = j - 1;
+                    while (m >= i && a[m] > k) { a[m + 1] = a[m]; m--; }
+                    a[m + 1] = k;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const unsigned long long th = (unsigned long long)tile << 32;
+    for (int i = tid; i < L; i += kSortThreads) {
+        const unsigned long long k = a[i];
+        keys_out[s0 + i] = th | (k >> 32);
+        vals_out[s0 + i] = (uint32_t)k;
+    }
+}
+
+}  // namespace gevo
+
+using namespace gevo;
+
+extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                                     uint64_t dup_capacity, uint64_t* keys, uint32_t* vals,
+                                     uint32_t* ranges, uint64_t* d_n_dup, void* workspace,
+                                     void* stream)
+{
+    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->radius ||
+        !proj->rgb_depth || !ranges || !d_n_dup || !workspace || !gevo_aligned(workspace, 256) ||
+        (dup_capacity > 0 && (!keys || !vals)) || dup_capacity > 0xffffffffull)
+        return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const WsLayout w = ws_layout(*layout, n, dup_capacity);
+    char* ws = reinterpret_cast<char*>(workspace);
+    uint32_t* err = reinterpret_cast<uint32_t*>(ws + w.err);
+    uint32_t* tile_count = reinterpret_cast<uint32_t*>(ws + w.tile_count);
+    uint32_t* tile_cursor = reinterpret_cast<uint32_t*>(ws + w.tile_cursor);
+    uint32_t* tile_order = reinterpret_cast<uint32_t*>(ws + w.tile_order);
+    uint32_t* tile_start = reinterpret_cast<uint32_t*>(ws + w.tile_start);
+    auto* bucket = reinterpret_cast<unsigned long long*>(ws + w.dup_tmp);
+    auto* bucket2 = reinterpret_cast<unsigned long long*>(ws + w.dup_tmp2);
+    const int T = layout->total_tiles;
+
+    if (cudaMemsetAsync(tile_count, 0, sizeof(uint32_t) * T, st) != cudaSuccess) return GEVO_ERR_CUDA;
+    const size_t total = (size_t)layout->n_views * n;
+    const int sms = sm_count();
+    const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)sms * 8);
+    if (total > 0) {
+        k_count<<<std::max(grid, 1), 256, 0, st>>>(*layout, n,
+                                                   reinterpret_cast<const float2*>(proj->xy),
+                                                   proj->radius, tile_count);
+        GEVO_CHECK_LAUNCH();
+    }
+    k_scan<<<1, 1024, 0, st>>>(T, dup_capacity, tile_count, tile_start, tile_cursor, tile_order,
+                               ranges, d_n_dup, err);
+    GEVO_CHECK_LAUNCH();
+    if (total > 0 && dup_capacity > 0) {
+        k_scatter<<<std::max(grid, 1), 256, 0, st>>>(
+            *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
+            reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor, d_n_dup,
+            dup_capacity, bucket);
+        GEVO_CHECK_LAUNCH();
+        const size_t smem = sizeof(unsigned long long) * 2 * kSortSmemItems;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        k_segsort<<<T, kSortThreads, smem, st>>>(tile_order, tile_start, tile_count, d_n_dup,
+                                                 dup_capacity, bucket, bucket2,
+                                                 reinterpret_cast<unsigned long long*>(keys), vals);
+        GEVO_CHECK_LAUNCH();
+    }
+    return GEVO_OK;
+}

@@ -1,0 +1,92 @@
+// Internal declarations shared by the CUDA translation units of libgevo.
+// Constants are those of the 3DGS formulation the paper renders with
+// (Section I "GS"); the paper itself states none of them.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/gevo.h"
+
+namespace gevo {
+
+constexpr float kNearZ = 0.2f;          // cull at or in front of 0.2 m
+constexpr float kDilation = 0.3f;       // px^2 added to the 2-D covariance
+constexpr float kGuard = 1.3f;          // Jacobian clamp: 1.3x half field of view
+constexpr float kAlphaMax = 0.99f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kTStop = 1e-4f;
+constexpr int kTile = GEVO_TILE;        // 16
+constexpr int kTilePixels = kTile * kTile;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// Bits of the sticky device error word.
+constexpr uint32_t kErrCapacity = 1u << 0;
+constexpr uint32_t kErrNonFinite = 1u << 1;
+
+// Workspace layout (offsets in bytes from the 256-byte aligned base).
+struct WsLayout {
+    size_t err;          // uint32 error word + uint32 queue heads [8]
+    size_t tile_count;   // uint32 [T]
+    size_t tile_cursor;  // uint32 [T]
+    size_t tile_order;   // uint32 [T]  heaviest first
+    size_t tile_start;   // uint32 [T]  exclusive scan of counts
+    size_t dup_tmp;      // uint64 [cap]  (depth bits << 32 | id), bucketed by tile
+    size_t dup_tmp2;     // uint64 [cap]  ping-pong for long tiles
+    size_t dxi_acc;      // float [V][6]
+    size_t total;
+};
+WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap);
+
+// Queue-head slots inside the error block.
+constexpr int kQueueFwd = 1;
+constexpr int kQueueBwd = 2;
+constexpr int kQueueSort = 3;
+
+// Which view owns global tile t (uniform per block; at most 64 views).
+__device__ __forceinline__ int view_of_tile(const gevo_layout& L, int t)
+{
+    int v = 0;
+    while (v + 1 < L.n_views && t >= L.tile_base[v + 1]) ++v;
+    return v;
+}
+
+// Tile rectangle in binary32 (identical rounding in every kernel that bins):
+// [floor((m - r) / 16), floor((m + r + 15) / 16)) per axis, clamped to the grid.
+__device__ __forceinline__ void tile_rect(float mx, float my, int r, int tiles_x, int tiles_y,
+                                          int& x0, int& y0, int& x1, int& y1)
+{
+    const float rf = (float)r;
+    float a = floorf(__fmul_rn(__fsub_rn(mx, rf), 0.0625f));
+    float b = floorf(__fmul_rn(__fsub_rn(my, rf), 0.0625f));
+    float c = floorf(__fmul_rn(__fadd_rn(__fadd_rn(mx, rf), 15.0f), 0.0625f));
+    float d = floorf(__fmul_rn(__fadd_rn(__fadd_rn(my, rf), 15.0f), 0.0625f));
+    x0 = (int)fminf(fmaxf(a, 0.0f), (float)tiles_x);
+    y0 = (int)fminf(fmaxf(b, 0.0f), (float)tiles_y);
+    x1 = (int)fminf(fmaxf(c, 0.0f), (float)tiles_x);
+    y1 = (int)fminf(fmaxf(d, 0.0f), (float)tiles_y);
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+int sm_count();
+int device_max_smem_optin();
+
+}  // namespace gevo
+
+#define GEVO_CHECK_LAUNCH()                                   \
+    do {                                                      \
+        if (cudaGetLastError() != cudaSuccess) return GEVO_ERR_CUDA; \
+    } while (0)
+
+static inline bool gevo_aligned(const void* p, size_t a)
+{
+    return ((uintptr_t)p % a) == 0;
+}

@@ -1,0 +1,484 @@
+// Stage a5 (front-to-back alpha blending) and stage a6 (its reverse walk) of the
+// splatting renderer R(M, T) GEVO optimises through (Section I "GS"; Section
+// III-B Eq. 2, Eq. 3 and the rendered past keyframes of Eq. 6).
+//
+// Work item = one 16x16 tile of one view.  A block of 256 / PPT threads owns the
+// tile; thread t owns pixels (t % 16, (t / 16) * PPT + k), k < PPT, so a warp
+// covers a compact 16 x (2 PPT) strip.  The tile's list is staged into shared
+// memory in batches of 256 records gathered by Gaussian id (coalesced-by-id
+// reads of 40-byte records that mostly hit L2); every thread then walks the
+// batch from shared memory.  Per-pixel state stays in registers.
+//
+// Early termination: a pixel stops at the first entry that would push T below
+// 1e-4; a thread leaves the batch loop when all its pixels stopped, and the
+// block leaves the tile when every thread has (__syncthreads_and per batch).
+//
+// Exponentials: the conic is pre-scaled by -log2(e)/2 (and -log2(e) for the
+// cross term) when staged, so alpha = o * ex2(power2) costs one MUFU.EX2.  The
+// backward evaluates the very same expression, so both passes take identical
+// skip / clamp / stop decisions.
+#include "gevo_internal.cuh"
+
+namespace gevo {
+
+constexpr int kBatch = 256;
+
+struct Rec {
+    float2 xy;
+    float4 co;   // pre-scaled conic (a', b', c') and opacity
+    float4 rz;   // colour, depth
+};
+
+__device__ __forceinline__ float4 prescale(float4 co)
+{
+    return make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, co.w);
+}
+
+// log2 of the Gaussian falloff at offset (dx, dy); identical in both passes.
+__device__ __forceinline__ float power2_at(const float4& co, float dx, float dy)
+{
+    const float ax = __fmul_rn(co.x, dx);
+    const float cy = __fmul_rn(co.z, dy);
+    const float bxy = __fmul_rn(__fmul_rn(co.y, dx), dy);
+    return __fmaf_rn(ax, dx, __fmaf_rn(cy, dy, bxy));
+}
+
+__device__ __forceinline__ void tile_of(const gevo_layout& L, int tile, int& v, int& x0, int& y0)
+{
+    v = view_of_tile(L, tile);
+    const int local = tile - L.tile_base[v];
+    const int tx = L.tiles_x[v];
+    x0 = (local % tx) * kTile;
+    y0 = (local / tx) * kTile;
+}
+
+template <int PPT>
+__global__ void __launch_bounds__(256 / PPT)
+k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
+             const float4* __restrict__ rz, const uint32_t* __restrict__ vals,
+             const uint2* __restrict__ ranges, float bg0, float bg1, float bg2,
+             float* __restrict__ out_rgb, float* __restrict__ out_d, float* __restrict__ out_T,
+             uint32_t* __restrict__ out_nc, uint32_t* __restrict__ out_ne,
+             const uint32_t* __restrict__ order, uint32_t* queue, int n_items)
+{
+    constexpr int NT = 256 / PPT;
+    __shared__ float2 s_xy[kBatch];
+    __shared__ float4 s_co[kBatch];
+    __shared__ float4 s_rz[kBatch];
+    __shared__ uint32_t s_item;
+    const int tid = threadIdx.x;
+
+    for (int it = 0;; it++) {
+        int item;
+        if (queue) {
+            if (tid == 0) s_item = atomicAdd(queue, 1u);
+            __syncthreads();
+            item = (int)s_item;
+            __syncthreads();
+        } else {
+            if (it > 0) break;
+            item = blockIdx.x;
+        }
+        if (item >= n_items) break;
+        const int tile = order ? (int)order[item] : item;
+        int v, x0, y0;
+        tile_of(L, tile, v, x0, y0);
+        const int W = L.width[v], H = L.height[v];
+        const size_t P = (size_t)W * H;
+        const int px = x0 + (tid & 15);
+        const int py0 = y0 + (tid >> 4) * PPT;
+        const uint2 rg = ranges[tile];
+        const size_t vbase = (size_t)v * n;
+
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], Dp[PPT];
+        uint32_t last[PPT], cnt[PPT];
+        bool done[PPT];
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            T[k] = 1.f; C0[k] = C1[k] = C2[k] = Dp[k] = 0.f;
+            last[k] = 0u; cnt[k] = 0u;
+            done[k] = !(px < W && py0 + k < H);
+        }
+        const float fpx = (float)px;
+
+        for (uint32_t b = rg.x; b < rg.y; b += kBatch) {
+            bool mine = true;
+#pragma unroll
+            for (int k = 0; k < PPT; k++) mine = mine && done[k];
+            if (__syncthreads_and(mine)) break;
+            const int nb = (int)min((uint32_t)kBatch, rg.y - b);
+            for (int j = tid; j < nb; j += NT) {
+                const size_t id = vbase + vals[b + j];
+                s_xy[j] = xy[id];
+                s_co[j] = prescale(co[id]);
+                s_rz[j] = rz[id];
+            }
+            __syncthreads();
+            for (int j = 0; j < nb; j++) {
+                bool all = true;
+#pragma unroll
+                for (int k = 0; k < PPT; k++) all = all && done[k];
+                if (all) break;
+                const float2 m = s_xy[j];
+                const float4 c = s_co[j];
+                const float dx = __fsub_rn(m.x, fpx);
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    if (done[k]) continue;
+                    cnt[k]++;
+                    const float dy = __fsub_rn(m.y, (float)(py0 + k));
+                    const float p2 = power2_at(c, dx, dy);
+                    if (p2 > 0.f) continue;
+                    const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, ex2_approx(p2)));
+                    if (alpha < kAlphaMin) continue;
+                    const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+                    if (Tn < kTStop) { done[k] = true; continue; }
+                    const float4 r = s_rz[j];
+                    const float w = __fmul_rn(alpha, T[k]);
+                    C0[k] = __fmaf_rn(w, r.x, C0[k]);
+                    C1[k] = __fmaf_rn(w, r.y, C1[k]);
+                    C2[k] = __fmaf_rn(w, r.z, C2[k]);
+                    Dp[k] = __fmaf_rn(w, r.w, Dp[k]);
+                    T[k] = Tn;
+                    last[k] = b + j - rg.x + 1;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            const int py = py0 + k;
+            if (px < W && py < H) {
+                const size_t pix = (size_t)py * W + px;
+                float* rgb = out_rgb + 3 * (size_t)L.pix_base[v];
+                rgb[pix] = __fmaf_rn(T[k], bg0, C0[k]);
+                rgb[P + pix] = __fmaf_rn(T[k], bg1, C1[k]);
+                rgb[2 * P + pix] = __fmaf_rn(T[k], bg2, C2[k]);
+                const size_t gp = (size_t)L.pix_base[v] + pix;
+                out_d[gp] = Dp[k];
+                out_T[gp] = T[k];
+                out_nc[gp] = last[k];
+                if (out_ne) out_ne[gp] = cnt[k];
+            }
+        }
+    }
+}
+
+// Rows of visible records get zeroed before the reverse walk accumulates.
+__global__ void k_zero_grad2d(size_t total, const int* __restrict__ radius, float2* gxy,
+                              float4* gco, float4* grz)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+         i += (size_t)gridDim.x * blockDim.x) {
+        if (radius[i] > 0) {
+            gxy[i] = make_float2(0.f, 0.f);
+            gco[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            grz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int PPT>
+__global__ void __launch_bounds__(256 / PPT)
+k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
+             const float4* __restrict__ rz, const uint32_t* __restrict__ vals,
+             const uint2* __restrict__ ranges, float bg0, float bg1, float bg2,
+             const float* __restrict__ T_final, const uint32_t* __restrict__ n_contrib,
+             const float* __restrict__ dL_drgb, const float* __restrict__ dL_dd,
+             const float* __restrict__ dL_dT, float2* __restrict__ g_xy, float4* __restrict__ g_co,
+             float4* __restrict__ g_rz, const uint32_t* __restrict__ order, uint32_t* queue,
+             int n_items)
+{
+    constexpr int NT = 256 / PPT;
+    constexpr int NW = NT / 32;
+    __shared__ float2 s_xy[kBatch];
+    __shared__ float4 s_co[kBatch];
+    __shared__ float4 s_rz[kBatch];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ float s_g[kBatch][10];
+    __shared__ uint32_t s_item;
+    __shared__ uint32_t s_max[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int it = 0;; it++) {
+        int item;
+        if (queue) {
+            if (tid == 0) s_item = atomicAdd(queue, 1u);
+            __syncthreads();
+            item = (int)s_item;
+            __syncthreads();
+        } else {
+            if (it > 0) break;
+            item = blockIdx.x;
+        }
+        if (item >= n_items) break;
+        const int tile = order ? (int)order[item] : item;
+        int v, x0, y0;
+        tile_of(L, tile, v, x0, y0);
+        const int W = L.width[v], H = L.height[v];
+        const size_t P = (size_t)W * H;
+        const int px = x0 + (tid & 15);
+        const int py0 = y0 + (tid >> 4) * PPT;
+        const uint2 rg = ranges[tile];
+        const size_t vbase = (size_t)v * n;
+        const float fpx = (float)px;
+
+        float T[PPT], S0[PPT], S1[PPT], S2[PPT], SD[PPT];
+        float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gTT[PPT];
+        uint32_t last[PPT];
+        uint32_t mymax = 0;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            const int py = py0 + k;
+            S0[k] = bg0; S1[k] = bg1; S2[k] = bg2; SD[k] = 0.f;
+            if (px < W && py < H) {
+                const size_t pix = (size_t)py * W + px;
+                const size_t gp = (size_t)L.pix_base[v] + pix;
+                const float* g3 = dL_drgb + 3 * (size_t)L.pix_base[v];
+                T[k] = T_final[gp];
+                last[k] = n_contrib[gp];
+                gC0[k] = g3[pix]; gC1[k] = g3[P + pix]; gC2[k] = g3[2 * P + pix];
+                gD[k] = dL_dd ? dL_dd[gp] : 0.f;
+                gTT[k] = dL_dT ? dL_dT[gp] * T[k] : 0.f;
+            } else {
+                T[k] = 1.f; last[k] = 0u;
+                gC0[k] = gC1[k] = gC2[k] = gD[k] = gTT[k] = 0.f;
+            }
+            mymax = max(mymax, last[k]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+        if (lane == 0) s_max[warp] = mymax;
+        __syncthreads();
+        uint32_t bmax = 0;
+#pragma unroll
+        for (int w = 0; w < NW; w++) bmax = max(bmax, s_max[w]);
+
+        const uint32_t end = rg.x + bmax;
+        for (uint32_t bend = end; bend > rg.x; bend -= min((uint32_t)kBatch, bend - rg.x)) {
+            const uint32_t bstart = bend - min((uint32_t)kBatch, bend - rg.x);
+            const int nb = (int)(bend - bstart);
+            __syncthreads();
+            for (int j = tid; j < nb; j += NT) {
+                const uint32_t id = vals[bstart + j];
+                const size_t gid = vbase + id;
+                s_id[j] = id;
+                s_xy[j] = xy[gid];
+                s_co[j] = prescale(co[gid]);
+                s_rz[j] = rz[gid];
+#pragma unroll
+                for (int q = 0; q < 10; q++) s_g[j][q] = 0.f;
+            }
+            __syncthreads();
+            for (int j = nb - 1; j >= 0; j--) {
+                const uint32_t pos = bstart + j - rg.x;   // list position
+                const float2 m = s_xy[j];
+                const float4 c = s_co[j];
+                const float4 r = s_rz[j];
+                const float dx = __fsub_rn(m.x, fpx);
+                float a_xy0 = 0.f, a_xy1 = 0.f, a_ca = 0.f, a_cb = 0.f, a_cc = 0.f, a_o = 0.f;
+                float a_r = 0.f, a_g = 0.f, a_b = 0.f, a_z = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    if (pos >= last[k]) continue;
+                    const float dy = __fsub_rn(m.y, (float)(py0 + k));
+                    const float p2 = power2_at(c, dx, dy);
+                    if (p2 > 0.f) continue;
+                    const float G = ex2_approx(p2);
+                    const float og = __fmul_rn(c.w, G);
+                    const float alpha = fminf(kAlphaMax, og);
+                    if (alpha < kAlphaMin) continue;
+                    any = true;
+                    const float om = 1.f - alpha;
+                    const float inv = 1.f / om;
+                    const float Ti = T[k] * inv;
+                    T[k] = Ti;
+                    const float w = alpha * Ti;
+                    float dLda = gC0[k] * (r.x - S0[k]) + gC1[k] * (r.y - S1[k]) +
+                                 gC2[k] * (r.z - S2[k]) + gD[k] * (r.w - SD[k]);
+                    dLda = dLda * Ti - gTT[k] * inv;
+                    S0[k] = alpha * r.x + om * S0[k];
+                    S1[k] = alpha * r.y + om * S1[k];
+                    S2[k] = alpha * r.z + om * S2[k];
+                    SD[k] = alpha * r.w + om * SD[k];
+                    a_r += gC0[k] * w; a_g += gC1[k] * w; a_b += gC2[k] * w; a_z += gD[k] * w;
+                    if (og <= kAlphaMax) {
+                        a_o += dLda * G;
+                        const float dp = dLda * alpha;
+                        a_ca += -0.5f * dx * dx * dp;
+                        a_cb += -dx * dy * dp;
+                        a_cc += -0.5f * dy * dy * dp;
+                        const float s = dp * kLn2;
+                        a_xy0 += s * (2.f * c.x * dx + c.y * dy);
+                        a_xy1 += s * (2.f * c.z * dy + c.y * dx);
+                    }
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    a_xy0 = warp_sum(a_xy0); a_xy1 = warp_sum(a_xy1);
+                    a_ca = warp_sum(a_ca); a_cb = warp_sum(a_cb); a_cc = warp_sum(a_cc);
+                    a_o = warp_sum(a_o);
+                    a_r = warp_sum(a_r); a_g = warp_sum(a_g); a_b = warp_sum(a_b); a_z = warp_sum(a_z);
+                    if (lane == 0) {
+                        float* gg = s_g[j];
+                        atomicAdd(gg + 0, a_xy0); atomicAdd(gg + 1, a_xy1);
+                        atomicAdd(gg + 2, a_ca); atomicAdd(gg + 3, a_cb); atomicAdd(gg + 4, a_cc);
+                        atomicAdd(gg + 5, a_o);
+                        atomicAdd(gg + 6, a_r); atomicAdd(gg + 7, a_g); atomicAdd(gg + 8, a_b);
+                        atomicAdd(gg + 9, a_z);
+                    }
+                }
+            }
+            __syncthreads();
+            for (int j = tid; j < nb; j += NT) {
+                const float* gg = s_g[j];
+                bool nz = false;
+#pragma unroll
+                for (int q = 0; q < 10; q++) nz = nz || gg[q] != 0.f;
+                if (!nz) continue;
+                const size_t gid = vbase + s_id[j];
+                atomicAdd(g_xy + gid, make_float2(gg[0], gg[1]));
+                atomicAdd(g_co + gid, make_float4(gg[2], gg[3], gg[4], gg[5]));
+                atomicAdd(g_rz + gid, make_float4(gg[6], gg[7], gg[8], gg[9]));
+            }
+        }
+    }
+}
+
+static int pick_ppt(const gevo_tuning* t)
+{
+    const int th = t ? t->threads_per_tile : 256;
+    return th == 64 ? 4 : (th == 128 ? 2 : 1);
+}
+
+template <int PPT, typename K>
+static int persistent_grid(K kernel, const gevo_tuning* t)
+{
+    int per_sm = t ? t->blocks_per_sm : 0;
+    if (per_sm <= 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256 / PPT, 0);
+        per_sm = occ > 0 ? occ : 1;
+    }
+    return per_sm * sm_count();
+}
+
+template <int PPT>
+static gevo_status launch_fwd(const gevo_layout& L, int n, const gevo_proj& p, const uint32_t* vals,
+                              const uint32_t* ranges, const float* bg, float* rgb, float* depth,
+                              float* Tf, uint32_t* nc, uint32_t* ne, const gevo_tuning* t,
+                              char* ws, cudaStream_t st)
+{
+    const WsLayout w = ws_layout(L, n, 0);
+    const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + w.tile_order);
+    uint32_t* queue = nullptr;
+    int grid = L.total_tiles;
+    if (t && t->persistent) {
+        queue = reinterpret_cast<uint32_t*>(ws + w.err) + kQueueFwd;
+        if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GEVO_ERR_CUDA;
+        grid = std::min(grid, persistent_grid<PPT>(k_render_fwd<PPT>, t));
+    }
+    k_render_fwd<PPT><<<grid, 256 / PPT, 0, st>>>(
+        L, n, reinterpret_cast<const float2*>(p.xy), reinterpret_cast<const float4*>(p.conic_opacity),
+        reinterpret_cast<const float4*>(p.rgb_depth), vals, reinterpret_cast<const uint2*>(ranges),
+        bg[0], bg[1], bg[2], rgb, depth, Tf, nc, ne, order, queue, L.total_tiles);
+    GEVO_CHECK_LAUNCH();
+    return GEVO_OK;
+}
+
+template <int PPT>
+static gevo_status launch_bwd(const gevo_layout& L, int n, const gevo_proj& p, const uint32_t* vals,
+                              const uint32_t* ranges, const float* bg, const float* Tf,
+                              const uint32_t* nc, const float* gC, const float* gD, const float* gT,
+                              const gevo_grad2d& out, const gevo_tuning* t, char* ws,
+                              cudaStream_t st)
+{
+    const WsLayout w = ws_layout(L, n, 0);
+    const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + w.tile_order);
+    uint32_t* queue = nullptr;
+    int grid = L.total_tiles;
+    if (t && t->persistent) {
+        queue = reinterpret_cast<uint32_t*>(ws + w.err) + kQueueBwd;
+        if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GEVO_ERR_CUDA;
+        grid = std::min(grid, persistent_grid<PPT>(k_render_bwd<PPT>, t));
+    }
+    k_render_bwd<PPT><<<grid, 256 / PPT, 0, st>>>(
+        L, n, reinterpret_cast<const float2*>(p.xy), reinterpret_cast<const float4*>(p.conic_opacity),
+        reinterpret_cast<const float4*>(p.rgb_depth), vals, reinterpret_cast<const uint2*>(ranges),
+        bg[0], bg[1], bg[2], Tf, nc, gC, gD, gT, reinterpret_cast<float2*>(out.xy),
+        reinterpret_cast<float4*>(out.conic_opacity), reinterpret_cast<float4*>(out.rgb_depth),
+        order, queue, L.total_tiles);
+    GEVO_CHECK_LAUNCH();
+    return GEVO_OK;
+}
+
+static bool valid_tuning(const gevo_tuning* t)
+{
+    if (!t) return true;
+    return (t->threads_per_tile == 64 || t->threads_per_tile == 128 || t->threads_per_tile == 256) &&
+           t->blocks_per_sm >= 0;
+}
+
+}  // namespace gevo
+
+using namespace gevo;
+
+extern "C" gevo_status gevo_render_fwd(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                                       const uint32_t* vals, const uint32_t* ranges,
+                                       const float* bg, float* rgb, float* depth, float* T_final,
+                                       uint32_t* n_contrib, uint32_t* n_eval,
+                                       const gevo_tuning* tuning, void* workspace, void* stream)
+{
+    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+        !proj->rgb_depth || !ranges || !bg || !rgb || !depth || !T_final || !n_contrib ||
+        !workspace || !gevo_aligned(workspace, 256) || !valid_tuning(tuning) ||
+        !gevo_aligned(ranges, 8) || !gevo_aligned(proj->conic_opacity, 16) ||
+        !gevo_aligned(proj->rgb_depth, 16) || !gevo_aligned(proj->xy, 8))
+        return GEVO_ERR_INVALID;
+    if (!vals) return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = reinterpret_cast<char*>(workspace);
+    switch (pick_ppt(tuning)) {
+    case 4: return launch_fwd<4>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
+    case 2: return launch_fwd<2>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
+    default: return launch_fwd<1>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
+    }
+}
+
+extern "C" gevo_status gevo_render_bwd(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                                       const uint32_t* vals, const uint32_t* ranges,
+                                       const float* bg, const float* T_final,
+                                       const uint32_t* n_contrib, const float* dL_drgb,
+                                       const float* dL_ddepth, const float* dL_dT,
+                                       gevo_grad2d* out, const gevo_tuning* tuning,
+                                       void* workspace, void* stream)
+{
+    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+        !proj->rgb_depth || !proj->radius || !vals || !ranges || !bg || !T_final || !n_contrib ||
+        !dL_drgb || !out || !out->xy || !out->conic_opacity || !out->rgb_depth || !workspace ||
+        !gevo_aligned(workspace, 256) || !valid_tuning(tuning) || !gevo_aligned(ranges, 8) ||
+        !gevo_aligned(out->conic_opacity, 16) || !gevo_aligned(out->rgb_depth, 16) ||
+        !gevo_aligned(out->xy, 8))
+        return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = reinterpret_cast<char*>(workspace);
+    const size_t total = (size_t)layout->n_views * n;
+    if (total > 0) {
+        const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)sm_count() * 16);
+        k_zero_grad2d<<<grid, 256, 0, st>>>(total, proj->radius, reinterpret_cast<float2*>(out->xy),
+                                            reinterpret_cast<float4*>(out->conic_opacity),
+                                            reinterpret_cast<float4*>(out->rgb_depth));
+        GEVO_CHECK_LAUNCH();
+    }
+    switch (pick_ppt(tuning)) {
+    case 4: return launch_bwd<4>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
+    case 2: return launch_bwd<2>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
+    default: return launch_bwd<1>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
+    }
+}

@@ -1,0 +1,205 @@
+"""Buffers and call sequence of the rasterizer (stages a1-a8) on one GPU.
+
+`Pipeline` owns the device buffers of one (Gaussian count, set of view sizes,
+duplicate capacity) configuration and issues the C ABI calls in order on the
+current stream; `GevoRasterize` puts the forward / backward pair behind
+torch.autograd.  torch provides device memory and streams only: every stage of
+the computation runs in libgevo's kernels.
+
+Renders are the R(M, T) of GEVO's objectives (Section III-B): Eq. 2 (local
+stage), Eq. 3 (global stage) and the rendered past keyframes of Eq. 6.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _abi as abi
+
+DEFAULT_TUNING = {"threads_per_tile": 256, "persistent": 0, "blocks_per_sm": 0}
+
+
+def camera_tensor(cams, device="cuda") -> torch.Tensor:
+    """[V, 16] float32: R (row-major, world->camera), t, fx, fy, cx, cy."""
+    rows = []
+    for c in cams:
+        r = np.zeros(16, np.float32)
+        r[0:9] = np.asarray(c["R"], np.float32).reshape(9)
+        r[9:12] = np.asarray(c["t"], np.float32)
+        r[12:16] = [c["fx"], c["fy"], c["cx"], c["cy"]]
+        rows.append(r)
+    return torch.from_numpy(np.stack(rows)).to(device)
+
+
+def gaussians_to_device(scene: dict, device="cuda") -> dict:
+    g = {}
+    for k in ("means", "scales", "quats", "opacities", "sh", "rgb"):
+        if scene.get(k) is not None:
+            g[k] = torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).to(device)
+    g["sh_degree"] = int(scene.get("sh_degree", 0))
+    return g
+
+
+class Pipeline:
+    """Device buffers + the stage calls for one configuration.
+
+    sizes: list of (W, H) per view.  colour: "rgb" or "sh" (with sh_degree).
+    dup_capacity: (Gaussian, tile) pairs the sort may hold."""
+
+    def __init__(self, n: int, sizes, dup_capacity: int, colour: str = "rgb", sh_degree: int = 0,
+                 device="cuda", tuning=None):
+        self.n = int(n)
+        self.sizes = [(int(w), int(h)) for w, h in sizes]
+        self.V = len(self.sizes)
+        self.device = torch.device(device)
+        self.colour = colour
+        self.sh_degree = int(sh_degree)
+        self.tuning = dict(DEFAULT_TUNING if tuning is None else tuning)
+        self.layout = abi.gevo_layout_init([s[0] for s in self.sizes], [s[1] for s in self.sizes])
+        self.T = int(self.layout.total_tiles)
+        self.P = int(self.layout.total_pixels)
+        self.pix_base = [int(self.layout.pix_base[v]) for v in range(self.V + 1)]
+        self.alloc_capacity(dup_capacity)
+        dev, f32, i32 = self.device, torch.float32, torch.int32
+        VN = max(self.V * self.n, 1)
+        self.proj = dict(xy=torch.zeros(VN, 2, dtype=f32, device=dev),
+                         conic_opacity=torch.zeros(VN, 4, dtype=f32, device=dev),
+                         rgb_depth=torch.zeros(VN, 4, dtype=f32, device=dev),
+                         radius=torch.zeros(VN, dtype=i32, device=dev),
+                         tiles_touched=torch.zeros(VN, dtype=i32, device=dev))
+        self.ranges = torch.zeros(self.T, 2, dtype=i32, device=dev)
+        self.n_dup = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.rgb = torch.zeros(3 * self.P, dtype=f32, device=dev)
+        self.depth = torch.zeros(self.P, dtype=f32, device=dev)
+        self.T_final = torch.zeros(self.P, dtype=f32, device=dev)
+        self.n_contrib = torch.zeros(self.P, dtype=i32, device=dev)
+        self.n_eval = torch.zeros(self.P, dtype=i32, device=dev)
+        self.grad2d = dict(xy=torch.zeros(VN, 2, dtype=f32, device=dev),
+                           conic_opacity=torch.zeros(VN, 4, dtype=f32, device=dev),
+                           rgb_depth=torch.zeros(VN, 4, dtype=f32, device=dev))
+        self.dL_drgb = torch.zeros(3 * self.P, dtype=f32, device=dev)
+        self.dL_ddepth = torch.zeros(self.P, dtype=f32, device=dev)
+        self.loss = torch.zeros(self.V, dtype=f32, device=dev)
+        self.dxi = torch.zeros(self.V, 6, dtype=f32, device=dev)
+        K = (self.sh_degree + 1) ** 2
+        n1 = max(self.n, 1)
+        self.grads = dict(means=torch.zeros(n1, 3, dtype=f32, device=dev),
+                          scales=torch.zeros(n1, 3, dtype=f32, device=dev),
+                          quats=torch.zeros(n1, 4, dtype=f32, device=dev),
+                          opacities=torch.zeros(n1, dtype=f32, device=dev))
+        if colour == "rgb":
+            self.grads["rgb"] = torch.zeros(n1, 3, dtype=f32, device=dev)
+        else:
+            self.grads["sh"] = torch.zeros(n1, K, 3, dtype=f32, device=dev)
+
+    def alloc_capacity(self, dup_capacity: int):
+        self.capacity = max(int(dup_capacity), 1)
+        nbytes = abi.gevo_workspace_bytes(self.layout, self.n, self.capacity)
+        self.ws = torch.zeros(nbytes, dtype=torch.uint8, device=self.device)
+        self.keys = torch.zeros(self.capacity, dtype=torch.int64, device=self.device)
+        self.vals = torch.zeros(self.capacity, dtype=torch.int32, device=self.device)
+
+    # ---- per-view views of the planar outputs -------------------------------------------
+    def view_rgb(self, buf, v):
+        W, H = self.sizes[v]
+        return buf[3 * self.pix_base[v]:3 * self.pix_base[v + 1]].view(3, H, W)
+
+    def view_plane(self, buf, v):
+        W, H = self.sizes[v]
+        return buf[self.pix_base[v]:self.pix_base[v + 1]].view(H, W)
+
+    # ---- stages ----------------------------------------------------------------------
+    def project(self, g, cams):
+        abi.gevo_project(self.layout, g, cams, self.proj, self.ws)
+
+    def bin_sort(self):
+        abi.gevo_bin_sort(self.layout, self.n, self.proj, self.capacity, self.keys, self.vals,
+                          self.ranges, self.n_dup, self.ws)
+
+    def render_fwd(self, bg=(0.0, 0.0, 0.0), n_eval=False, tuning=None):
+        abi.gevo_render_fwd(self.layout, self.n, self.proj, self.vals, self.ranges, bg, self.rgb,
+                            self.depth, self.T_final, self.n_contrib,
+                            self.n_eval if n_eval else None, self.ws,
+                            tuning or self.tuning)
+
+    def loss_l1(self, target_rgb, target_depth=None, lambda_depth=0.0):
+        abi.gevo_loss_l1(self.layout, self.rgb, target_rgb,
+                         self.depth if lambda_depth else None,
+                         target_depth if lambda_depth else None, lambda_depth, self.dL_drgb,
+                         self.dL_ddepth if lambda_depth else None, self.loss, self.ws)
+
+    def render_bwd(self, dL_drgb, dL_ddepth=None, dL_dT=None, bg=(0.0, 0.0, 0.0), tuning=None):
+        abi.gevo_render_bwd(self.layout, self.n, self.proj, self.vals, self.ranges, bg,
+                            self.T_final, self.n_contrib, dL_drgb, dL_ddepth, dL_dT, self.grad2d,
+                            self.ws, tuning or self.tuning)
+
+    def project_bwd(self, g, cams, want_dxi=True):
+        abi.gevo_project_bwd(self.layout, g, cams, self.proj, self.grad2d, self.grads,
+                             self.dxi if want_dxi else None, self.ws)
+
+    # ---- composites ------------------------------------------------------------------
+    def forward(self, g, cams, bg=(0.0, 0.0, 0.0), n_eval=False):
+        self.project(g, cams)
+        self.bin_sort()
+        self.render_fwd(bg, n_eval)
+
+    def step(self, g, cams, target_rgb, target_depth=None, lambda_depth=0.0,
+             bg=(0.0, 0.0, 0.0), want_dxi=True):
+        """One forward + L1 loss + backward pass over every view (no host sync)."""
+        self.forward(g, cams, bg)
+        self.loss_l1(target_rgb, target_depth, lambda_depth)
+        self.render_bwd(self.dL_drgb, self.dL_ddepth if lambda_depth else None, None, bg)
+        self.project_bwd(g, cams, want_dxi)
+
+    def last_error(self) -> int:
+        return abi.gevo_last_error(self.ws)
+
+    def ensure_capacity(self, g, cams, slack=1.25):
+        """Host-synchronising sizing pass: project + count, then grow the duplicate
+        capacity if needed.  Returns the duplicate count D."""
+        self.project(g, cams)
+        self.bin_sort()
+        D = int(self.n_dup.item())
+        if D > self.capacity:
+            abi.gevo_last_error(self.ws)
+            self.alloc_capacity(int(D * slack) + 1024)
+        return D
+
+
+class GevoRasterize(torch.autograd.Function):
+    """(means, scales, quats, opacities, colours, twist) -> (rgb, depth, T_final).
+
+    colours: rgb [N,3] or SH [N,K,3] (as the pipeline was built).  twist: [V,6]
+    zeros standing for a left se(3) perturbation of each view's pose; its
+    gradient is dL/dxi.  Outputs are the planar view-major buffers described in
+    include/gevo.h (use Pipeline.view_rgb / view_plane to slice views).  The
+    backward recomputes alpha from the kept n_contrib and T_final."""
+
+    @staticmethod
+    def forward(ctx, means, scales, quats, opacities, colours, twist, pipe, cams, bg):
+        g = dict(means=means.detach().contiguous(), scales=scales.detach().contiguous(),
+                 quats=quats.detach().contiguous(), opacities=opacities.detach().contiguous(),
+                 sh_degree=pipe.sh_degree)
+        g["rgb" if pipe.colour == "rgb" else "sh"] = colours.detach().contiguous()
+        pipe.forward(g, cams, bg)
+        ctx.pipe, ctx.g, ctx.cams, ctx.bg = pipe, g, cams, bg
+        return pipe.rgb.clone(), pipe.depth.clone(), pipe.T_final.clone()
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_T):
+        pipe = ctx.pipe
+        z = lambda t, like: (t.contiguous() if t is not None else torch.zeros_like(like))
+        pipe.render_bwd(z(g_rgb, pipe.rgb), z(g_depth, pipe.depth),
+                        g_T.contiguous() if g_T is not None else None, ctx.bg)
+        pipe.project_bwd(ctx.g, ctx.cams, want_dxi=True)
+        gr = pipe.grads
+        col = gr["rgb"] if pipe.colour == "rgb" else gr["sh"]
+        return (gr["means"].clone(), gr["scales"].clone(), gr["quats"].clone(),
+                gr["opacities"].clone(), col.clone(), pipe.dxi.clone(), None, None, None)
+
+
+def rasterize(pipe: Pipeline, means, scales, quats, opacities, colours, cams, twist=None,
+              bg=(0.0, 0.0, 0.0)):
+    if twist is None:
+        twist = torch.zeros(pipe.V, 6, device=means.device, requires_grad=False)
+    return GevoRasterize.apply(means, scales, quats, opacities, colours, twist, pipe, cams, bg)

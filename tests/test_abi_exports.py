@@ -1,0 +1,60 @@
+"""CPU checks of the C ABI library: it builds for sm_103a, loads without a GPU,
+exports every symbol include/gevo.h declares, and its host-only set-up calls
+(layout, workspace size, status strings) behave as the header states.  No
+compute entry point is called here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "gevo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gevo_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2409_09295_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_stage_calls():
+    names = _declared()
+    for want in ("gevo_project", "gevo_bin_sort", "gevo_render_fwd", "gevo_render_bwd",
+                 "gevo_project_bwd", "gevo_loss_l1", "gevo_layout_init",
+                 "gevo_workspace_bytes", "gevo_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2409_09295_gb300 import _abi
+    assert sorted(_abi.EXPORTS) == sorted(n for n in _declared())
+
+
+def test_layout_and_workspace_host_calls():
+    from paper_2409_09295_gb300 import _abi
+    L = _abi.gevo_layout_init([640] * 12 + [320] * 4, [480] * 12 + [240] * 4)
+    assert L.n_views == 16
+    assert L.total_tiles == 12 * 40 * 30 + 4 * 20 * 15
+    assert L.total_pixels == 12 * 640 * 480 + 4 * 320 * 240
+    assert [L.tile_base[v] for v in (0, 1, 12, 16)] == [0, 1200, 14400, 15600]
+    L2 = _abi.gevo_layout_init([1200], [680])
+    assert (L2.tiles_x[0], L2.tiles_y[0]) == (75, 43)   # partial last tile row
+    ws = _abi.gevo_workspace_bytes(L, 500_000, 10_000_000)
+    assert ws >= 16 * 10_000_000 and ws % 256 == 0
+    with pytest.raises(_abi.GevoError):
+        _abi.gevo_layout_init([], [])
+    with pytest.raises(_abi.GevoError):
+        _abi.gevo_layout_init([0], [10])
+    assert _abi.gevo_status_str(2) == "duplicate capacity exceeded"
+    assert _abi.gevo_version() == 1
