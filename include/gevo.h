@@ -59,7 +59,8 @@ typedef enum {
     GEVO_ERR_CAPACITY = 2,  /* device: duplicate count exceeded dup_capacity     */
     GEVO_ERR_CUDA = 3,      /* a CUDA runtime call or launch failed              */
     GEVO_ERR_TIMEOUT = 4,   /* reserved: no call waits on the device             */
-    GEVO_ERR_NONFINITE = 5  /* device: a non-finite projected value was culled   */
+    GEVO_ERR_NONFINITE = 5, /* device: a non-finite projected value was culled   */
+    GEVO_ERR_SCRATCH_LIMIT = 6 /* sizes exceed gevo_bin_sort_noalloc's fixed scratch */
 } gevo_status;
 
 /* Pinhole camera of one view, world -> camera: p_c = R * p_w + t, camera x
@@ -198,6 +199,31 @@ gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,
 gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
                           uint64_t dup_capacity, uint64_t* keys, uint32_t* vals,
                           uint32_t* ranges, uint64_t* d_n_dup, void* workspace, void* stream);
+
+/* Same operation and outputs as gevo_bin_sort, for callers that cannot
+ * allocate device memory: no workspace argument, and the call itself allocates
+ * nothing (no cudaMalloc, no allocating library routine).  Such callers include
+ * plug-ins hosted by a renderer or an inference server that owns every device
+ * allocation, and real-time loops where an allocator call, with its latency
+ * and implicit synchronisation, is not allowed.  The paper has no counterpart:
+ * this is a deployment variant of stages a2-a4.
+ * Scratch: a file-scope static device array of GEVO_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.  It caps
+ * dup_capacity at GEVO_NOALLOC_MAX_DUPS and the layout at GEVO_NOALLOC_MAX_TILES
+ * tiles; larger sizes return GEVO_ERR_SCRATCH_LIMIT without launching.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and clears the parts that must
+ * start at zero, so calls whose GPU work overlaps (other streams, other host
+ * threads) race and must be serialised by the caller.  A duplicate count above
+ * dup_capacity is reported only through *d_n_dup > dup_capacity (the ranges are
+ * then all (0, 0)); there is no workspace for gevo_last_error to read. */
+#define GEVO_NOALLOC_MAX_DUPS (1ull << 21)
+#define GEVO_NOALLOC_MAX_TILES (1 << 16)
+#define GEVO_NOALLOC_SCRATCH_BYTES ((size_t)35 << 20)
+gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                                  uint64_t dup_capacity, uint64_t* keys, uint32_t* vals,
+                                  uint32_t* ranges, uint64_t* d_n_dup, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Stage a5: front-to-back blending (R(M, T) of Eq. 2, 3 and 6)             */

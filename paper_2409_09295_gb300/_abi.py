@@ -18,7 +18,8 @@ MAX_VIEWS = 64
 TILE = 16
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "duplicate capacity exceeded", 3: "CUDA error",
-          4: "device wait timed out", 5: "non-finite value culled"}
+          4: "device wait timed out", 5: "non-finite value culled",
+          6: "size exceeds the fixed no-allocation scratch"}
 
 
 class GevoError(RuntimeError):
@@ -68,7 +69,7 @@ class Tuning(ctypes.Structure):
 # Every symbol include/gevo.h declares (checked by the CPU test-suite).
 EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin_sort",
            "gevo_render_fwd", "gevo_render_bwd", "gevo_project_bwd", "gevo_loss_l1",
-           "gevo_last_error", "gevo_status_str", "gevo_version"]
+           "gevo_last_error", "gevo_status_str", "gevo_version", "gevo_bin_sort_noalloc"]
 
 _lib = None
 
@@ -97,6 +98,8 @@ def load(build_if_missing: bool = True):
     L.gevo_workspace_bytes.restype = ctypes.c_size_t
     L.gevo_project.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), vp, vp]
     L.gevo_bin_sort.argtypes = [P(Layout), i32, P(Proj), u64, vp, vp, vp, vp, vp, vp]
+    L.gevo_bin_sort_noalloc.argtypes = [P(Layout), i32, P(Proj), u64, vp, vp, vp, vp, vp]
+    L.gevo_bin_sort_noalloc.restype = ctypes.c_int
     L.gevo_render_fwd.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp, vp,
                                   P(Tuning), vp, vp]
     L.gevo_render_bwd.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp, vp,
@@ -200,6 +203,16 @@ def gevo_bin_sort(layout, n, proj: dict, dup_capacity, keys, vals, ranges, d_n_d
     _check("gevo_bin_sort", load().gevo_bin_sort(
         ctypes.byref(layout), int(n), ctypes.byref(P_), int(dup_capacity), _p(keys), _p(vals),
         _p(ranges), _p(d_n_dup), _p(ws), _stream(stream)))
+
+
+def gevo_bin_sort_noalloc(layout, n, proj: dict, dup_capacity, keys, vals, ranges, d_n_dup,
+                          stream=None):
+    """gevo_bin_sort without a workspace: for callers that cannot allocate device
+    memory; its scratch is a fixed static device array (see include/gevo.h)."""
+    P_ = proj_struct(proj)
+    _check("gevo_bin_sort_noalloc", load().gevo_bin_sort_noalloc(
+        ctypes.byref(layout), int(n), ctypes.byref(P_), int(dup_capacity), _p(keys), _p(vals),
+        _p(ranges), _p(d_n_dup), _stream(stream)))
 
 
 def gevo_render_fwd(layout, n, proj: dict, vals, ranges, bg, rgb, depth, T_final, n_contrib,

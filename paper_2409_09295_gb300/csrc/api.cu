@@ -113,6 +113,7 @@ const char* gevo_status_str(gevo_status s)
     case GEVO_ERR_CUDA: return "CUDA error";
     case GEVO_ERR_TIMEOUT: return "device wait timed out";
     case GEVO_ERR_NONFINITE: return "non-finite value culled";
+    case GEVO_ERR_SCRATCH_LIMIT: return "size exceeds the fixed no-allocation scratch";
     }
     return "unknown status";
 }

@@ -341,3 +341,92 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
     }
     return GEVO_OK;
 }
+
+// ---------------------------------------------------------------------------
+// gevo_bin_sort_noalloc: the same sort for callers that cannot allocate device
+// memory (for example plug-ins of a host application that owns every device
+// allocation, or real-time loops that must not call an allocator).  Its
+// scratch is the static array below; the launch sequence is that of
+// gevo_bin_sort with workspace pointers into the array.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace gevo {
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GEVO_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch per device ordinal.  In host code the
+// array's name is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress with the device current.
+static void* noalloc_scratch_address()
+{
+    static std::mutex mu;
+    static void* addr[256] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+}  // namespace gevo
+
+extern "C" gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t n,
+                                             const gevo_proj* proj, uint64_t dup_capacity,
+                                             uint64_t* keys, uint32_t* vals, uint32_t* ranges,
+                                             uint64_t* d_n_dup, void* stream)
+{
+    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->radius ||
+        !proj->rgb_depth || !ranges || !d_n_dup || (dup_capacity > 0 && (!keys || !vals)))
+        return GEVO_ERR_INVALID;
+    if (dup_capacity > GEVO_NOALLOC_MAX_DUPS || layout->total_tiles > GEVO_NOALLOC_MAX_TILES)
+        return GEVO_ERR_SCRATCH_LIMIT;
+    const WsLayout w = ws_layout(*layout, n, dup_capacity);
+    if (w.total > GEVO_NOALLOC_SCRATCH_BYTES) return GEVO_ERR_SCRATCH_LIMIT;
+    char* ws = reinterpret_cast<char*>(noalloc_scratch_address());
+    if (!ws) return GEVO_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t* err = reinterpret_cast<uint32_t*>(ws + w.err);
+    uint32_t* tile_count = reinterpret_cast<uint32_t*>(ws + w.tile_count);
+    uint32_t* tile_cursor = reinterpret_cast<uint32_t*>(ws + w.tile_cursor);
+    uint32_t* tile_order = reinterpret_cast<uint32_t*>(ws + w.tile_order);
+    uint32_t* tile_start = reinterpret_cast<uint32_t*>(ws + w.tile_start);
+    auto* bucket = reinterpret_cast<unsigned long long*>(ws + w.dup_tmp);
+    auto* bucket2 = reinterpret_cast<unsigned long long*>(ws + w.dup_tmp2);
+    const int T = layout->total_tiles;
+    // the array keeps the previous call's contents: zero the error word and the
+    // tile counts; every other scratch field is fully written before it is read
+    if (cudaMemsetAsync(err, 0, 64, st) != cudaSuccess) return GEVO_ERR_CUDA;
+    if (cudaMemsetAsync(tile_count, 0, sizeof(uint32_t) * T, st) != cudaSuccess) return GEVO_ERR_CUDA;
+    const size_t total = (size_t)layout->n_views * n;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)sm_count() * 8);
+    if (total > 0) {
+        k_count<<<std::max(grid, 1), 256, 0, st>>>(*layout, n,
+                                                   reinterpret_cast<const float2*>(proj->xy),
+                                                   proj->radius, tile_count);
+        GEVO_CHECK_LAUNCH();
+    }
+    k_scan<<<1, 1024, 0, st>>>(T, dup_capacity, tile_count, tile_start, tile_cursor, tile_order,
+                               ranges, d_n_dup, err);
+    GEVO_CHECK_LAUNCH();
+    if (total > 0 && dup_capacity > 0) {
+        k_scatter<<<std::max(grid, 1), 256, 0, st>>>(
+            *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
+            reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor, d_n_dup,
+            dup_capacity, bucket);
+        GEVO_CHECK_LAUNCH();
+        const size_t smem = sizeof(unsigned long long) * 2 * kSortSmemItems;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            attr = true;
+        }
+        k_segsort<<<T, kSortThreads, smem, st>>>(tile_order, tile_start, tile_count, d_n_dup,
+                                                 dup_capacity, bucket, bucket2,
+                                                 reinterpret_cast<unsigned long long*>(keys), vals);
+        GEVO_CHECK_LAUNCH();
+    }
+    return GEVO_OK;
+}
