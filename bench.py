@@ -36,7 +36,7 @@ WORKLOAD = "16 keyframe views (12x640x480 + 4x320x240), 500k Gaussians, SH degre
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--plain-steps", type=int, default=5)
@@ -70,7 +70,7 @@ class Clocks:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -149,6 +149,9 @@ def run_reference(args, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+FLOP_FWD, FLOP_BWD = 24, 71   # FP32 FLOPs per evaluated list entry (FMA = 2)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -205,10 +208,12 @@ def main():
     torch.cuda.synchronize()
     clocks.start()
     wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
     for k in range(args.steps):
         flush.zero_()                      # L2 flushed between timed steps
         rep.replay(evs[k])
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     wall1 = time.perf_counter()
     if world > 1:
         dist.barrier()
@@ -280,24 +285,43 @@ def main():
     plain_line = {"evals_per_s": (E_fwd + E_bwd) / (pms / 1e3), "views_per_s": V / (pms / 1e3),
                   "ms_per_step": pms}
 
-    # ---- roofline of the dominant stage ------------------------------------------------
+    # ---- rooflines (algorithmic work per launch / live event time) ---------------------
     pk = peaks()
-    dom = max(stage_ms, key=stage_ms.get)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk_peak = float(pk.get("sm_max_mhz", 2070.0))
     fp32_peak = sm_count * 128 * 2 * clk_peak * 1e6 / 1e12   # TFLOP/s, FMA = 2
-    FLOP_FWD, FLOP_BWD = 24, 71                 # per evaluated entry (design notes)
-    if dom == "render_bwd":
-        flops = FLOP_BWD * E_bwd
-    else:
-        flops = FLOP_FWD * E_fwd
-    achieved = flops / (stage_ms[dom] / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": {"render_bwd": "k_render_bwd",
-                                         "forward": "k_render_fwd (forward graph)",
-                                         "project_bwd": "k_project_bwd"}[dom],
-            "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
-            "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {clk_peak:.0f} MHz"}
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    N = int(g["means"].shape[0])
+    VN = V * N
+    vis = int((rep.pipe.proj["radius"] > 0).sum())
+    D = rep.n_dup
+    P = rep.pipe.P
+    K = (scene["sh_degree"] + 1) ** 2
+    param_b = 4 * (3 + 3 + 4 + 1 + 3 * K)
+    work = {  # (bound, algorithmic amount per launch, unit)
+        "project": ("hbm", param_b * N + 48 * vis + 8 * (VN - vis), "GB/s"),
+        "bin_sort": ("hbm", 24 * VN + 4 * vis + 28 * D + 16 * rep.pipe.T, "GB/s"),
+        "render_fwd": ("alu", FLOP_FWD * E_fwd, "TFLOP/s"),
+        "loss": ("hbm", 48 * P + 4 * VN + 40 * vis, "GB/s"),
+        "render_bwd": ("alu", FLOP_BWD * E_bwd, "TFLOP/s"),
+        "project_bwd": ("hbm", 2 * param_b * N + 4 * VN + 40 * vis, "GB/s"),
+    }
+    kernels = {"project": "k_project_fwd", "bin_sort": "k_count_smem+k_scan+k_scatter_smem+k_segsort",
+               "render_fwd": "k_render_fwd", "loss": "k_loss_l1+k_zero_grad2d",
+               "render_bwd": "k_render_bwd", "project_bwd": "k_project_bwd"}
+    roofs = {}
+    for name, (bound, amount, unit) in work.items():
+        sec = stage_ms[name] / 1e3
+        if bound == "alu":
+            ach, peak = amount / sec / 1e12, fp32_peak
+        else:
+            ach, peak = amount / sec / 1e9, hbm_peak
+        roofs[name] = {"bound": bound, "kernel": kernels[name], "achieved": ach, "peak": peak,
+                       "unit": unit, "frac": ach / peak, "ms": stage_ms[name]}
+    dom = "render_bwd"   # the largest share of the step (profiles/ launch list)
+    roof = dict(roofs[dom])
+    roof.update({"traffic": None,
+                 "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {clk_peak:.0f} MHz"})
 
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -308,8 +332,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed (256 MB write) between timed steps",
                        "tuning_fwd": rep.tuning_fwd, "tuning_bwd": rep.tuning_bwd,
-                       "graphs": "3 CUDA graphs per step"},
-            "views_per_s": views_per_s, "stage_ms": stage_ms,
+                       "graphs": "6 CUDA graphs per step (one per stage)"},
+            "views_per_s": views_per_s, "stage_ms": stage_ms, "rooflines": roofs,
             "plain": plain_line, "speedup_vs_plain": value / plain_line["evals_per_s"],
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -318,7 +342,7 @@ def main():
     line["gpu_launches"] = launches_per_step(rep) * args.steps
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, E, desc = oracle_sample()
+        dt, E, desc = oracle_sample(views=(0, 1, 2, 12, 13, 14))
         line["cpu_baseline"] = {"value": E / dt, "unit": "evals/s", "cores": 1, "kind": "oracle",
                                 "sample": desc + f", {dt:.1f} s"}
     if rank == 0:
@@ -329,9 +353,9 @@ def main():
 
 def launches_per_step(rep) -> int:
     """Kernels of ours launched per step: project (1), bin_sort (count, scan,
-    scatter, segsort = 4), render_fwd (1), loss (1), render_bwd (zero + walk = 2),
-    project_bwd (1)."""
-    return 1 + 4 + 1 + 1 + 2 + 1
+    scatter, segsort = 4), render_fwd (1), loss (1), grad2d_zero (1), render_bwd
+    (1), project_bwd (1)."""
+    return 1 + 4 + 1 + 1 + 1 + 1 + 1
 
 
 if __name__ == "__main__":

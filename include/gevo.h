@@ -256,14 +256,19 @@ gevo_status gevo_render_fwd(const gevo_layout* layout, int32_t n, const gevo_pro
  * pixel's list from n_contrib - 1 down to 0, recomputing alpha and recovering
  * T by T / (1 - alpha) from T_final; per-Gaussian sums are warp-reduced and
  * added with FP32 atomics (summation order is not deterministic).
- * out: rows of entries with radius > 0 are zeroed and then accumulated; rows
- * of culled entries are left untouched. */
+ * out: accumulated (+=) -- clear it first with gevo_grad2d_zero; rows of culled
+ * entries are never touched.  Launches exactly one kernel. */
 gevo_status gevo_render_bwd(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
                             const uint32_t* vals, const uint32_t* ranges, const float* bg,
                             const float* T_final, const uint32_t* n_contrib,
                             const float* dL_drgb, const float* dL_ddepth, const float* dL_dT,
                             gevo_grad2d* out, const gevo_tuning* tuning, void* workspace,
                             void* stream);
+
+/* Zeroes the rows of *out that belong to entries with radius > 0 (the only
+ * rows gevo_render_bwd accumulates into and gevo_project_bwd reads). */
+gevo_status gevo_grad2d_zero(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                             gevo_grad2d* out, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Stage a7: projection derivative incl. the se(3) pose gradient            */

@@ -69,7 +69,8 @@ class Tuning(ctypes.Structure):
 # Every symbol include/gevo.h declares (checked by the CPU test-suite).
 EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin_sort",
            "gevo_render_fwd", "gevo_render_bwd", "gevo_project_bwd", "gevo_loss_l1",
-           "gevo_last_error", "gevo_status_str", "gevo_version", "gevo_bin_sort_noalloc"]
+           "gevo_last_error", "gevo_status_str", "gevo_version", "gevo_bin_sort_noalloc",
+           "gevo_grad2d_zero"]
 
 _lib = None
 
@@ -104,6 +105,8 @@ def load(build_if_missing: bool = True):
                                   P(Tuning), vp, vp]
     L.gevo_render_bwd.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp, vp,
                                   P(Grad2d), P(Tuning), vp, vp]
+    L.gevo_grad2d_zero.argtypes = [P(Layout), i32, P(Proj), P(Grad2d), vp]
+    L.gevo_grad2d_zero.restype = ctypes.c_int
     L.gevo_project_bwd.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d),
                                    P(GaussianGrads), vp, vp, vp]
     L.gevo_loss_l1.argtypes = [P(Layout), vp, vp, vp, vp, f32, vp, vp, vp, vp, vp]
@@ -236,6 +239,14 @@ def gevo_render_bwd(layout, n, proj: dict, vals, ranges, bg, T_final, n_contrib,
         ctypes.byref(layout), int(n), ctypes.byref(P_), _p(vals), _p(ranges), bgv, _p(T_final),
         _p(n_contrib), _p(dL_drgb), _p(dL_ddepth), _p(dL_dT), ctypes.byref(G2),
         ctypes.byref(tu) if tu is not None else None, _p(ws), _stream(stream)))
+
+
+def gevo_grad2d_zero(layout, n, proj: dict, grad2d: dict, stream=None):
+    P_ = proj_struct(proj)
+    G2 = grad2d_struct(grad2d)
+    _check("gevo_grad2d_zero", load().gevo_grad2d_zero(ctypes.byref(layout), int(n),
+                                                       ctypes.byref(P_), ctypes.byref(G2),
+                                                       _stream(stream)))
 
 
 def gevo_project_bwd(layout, g: dict, cams, proj: dict, grad2d: dict, out: dict, dxi, ws,

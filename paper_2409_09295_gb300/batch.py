@@ -73,23 +73,38 @@ class BatchedReplay:
 
     # ---- stages with the chosen shapes ------------------------------------------------
     def _forward(self):
-        p = self.pipe
-        p.project(self.g, self.camt)
-        p.bin_sort()
-        p.render_fwd(self.bg, tuning=self.tuning_fwd)
-        p.loss_l1(self.target_rgb, self.target_depth, self.lambda_depth)
+        self._project()
+        self._bin_sort()
+        self._render_fwd()
+        self._loss()
+
+    def _project(self):
+        self.pipe.project(self.g, self.camt)
+
+    def _bin_sort(self):
+        self.pipe.bin_sort()
+
+    def _render_fwd(self):
+        self.pipe.render_fwd(self.bg, tuning=self.tuning_fwd)
+
+    def _loss(self):
+        self.pipe.loss_l1(self.target_rgb, self.target_depth, self.lambda_depth)
+        self.pipe.grad2d_zero()
 
     def _render_bwd(self):
         p = self.pipe
         p.render_bwd(p.dL_drgb, p.dL_ddepth if self.lambda_depth else None, None, self.bg,
-                     tuning=self.tuning_bwd)
+                     tuning=self.tuning_bwd, zero=False)
 
     def _project_bwd(self):
         self.pipe.project_bwd(self.g, self.camt, self.want_dxi)
 
     def stages(self):
-        return [("forward", self._forward), ("render_bwd", self._render_bwd),
-                ("project_bwd", self._project_bwd)]
+        """One step as six stages, each captured into its own graph so that every
+        stage can be timed with events between graph launches."""
+        return [("project", self._project), ("bin_sort", self._bin_sort),
+                ("render_fwd", self._render_fwd), ("loss", self._loss),
+                ("render_bwd", self._render_bwd), ("project_bwd", self._project_bwd)]
 
     def step_eager(self):
         for _, f in self.stages():
@@ -117,7 +132,7 @@ class BatchedReplay:
             best = None
             for c in CANDIDATES:
                 t = _time(lambda: p.render_bwd(p.dL_drgb, p.dL_ddepth if self.lambda_depth else None,
-                                               None, self.bg, tuning=c), reps)
+                                               None, self.bg, tuning=c, zero=False), reps)
                 self.tune_log.append(("render_bwd", c, t))
                 if best is None or t < best[0]:
                     best = (t, c)
@@ -126,8 +141,7 @@ class BatchedReplay:
 
     # ---- graphs ------------------------------------------------------------------------
     def capture(self):
-        """Captures each stage into its own CUDA graph (three graphs per step, so
-        a stage can be timed with events between graph launches)."""
+        """Captures each stage into its own CUDA graph."""
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):

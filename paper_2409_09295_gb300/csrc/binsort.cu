@@ -9,8 +9,9 @@
 //   3. k_scatter : each duplicate (depth bits << 32 | id) goes into its tile's
 //                  bucket (8 bytes written per duplicate);
 //   4. k_segsort : one block per tile sorts its bucket in shared memory (stable
-//                  LSD radix over the varying depth bytes, then equal depths by
-//                  id) and writes the final 64-bit keys and 32-bit values.
+//                  LSD radix over the varying depth bytes, each warp scattering
+//                  its own chunk, then equal depths by id) and writes the final
+//                  64-bit keys and 32-bit values.
 // The tile is handled by counting, so the sort only moves the depth half; the
 // result is the unique (tile, depth bits, id) order, identical to a full sort.
 #include "gevo_internal.cuh"
@@ -140,6 +141,120 @@ k_scatter(gevo_layout L, int n, const float2* __restrict__ xy, const int* __rest
     }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory binning: block (c, v) handles Gaussians [c*kBinChunk, ...) of
+// view v and keeps a histogram of view v's tiles in shared memory, so global
+// atomics drop from one per duplicate to one per (block, touched tile).
+// Rectangles wider than a warp are expanded by the whole warp (lane k takes
+// tiles k, k+32, ...), so one large splat does not serialise its warp.
+// ---------------------------------------------------------------------------
+constexpr int kBinThreads = 256;
+constexpr int kBinChunk = 2048;
+constexpr int kBinMaxSmemTiles = 16384;   // views with more tiles use k_count / k_scatter
+
+template <typename F>
+__device__ __forceinline__ void for_each_dup(const gevo_layout& L, int v, int n, int g0, int g1,
+                                             const float2* __restrict__ xy,
+                                             const int* __restrict__ radius, F&& f)
+{
+    // The duplicates of the warp's 32 Gaussians are laid end to end (warp
+    // prefix sum of the rectangle areas) and dealt out round-robin to the
+    // lanes, so every lane does the same amount of work whatever the sizes.
+    const int lane = threadIdx.x & 31;
+    const int tx = L.tiles_x[v], ty = L.tiles_y[v];
+    const size_t vb = (size_t)v * n;
+    for (int gs = g0 + (int)(threadIdx.x & ~31); gs < g1; gs += kBinThreads) {
+        const int g = gs + lane;
+        int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+        if (g < g1) {
+            const int r = radius[vb + g];
+            if (r > 0) {
+                const float2 m = xy[vb + g];
+                tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
+            }
+        }
+        const int w = x1 - x0;
+        const int area = w * (y1 - y0);
+        int incl = area;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = incl - area;
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            // owner lane: the last lane whose exclusive prefix is <= k
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int e = __shfl_sync(0xffffffffu, excl, src + step);
+                if (k >= e) src += step;
+            }
+            const int sx0 = __shfl_sync(0xffffffffu, x0, src);
+            const int sy0 = __shfl_sync(0xffffffffu, y0, src);
+            const int sw = __shfl_sync(0xffffffffu, w, src);
+            const int se = __shfl_sync(0xffffffffu, excl, src);
+            const int sg = __shfl_sync(0xffffffffu, g, src);
+            if (k < total) {
+                const int local = k - se;
+                const int yy = sy0 + local / sw, xx = sx0 + local % sw;
+                f(sg, yy * tx + xx);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+k_count_smem(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restrict__ radius,
+             uint32_t* __restrict__ tile_count)
+{
+    extern __shared__ uint32_t s_hist[];
+    const int v = blockIdx.y;
+    const int nt = L.tiles_x[v] * L.tiles_y[v];
+    for (int t = threadIdx.x; t < nt; t += kBinThreads) s_hist[t] = 0u;
+    __syncthreads();
+    const int g0 = blockIdx.x * kBinChunk, g1 = min(n, g0 + kBinChunk);
+    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int, int t) { atomicAdd(s_hist + t, 1u); });
+    __syncthreads();
+    uint32_t* dst = tile_count + L.tile_base[v];
+    for (int t = threadIdx.x; t < nt; t += kBinThreads) {
+        const uint32_t c = s_hist[t];
+        if (c) atomicAdd(dst + t, c);
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+k_scatter_smem(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restrict__ radius,
+               const float4* __restrict__ rgbz, const uint32_t* __restrict__ tile_start,
+               uint32_t* __restrict__ tile_cursor, const uint64_t* __restrict__ d_n_dup, uint64_t cap,
+               unsigned long long* __restrict__ bucket)
+{
+    extern __shared__ uint32_t s_hist[];
+    if (*d_n_dup > cap) return;
+    const int v = blockIdx.y;
+    const int nt = L.tiles_x[v] * L.tiles_y[v];
+    const int base = L.tile_base[v];
+    for (int t = threadIdx.x; t < nt; t += kBinThreads) s_hist[t] = 0u;
+    __syncthreads();
+    const int g0 = blockIdx.x * kBinChunk, g1 = min(n, g0 + kBinChunk);
+    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int, int t) { atomicAdd(s_hist + t, 1u); });
+    __syncthreads();
+    // reserve a contiguous run of each touched tile's bucket for this block
+    for (int t = threadIdx.x; t < nt; t += kBinThreads) {
+        const uint32_t c = s_hist[t];
+        if (c) s_hist[t] = tile_start[base + t] + atomicAdd(tile_cursor + base + t, c);
+    }
+    __syncthreads();
+    const size_t vb = (size_t)v * n;
+    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int g, int t) {
+        const uint32_t slot = atomicAdd(s_hist + t, 1u);
+        const uint32_t dbits = __float_as_uint(rgbz[vb + g].w);
+        bucket[slot] = ((unsigned long long)dbits << 32) | (uint32_t)g;
+    });
+}
+
 // Exclusive scan of 256 values held one per thread (blockDim == 256).
 __device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t* s_tmp)
 {
@@ -158,45 +273,44 @@ __device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t* s_tmp)
     return off + incl - v;
 }
 
-// One stable LSD pass over the byte of `a` at bit `shift`, a -> b.
+// One stable LSD pass over the byte of `a` at bit `shift`, a -> b.  Warp w owns
+// the contiguous chunk [w L/8, (w+1) L/8): it counts its digits, one block scan
+// turns the per-warp counts into per-warp digit offsets, then each warp scatters
+// its chunk in rounds of 32 with warp-synchronous ranking (match_any).  Order is
+// kept at every level (chunk, round, lane), so the pass is stable; the block
+// synchronises five times per pass whatever the tile's length.
 __device__ void radix_pass(const unsigned long long* a, unsigned long long* b, int L, int shift,
-                           uint32_t* s_base, uint32_t (*s_cnt)[256], uint32_t (*s_off)[256],
-                           uint32_t* s_tmp)
+                           uint32_t (*s_off)[256], uint32_t* s_tmp)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    s_base[tid] = 0;
+    const int chunk = (L + kSortWarps - 1) / kSortWarps;
+    const int lo = min(L, warp * chunk), hi = min(L, lo + chunk);
+    for (int d = lane; d < 256; d += 32) s_off[warp][d] = 0u;
+    __syncwarp();
+    for (int i = lo + lane; i < hi; i += 32) atomicAdd(&s_off[warp][(a[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    uint32_t tot = 0;
 #pragma unroll
-    for (int w = 0; w < kSortWarps; w++) s_cnt[w][tid] = 0;
-    __syncthreads();
-    for (int i = tid; i < L; i += kSortThreads) atomicAdd(&s_base[(a[i] >> shift) & 255u], 1u);
-    __syncthreads();
-    const uint32_t h = s_base[tid];
-    const uint32_t ex = block_exscan256(h, s_tmp);
-    s_base[tid] = ex;
+    for (int w = 0; w < kSortWarps; w++) tot += s_off[w][tid];
+    uint32_t run = block_exscan256(tot, s_tmp);
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) {
+        const uint32_t c = s_off[w][tid];
+        s_off[w][tid] = run;
+        run += c;
+    }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
-    for (int r = 0; r < L; r += kSortThreads) {
-        const int i = r + tid;
-        const bool valid = i < L;
+    for (int r = lo; r < hi; r += 32) {
+        const int i = r + lane;
+        const bool valid = i < hi;
         const unsigned long long key = valid ? a[i] : 0ull;
         const uint32_t dg = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t rank = __popc(peers & lt);
-        if (valid && (__ffs(peers) - 1) == lane) s_cnt[warp][dg] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t run = s_base[tid];
-#pragma unroll
-            for (int w = 0; w < kSortWarps; w++) {
-                const uint32_t c = s_cnt[w][tid];
-                s_off[w][tid] = run;
-                run += c;
-                s_cnt[w][tid] = 0;
-            }
-            s_base[tid] = run;
-        }
-        __syncthreads();
-        if (valid) b[s_off[warp][dg] + rank] = key;
+        if (valid) b[s_off[warp][dg] + __popc(peers & lt)] = key;
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) s_off[warp][dg] += __popc(peers);
+        __syncwarp();
     }
     __syncthreads();
 }
@@ -209,8 +323,6 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
           uint32_t* __restrict__ vals_out)
 {
     extern __shared__ unsigned long long s_items[];   // 2 * kSortSmemItems
-    __shared__ uint32_t s_base[256];
-    __shared__ uint32_t s_cnt[kSortWarps][256];
     __shared__ uint32_t s_off[kSortWarps][256];
     __shared__ uint32_t s_tmp[kSortWarps];
     __shared__ uint32_t s_or[kSortWarps], s_and[kSortWarps];
@@ -254,7 +366,7 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
     if (L > 1) {
         for (int d = 0; d < 4; d++) {
             if (((vary >> (8 * d)) & 255u) == 0u) continue;
-            radix_pass(a, b, L, 32 + 8 * d, s_base, s_cnt, s_off, s_tmp);
+            radix_pass(a, b, L, 32 + 8 * d, s_off, s_tmp);
             unsigned long long* t = a;
             a = b;
             b = t;
@@ -281,6 +393,16 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
         const unsigned long long k = a[i];
         keys_out[s0 + i] = th | (k >> 32);
         vals_out[s0 + i] = (uint32_t)k;
+    }
+}
+
+static void bin_attributes(size_t bin_smem)
+{
+    static size_t done = 0;
+    if (bin_smem > 48 * 1024 && bin_smem > done) {
+        cudaFuncSetAttribute(k_count_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
+        cudaFuncSetAttribute(k_scatter_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
+        done = bin_smem;
     }
 }
 
@@ -313,20 +435,37 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
     const size_t total = (size_t)layout->n_views * n;
     const int sms = sm_count();
     const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)sms * 8);
+    int max_tiles = 0;
+    for (int v = 0; v < layout->n_views; v++)
+        max_tiles = std::max(max_tiles, layout->tiles_x[v] * layout->tiles_y[v]);
+    const bool smem_bins = max_tiles <= kBinMaxSmemTiles;
+    const dim3 bin_grid((n + kBinChunk - 1) / kBinChunk, layout->n_views);
+    const size_t bin_smem = sizeof(uint32_t) * (size_t)max_tiles;
+    if (smem_bins) bin_attributes(bin_smem);
     if (total > 0) {
-        k_count<<<std::max(grid, 1), 256, 0, st>>>(*layout, n,
-                                                   reinterpret_cast<const float2*>(proj->xy),
-                                                   proj->radius, tile_count);
+        if (smem_bins)
+            k_count_smem<<<bin_grid, kBinThreads, bin_smem, st>>>(
+                *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius, tile_count);
+        else
+            k_count<<<std::max(grid, 1), 256, 0, st>>>(*layout, n,
+                                                       reinterpret_cast<const float2*>(proj->xy),
+                                                       proj->radius, tile_count);
         GEVO_CHECK_LAUNCH();
     }
     k_scan<<<1, 1024, 0, st>>>(T, dup_capacity, tile_count, tile_start, tile_cursor, tile_order,
                                ranges, d_n_dup, err);
     GEVO_CHECK_LAUNCH();
     if (total > 0 && dup_capacity > 0) {
-        k_scatter<<<std::max(grid, 1), 256, 0, st>>>(
-            *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
-            reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor, d_n_dup,
-            dup_capacity, bucket);
+        if (smem_bins)
+            k_scatter_smem<<<bin_grid, kBinThreads, bin_smem, st>>>(
+                *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
+                reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor,
+                d_n_dup, dup_capacity, bucket);
+        else
+            k_scatter<<<std::max(grid, 1), 256, 0, st>>>(
+                *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
+                reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor, d_n_dup,
+                dup_capacity, bucket);
         GEVO_CHECK_LAUNCH();
         const size_t smem = sizeof(unsigned long long) * 2 * kSortSmemItems;
         static bool attr = false;
@@ -402,20 +541,37 @@ extern "C" gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t 
     if (cudaMemsetAsync(tile_count, 0, sizeof(uint32_t) * T, st) != cudaSuccess) return GEVO_ERR_CUDA;
     const size_t total = (size_t)layout->n_views * n;
     const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)sm_count() * 8);
+    int max_tiles = 0;
+    for (int v = 0; v < layout->n_views; v++)
+        max_tiles = std::max(max_tiles, layout->tiles_x[v] * layout->tiles_y[v]);
+    const bool smem_bins = max_tiles <= kBinMaxSmemTiles;
+    const dim3 bin_grid((n + kBinChunk - 1) / kBinChunk, layout->n_views);
+    const size_t bin_smem = sizeof(uint32_t) * (size_t)max_tiles;
+    if (smem_bins) bin_attributes(bin_smem);
     if (total > 0) {
-        k_count<<<std::max(grid, 1), 256, 0, st>>>(*layout, n,
-                                                   reinterpret_cast<const float2*>(proj->xy),
-                                                   proj->radius, tile_count);
+        if (smem_bins)
+            k_count_smem<<<bin_grid, kBinThreads, bin_smem, st>>>(
+                *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius, tile_count);
+        else
+            k_count<<<std::max(grid, 1), 256, 0, st>>>(*layout, n,
+                                                       reinterpret_cast<const float2*>(proj->xy),
+                                                       proj->radius, tile_count);
         GEVO_CHECK_LAUNCH();
     }
     k_scan<<<1, 1024, 0, st>>>(T, dup_capacity, tile_count, tile_start, tile_cursor, tile_order,
                                ranges, d_n_dup, err);
     GEVO_CHECK_LAUNCH();
     if (total > 0 && dup_capacity > 0) {
-        k_scatter<<<std::max(grid, 1), 256, 0, st>>>(
-            *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
-            reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor, d_n_dup,
-            dup_capacity, bucket);
+        if (smem_bins)
+            k_scatter_smem<<<bin_grid, kBinThreads, bin_smem, st>>>(
+                *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
+                reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor,
+                d_n_dup, dup_capacity, bucket);
+        else
+            k_scatter<<<std::max(grid, 1), 256, 0, st>>>(
+                *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
+                reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor, d_n_dup,
+                dup_capacity, bucket);
         GEVO_CHECK_LAUNCH();
         const size_t smem = sizeof(unsigned long long) * 2 * kSortSmemItems;
         static bool attr = false;

@@ -34,6 +34,34 @@ __device__ __forceinline__ float4 prescale(float4 co)
     return make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, co.w);
 }
 
+// Pixel box outside which alpha = o exp(-d^T Q d / 2) < 1/255 for certain:
+// the ellipse d^T Q d <= 2 ln(255 o) has half-extents sqrt(k2 Sigma_xx) and
+// sqrt(k2 Sigma_yy), Sigma = Q^-1.  det(Q) uses Kahan's fused 2x2 determinant
+// so elongated splats keep full precision; the box is widened by 0.1% + 1 px,
+// far more than the binary32 error of the per-pixel test near its threshold.
+// Returns (xmin, xmax, ymin, ymax); an empty box if o < 1/255.
+__device__ __forceinline__ float4 alpha_box(float2 m, float4 co)
+{
+    // alpha <= o everywhere: o < 1/255 (with a margin for __logf) can never blend
+    const float lg = __logf(255.f * co.w);
+    if (!(lg > -1e-4f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);
+    const float k2 = 2.f * fmaxf(lg, 0.f) + 2e-4f;
+    const float w = co.y * co.y;
+    const float e = __fmaf_rn(-co.y, co.y, w);
+    const float det = __fmaf_rn(co.x, co.z, -w) + e;
+    const float sxx = co.z / det, syy = co.x / det;
+    const float hx = sqrtf(k2 * sxx) * 1.001f + 1.f;
+    const float hy = sqrtf(k2 * syy) * 1.001f + 1.f;
+    if (!(det > 0.f) || !(hx < 1e30f) || !(hy < 1e30f))
+        return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);   // degenerate: never cull
+    return make_float4(m.x - hx, m.x + hx, m.y - hy, m.y + hy);
+}
+
+__device__ __forceinline__ bool box_misses(float4 box, float wx0, float wx1, float wy0, float wy1)
+{
+    return box.y < wx0 || box.x > wx1 || box.w < wy0 || box.z > wy1;
+}
+
 // log2 of the Gaussian falloff at offset (dx, dy); identical in both passes.
 __device__ __forceinline__ float power2_at(const float4& co, float dx, float dy)
 {
@@ -52,7 +80,7 @@ __device__ __forceinline__ void tile_of(const gevo_layout& L, int tile, int& v, 
     y0 = (local / tx) * kTile;
 }
 
-template <int PPT>
+template <int PPT, bool COUNT>
 __global__ void __launch_bounds__(256 / PPT)
 k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
              const float4* __restrict__ rz, const uint32_t* __restrict__ vals,
@@ -65,8 +93,11 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     __shared__ float2 s_xy[kBatch];
     __shared__ float4 s_co[kBatch];
     __shared__ float4 s_rz[kBatch];
+    __shared__ float4 s_box[kBatch];
     __shared__ uint32_t s_item;
     const int tid = threadIdx.x;
+    const int wrow0 = ((tid & ~31) >> 4) * PPT;   // first tile row of this warp
+    constexpr int WROWS = 2 * PPT;
 
     for (int it = 0;; it++) {
         int item;
@@ -109,38 +140,59 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
             const int nb = (int)min((uint32_t)kBatch, rg.y - b);
             for (int j = tid; j < nb; j += NT) {
                 const size_t id = vbase + vals[b + j];
-                s_xy[j] = xy[id];
-                s_co[j] = prescale(co[id]);
+                const float2 m = xy[id];
+                const float4 c = co[id];
+                s_xy[j] = m;
+                s_co[j] = prescale(c);
                 s_rz[j] = rz[id];
+                s_box[j] = alpha_box(m, c);
             }
             __syncthreads();
+            const float wx0 = (float)x0, wx1 = (float)(x0 + kTile - 1);
+            const float wy0 = (float)(y0 + wrow0), wy1 = (float)(y0 + wrow0 + WROWS - 1);
             for (int j = 0; j < nb; j++) {
                 bool all = true;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) all = all && done[k];
                 if (all) break;
+                if (box_misses(s_box[j], wx0, wx1, wy0, wy1)) {
+                    if (COUNT) {
+#pragma unroll
+                        for (int k = 0; k < PPT; k++) cnt[k] += done[k] ? 0u : 1u;
+                    }
+                    continue;
+                }
                 const float2 m = s_xy[j];
                 const float4 c = s_co[j];
+                const float4 r = s_rz[j];
                 const float dx = __fsub_rn(m.x, fpx);
+                const uint32_t pos1 = b + j - rg.x + 1;
+                // the PPT pixels are independent: evaluate them branch-free so
+                // their dependency chains interleave
+                float p2[PPT], G[PPT];
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    if (done[k]) continue;
-                    cnt[k]++;
                     const float dy = __fsub_rn(m.y, (float)(py0 + k));
-                    const float p2 = power2_at(c, dx, dy);
-                    if (p2 > 0.f) continue;
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, ex2_approx(p2)));
-                    if (alpha < kAlphaMin) continue;
+                    p2[k] = power2_at(c, dx, dy);
+                }
+#pragma unroll
+                for (int k = 0; k < PPT; k++) G[k] = ex2_approx(p2[k]);
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    if (COUNT) cnt[k] += done[k] ? 0u : 1u;
+                    const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, G[k]));
+                    const bool ok = !done[k] && !(p2[k] > 0.f) && !(alpha < kAlphaMin);
                     const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
-                    if (Tn < kTStop) { done[k] = true; continue; }
-                    const float4 r = s_rz[j];
-                    const float w = __fmul_rn(alpha, T[k]);
+                    const bool stop = ok && Tn < kTStop;
+                    const bool bl = ok && !stop;
+                    done[k] = done[k] || stop;
+                    const float w = bl ? __fmul_rn(alpha, T[k]) : 0.f;
                     C0[k] = __fmaf_rn(w, r.x, C0[k]);
                     C1[k] = __fmaf_rn(w, r.y, C1[k]);
                     C2[k] = __fmaf_rn(w, r.z, C2[k]);
                     Dp[k] = __fmaf_rn(w, r.w, Dp[k]);
-                    T[k] = Tn;
-                    last[k] = b + j - rg.x + 1;
+                    T[k] = bl ? Tn : T[k];
+                    last[k] = bl ? pos1 : last[k];
                 }
             }
         }
@@ -157,7 +209,7 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 out_d[gp] = Dp[k];
                 out_T[gp] = T[k];
                 out_nc[gp] = last[k];
-                if (out_ne) out_ne[gp] = cnt[k];
+                if (COUNT) out_ne[gp] = cnt[k];
             }
         }
     }
@@ -177,14 +229,48 @@ __global__ void k_zero_grad2d(size_t total, const int* __restrict__ radius, floa
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v)
+// Sums ten per-lane values over the warp by recursive halving: at each of the
+// five butterfly levels a lane keeps half of its partial sums and sends the
+// other half, so 12 shuffles replace 50.  Afterwards the even lanes with
+// `slot` in 0..9 hold the total of value `slot`; other lanes get slot = -1.
+__device__ __forceinline__ float warp_reduce10(const float v[10], int& slot)
 {
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+    float r[6];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int i = 0; i < 5; i++) {
+        const float keep = h16 ? v[5 + i] : v[i];
+        const float send = h16 ? v[i] : v[5 + i];
+        r[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    r[5] = 0.f;
+    float q[4];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float keep = h8 ? r[3 + i] : r[i];
+        const float send = h8 ? r[i] : r[3 + i];
+        q[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    q[3] = 0.f;
+    float u[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float keep = h4 ? q[2 + i] : q[i];
+        const float send = h4 ? q[i] : q[2 + i];
+        u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const float keep = h2 ? u[1] : u[0];
+    const float send = h2 ? u[0] : u[1];
+    float x = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    const int local = (h4 ? 2 : 0) + (h2 ? 1 : 0);
+    const bool valid = !(lane & 1) && (h8 ? local < 2 : local < 3);
+    slot = valid ? (h16 ? 5 : 0) + (h8 ? 3 : 0) + local : -1;
+    return x;
 }
 
-template <int PPT>
+template <int PPT, bool DD, bool DT>
 __global__ void __launch_bounds__(256 / PPT)
 k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
              const float4* __restrict__ rz, const uint32_t* __restrict__ vals,
@@ -200,11 +286,15 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     __shared__ float2 s_xy[kBatch];
     __shared__ float4 s_co[kBatch];
     __shared__ float4 s_rz[kBatch];
+    __shared__ float4 s_box[kBatch];
     __shared__ uint32_t s_id[kBatch];
     __shared__ float s_g[kBatch][10];
     __shared__ uint32_t s_item;
     __shared__ uint32_t s_max[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wrow0 = ((tid & ~31) >> 4) * PPT;
+    constexpr int WROWS = 2 * PPT;
+    (void)lane;
 
     for (int it = 0;; it++) {
         int item;
@@ -244,8 +334,8 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 T[k] = T_final[gp];
                 last[k] = n_contrib[gp];
                 gC0[k] = g3[pix]; gC1[k] = g3[P + pix]; gC2[k] = g3[2 * P + pix];
-                gD[k] = dL_dd ? dL_dd[gp] : 0.f;
-                gTT[k] = dL_dT ? dL_dT[gp] * T[k] : 0.f;
+                gD[k] = DD ? dL_dd[gp] : 0.f;
+                gTT[k] = DT ? dL_dT[gp] * T[k] : 0.f;
             } else {
                 T[k] = 1.f; last[k] = 0u;
                 gC0[k] = gC1[k] = gC2[k] = gD[k] = gTT[k] = 0.f;
@@ -268,71 +358,83 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
             for (int j = tid; j < nb; j += NT) {
                 const uint32_t id = vals[bstart + j];
                 const size_t gid = vbase + id;
+                const float2 m = xy[gid];
+                const float4 c = co[gid];
                 s_id[j] = id;
-                s_xy[j] = xy[gid];
-                s_co[j] = prescale(co[gid]);
+                s_xy[j] = m;
+                s_co[j] = prescale(c);
                 s_rz[j] = rz[gid];
+                s_box[j] = alpha_box(m, c);
 #pragma unroll
                 for (int q = 0; q < 10; q++) s_g[j][q] = 0.f;
             }
             __syncthreads();
+            const float wx0 = (float)x0, wx1 = (float)(x0 + kTile - 1);
+            const float wy0 = (float)(y0 + wrow0), wy1 = (float)(y0 + wrow0 + WROWS - 1);
             for (int j = nb - 1; j >= 0; j--) {
+                if (box_misses(s_box[j], wx0, wx1, wy0, wy1)) continue;
                 const uint32_t pos = bstart + j - rg.x;   // list position
                 const float2 m = s_xy[j];
                 const float4 c = s_co[j];
-                const float4 r = s_rz[j];
                 const float dx = __fsub_rn(m.x, fpx);
-                float a_xy0 = 0.f, a_xy1 = 0.f, a_ca = 0.f, a_cb = 0.f, a_cc = 0.f, a_o = 0.f;
-                float a_r = 0.f, a_g = 0.f, a_b = 0.f, a_z = 0.f;
+                float p2[PPT], G[PPT], dyk[PPT];
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    dyk[k] = __fsub_rn(m.y, (float)(py0 + k));
+                    p2[k] = power2_at(c, dx, dyk[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < PPT; k++) G[k] = ex2_approx(p2[k]);
+                float al[PPT];
+                bool use[PPT];
                 bool any = false;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    if (pos >= last[k]) continue;
-                    const float dy = __fsub_rn(m.y, (float)(py0 + k));
-                    const float p2 = power2_at(c, dx, dy);
-                    if (p2 > 0.f) continue;
-                    const float G = ex2_approx(p2);
-                    const float og = __fmul_rn(c.w, G);
-                    const float alpha = fminf(kAlphaMax, og);
-                    if (alpha < kAlphaMin) continue;
-                    any = true;
+                    al[k] = fminf(kAlphaMax, __fmul_rn(c.w, G[k]));
+                    use[k] = pos < last[k] && !(p2[k] > 0.f) && !(al[k] < kAlphaMin);
+                    any = any || use[k];
+                }
+                if (!__any_sync(0xffffffffu, any)) continue;
+                const float4 r = s_rz[j];
+                float a_xy0 = 0.f, a_xy1 = 0.f, a_ca = 0.f, a_cb = 0.f, a_cc = 0.f, a_o = 0.f;
+                float a_r = 0.f, a_g = 0.f, a_b = 0.f, a_z = 0.f;
+#pragma unroll
+                for (int k = 0; k < PPT; k++) {
+                    if (!use[k]) continue;
+                    const float alpha = al[k];
+                    const float dy = dyk[k];
                     const float om = 1.f - alpha;
-                    const float inv = 1.f / om;
+                    const float inv = __frcp_rn(om);
                     const float Ti = T[k] * inv;
                     T[k] = Ti;
                     const float w = alpha * Ti;
                     float dLda = gC0[k] * (r.x - S0[k]) + gC1[k] * (r.y - S1[k]) +
-                                 gC2[k] * (r.z - S2[k]) + gD[k] * (r.w - SD[k]);
-                    dLda = dLda * Ti - gTT[k] * inv;
+                                 gC2[k] * (r.z - S2[k]);
+                    if (DD) dLda += gD[k] * (r.w - SD[k]);
+                    dLda = dLda * Ti;
+                    if (DT) dLda -= gTT[k] * inv;
                     S0[k] = alpha * r.x + om * S0[k];
                     S1[k] = alpha * r.y + om * S1[k];
                     S2[k] = alpha * r.z + om * S2[k];
-                    SD[k] = alpha * r.w + om * SD[k];
-                    a_r += gC0[k] * w; a_g += gC1[k] * w; a_b += gC2[k] * w; a_z += gD[k] * w;
-                    if (og <= kAlphaMax) {
-                        a_o += dLda * G;
+                    if (DD) SD[k] = alpha * r.w + om * SD[k];
+                    a_r += gC0[k] * w; a_g += gC1[k] * w; a_b += gC2[k] * w;
+                    if (DD) a_z += gD[k] * w;
+                    if (__fmul_rn(c.w, G[k]) <= kAlphaMax) {
+                        a_o += dLda * G[k];
                         const float dp = dLda * alpha;
                         a_ca += -0.5f * dx * dx * dp;
                         a_cb += -dx * dy * dp;
                         a_cc += -0.5f * dy * dy * dp;
-                        const float s = dp * kLn2;
-                        a_xy0 += s * (2.f * c.x * dx + c.y * dy);
-                        a_xy1 += s * (2.f * c.z * dy + c.y * dx);
+                        const float sc = dp * kLn2;
+                        a_xy0 += sc * (2.f * c.x * dx + c.y * dy);
+                        a_xy1 += sc * (2.f * c.z * dy + c.y * dx);
                     }
                 }
-                if (__any_sync(0xffffffffu, any)) {
-                    a_xy0 = warp_sum(a_xy0); a_xy1 = warp_sum(a_xy1);
-                    a_ca = warp_sum(a_ca); a_cb = warp_sum(a_cb); a_cc = warp_sum(a_cc);
-                    a_o = warp_sum(a_o);
-                    a_r = warp_sum(a_r); a_g = warp_sum(a_g); a_b = warp_sum(a_b); a_z = warp_sum(a_z);
-                    if (lane == 0) {
-                        float* gg = s_g[j];
-                        atomicAdd(gg + 0, a_xy0); atomicAdd(gg + 1, a_xy1);
-                        atomicAdd(gg + 2, a_ca); atomicAdd(gg + 3, a_cb); atomicAdd(gg + 4, a_cc);
-                        atomicAdd(gg + 5, a_o);
-                        atomicAdd(gg + 6, a_r); atomicAdd(gg + 7, a_g); atomicAdd(gg + 8, a_b);
-                        atomicAdd(gg + 9, a_z);
-                    }
+                {
+                    const float vals10[10] = {a_xy0, a_xy1, a_ca, a_cb, a_cc, a_o, a_r, a_g, a_b, a_z};
+                    int slot;
+                    const float tot = warp_reduce10(vals10, slot);
+                    if (slot >= 0 && tot != 0.f) atomicAdd(&s_g[j][slot], tot);
                 }
             }
             __syncthreads();
@@ -382,9 +484,10 @@ static gevo_status launch_fwd(const gevo_layout& L, int n, const gevo_proj& p, c
     if (t && t->persistent) {
         queue = reinterpret_cast<uint32_t*>(ws + w.err) + kQueueFwd;
         if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GEVO_ERR_CUDA;
-        grid = std::min(grid, persistent_grid<PPT>(k_render_fwd<PPT>, t));
+        grid = std::min(grid, persistent_grid<PPT>(k_render_fwd<PPT, false>, t));
     }
-    k_render_fwd<PPT><<<grid, 256 / PPT, 0, st>>>(
+    auto kern = ne ? k_render_fwd<PPT, true> : k_render_fwd<PPT, false>;
+    kern<<<grid, 256 / PPT, 0, st>>>(
         L, n, reinterpret_cast<const float2*>(p.xy), reinterpret_cast<const float4*>(p.conic_opacity),
         reinterpret_cast<const float4*>(p.rgb_depth), vals, reinterpret_cast<const uint2*>(ranges),
         bg[0], bg[1], bg[2], rgb, depth, Tf, nc, ne, order, queue, L.total_tiles);
@@ -406,9 +509,11 @@ static gevo_status launch_bwd(const gevo_layout& L, int n, const gevo_proj& p, c
     if (t && t->persistent) {
         queue = reinterpret_cast<uint32_t*>(ws + w.err) + kQueueBwd;
         if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GEVO_ERR_CUDA;
-        grid = std::min(grid, persistent_grid<PPT>(k_render_bwd<PPT>, t));
+        grid = std::min(grid, persistent_grid<PPT>(k_render_bwd<PPT, true, false>, t));
     }
-    k_render_bwd<PPT><<<grid, 256 / PPT, 0, st>>>(
+    auto kern = gD ? (gT ? k_render_bwd<PPT, true, true> : k_render_bwd<PPT, true, false>)
+                   : (gT ? k_render_bwd<PPT, false, true> : k_render_bwd<PPT, false, false>);
+    kern<<<grid, 256 / PPT, 0, st>>>(
         L, n, reinterpret_cast<const float2*>(p.xy), reinterpret_cast<const float4*>(p.conic_opacity),
         reinterpret_cast<const float4*>(p.rgb_depth), vals, reinterpret_cast<const uint2*>(ranges),
         bg[0], bg[1], bg[2], Tf, nc, gC, gD, gT, reinterpret_cast<float2*>(out.xy),
@@ -468,17 +573,27 @@ extern "C" gevo_status gevo_render_bwd(const gevo_layout* layout, int32_t n, con
         return GEVO_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = reinterpret_cast<char*>(workspace);
-    const size_t total = (size_t)layout->n_views * n;
-    if (total > 0) {
-        const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)sm_count() * 16);
-        k_zero_grad2d<<<grid, 256, 0, st>>>(total, proj->radius, reinterpret_cast<float2*>(out->xy),
-                                            reinterpret_cast<float4*>(out->conic_opacity),
-                                            reinterpret_cast<float4*>(out->rgb_depth));
-        GEVO_CHECK_LAUNCH();
-    }
     switch (pick_ppt(tuning)) {
     case 4: return launch_bwd<4>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
     case 2: return launch_bwd<2>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
     default: return launch_bwd<1>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
     }
+}
+
+extern "C" gevo_status gevo_grad2d_zero(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                                        gevo_grad2d* out, void* stream)
+{
+    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->radius || !out || !out->xy ||
+        !out->conic_opacity || !out->rgb_depth || !gevo_aligned(out->conic_opacity, 16) ||
+        !gevo_aligned(out->rgb_depth, 16) || !gevo_aligned(out->xy, 8))
+        return GEVO_ERR_INVALID;
+    const size_t total = (size_t)layout->n_views * n;
+    if (total == 0) return GEVO_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = (int)std::min<size_t>((total + 255) / 256, (size_t)sm_count() * 16);
+    k_zero_grad2d<<<grid, 256, 0, st>>>(total, proj->radius, reinterpret_cast<float2*>(out->xy),
+                                        reinterpret_cast<float4*>(out->conic_opacity),
+                                        reinterpret_cast<float4*>(out->rgb_depth));
+    GEVO_CHECK_LAUNCH();
+    return GEVO_OK;
 }

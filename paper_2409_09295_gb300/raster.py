@@ -128,7 +128,14 @@ class Pipeline:
                          target_depth if lambda_depth else None, lambda_depth, self.dL_drgb,
                          self.dL_ddepth if lambda_depth else None, self.loss, self.ws)
 
-    def render_bwd(self, dL_drgb, dL_ddepth=None, dL_dT=None, bg=(0.0, 0.0, 0.0), tuning=None):
+    def grad2d_zero(self):
+        abi.gevo_grad2d_zero(self.layout, self.n, self.proj, self.grad2d)
+
+    def render_bwd(self, dL_drgb, dL_ddepth=None, dL_dT=None, bg=(0.0, 0.0, 0.0), tuning=None,
+                   zero=True):
+        """Record gradients; zero=False accumulates into the existing rows."""
+        if zero:
+            self.grad2d_zero()
         abi.gevo_render_bwd(self.layout, self.n, self.proj, self.vals, self.ranges, bg,
                             self.T_final, self.n_contrib, dL_drgb, dL_ddepth, dL_dT, self.grad2d,
                             self.ws, tuning or self.tuning)

@@ -192,12 +192,13 @@ def tracking_subscene(n: int = 2000, seed: int = 1003):
 # Synthetic 2-D records for stage-isolated tests (binning, blending).
 # ---------------------------------------------------------------------------
 def random_records(sizes, n: int, seed: int, frac_culled: float = 0.1,
-                   sigma_px=(0.5, 30.0)):
+                   sigma_px=(0.5, 30.0), opacity=(0.02, 1.0)):
     """Per (view, Gaussian) 2-D records drawn directly (not projected):
     xy float32 [V,N,2] (may lie off-screen), conic float32 [V,N,3] of a random
     positive-definite ellipse with axes sigma in `sigma_px`, opacity [N],
     rgb [V,N,3], depth float32 [V,N] in (0.5, 10), radius int32 [V,N] = a
-    3-sigma bound on the longer axis, 0 for a random `frac_culled` share."""
+    3-sigma bound on the longer axis, 0 for a random `frac_culled` share,
+    opacity uniform in `opacity`."""
     r = rng(seed)
     V = len(sizes)
     xy = np.zeros((V, n, 2), np.float32)
@@ -220,5 +221,5 @@ def random_records(sizes, n: int, seed: int, frac_culled: float = 0.1,
         radius[v] = np.ceil(3.0 * np.maximum(s1, s2)).astype(np.int32) + 1
         radius[v][r.uniform(size=n) < frac_culled] = 0
         rgb[v] = r.uniform(0.0, 1.0, (n, 3))
-    opac = r.uniform(0.02, 1.0, n).astype(np.float32)
+    opac = r.uniform(opacity[0], opacity[1], n).astype(np.float32)
     return dict(xy=xy, conic=conic, depth=depth, radius=radius, rgb=rgb, opacity=opac)

@@ -104,8 +104,8 @@ def test_bin_sort_overflow_sets_error_and_reports_true_count():
 # --------------------------------------------------------------------------
 # a5 / a6 on identical binary32 records
 # --------------------------------------------------------------------------
-def _staged(sizes, n, seed, sigma_px=(0.5, 12.0)):
-    rec = scenes.random_records(sizes, n, seed=seed, sigma_px=sigma_px)
+def _staged(sizes, n, seed, sigma_px=(0.5, 12.0), opacity=(0.02, 1.0)):
+    rec = scenes.random_records(sizes, n, seed=seed, sigma_px=sigma_px, opacity=opacity)
     ref_bins = oracle.bin_f32(sizes, rec["xy"], rec["radius"], rec["depth"])
     pipe = raster.Pipeline(n, sizes, ref_bins["n_dup"] + 16)
     upload_records(pipe, rec)
@@ -132,6 +132,30 @@ def test_render_fwd_staged_1e5(tuning):
         np.testing.assert_allclose(_np(pipe.view_plane(pipe.T_final, v))[ok], o["T"][ok], atol=1e-5, rtol=0)
         np.testing.assert_array_equal(_np(pipe.view_plane(pipe.n_contrib, v))[ok], o["n_contrib"][ok])
         np.testing.assert_array_equal(_np(pipe.view_plane(pipe.n_eval, v))[ok], o["n_eval"][ok])
+
+
+def test_render_fwd_faint_and_huge_splats():
+    """Opacities down to 0.001 (below the 1/255 skip level everywhere) and
+    splats up to ~800 px across: the per-warp culling box must never drop an
+    entry the per-pixel test would blend.  Decisions (n_contrib, n_eval) must
+    match exactly; a dropped entry would also move T by at least alpha >= 1/255
+    relative, while binary32 accumulation over m blended entries moves it by
+    about m * 4e-7 in T and m * 1e-6 in colour (the colour tolerance)."""
+    sizes = [(160, 96)]
+    rec, b, pipe = _staged(sizes, 1500, seed=53, sigma_px=(0.3, 120.0), opacity=(0.001, 1.0))
+    pipe.render_fwd((0.0, 0.0, 0.0), n_eval=True)
+    torch.cuda.synchronize()
+    o = oracle.render_fwd(160, 96, records_for_oracle(rec, 0), b["vals"], b["ranges"], (0, 0, 0))
+    ok = o["fragile"] == 0
+    assert ok.mean() > 0.95
+    np.testing.assert_array_equal(_np(pipe.view_plane(pipe.n_contrib, 0))[ok], o["n_contrib"][ok])
+    np.testing.assert_array_equal(_np(pipe.view_plane(pipe.n_eval, 0))[ok], o["n_eval"][ok])
+    T = _np(pipe.view_plane(pipe.T_final, 0))
+    rel = np.abs(T / o["T"] - 1.0)[ok]
+    assert rel.max() <= 2e-3, rel.max()
+    tol = 1e-5 + 1e-6 * o["n_contrib"]
+    err = np.abs(_np(pipe.view_rgb(pipe.rgb, 0)) - o["rgb"]).max(0)
+    assert (err[ok] <= tol[ok]).all(), (err[ok] / tol[ok]).max()
 
 
 def test_render_tunings_bitwise_identical():
