@@ -32,7 +32,9 @@
  *  - Conditions only the device can see (duplicate count above capacity)
  *    set a sticky error word in the workspace; outputs that depend on them are
  *    then defined as stated per call.  gevo_last_error() reads and clears it.
- *  - No kernel waits on another kernel or block: there are no spin-waits.
+ *  - No kernel waits on another kernel or block.  The only device-side wait is
+ *    the tensor-core GEMM's wait for its own MMAs (bounded: it gives up after
+ *    about a second, records GEVO_ERR_TIMEOUT and frees its tensor memory).
  *
  * Numerical constants of the formulation (3DGS defaults; the paper gives none):
  *   near plane z > 0.2, 2-D dilation 0.3 px^2, Jacobian guard band 1.3x the
@@ -58,7 +60,7 @@ typedef enum {
     GEVO_ERR_INVALID = 1,   /* bad argument, nothing launched                    */
     GEVO_ERR_CAPACITY = 2,  /* device: duplicate count exceeded dup_capacity     */
     GEVO_ERR_CUDA = 3,      /* a CUDA runtime call or launch failed              */
-    GEVO_ERR_TIMEOUT = 4,   /* reserved: no call waits on the device             */
+    GEVO_ERR_TIMEOUT = 4,   /* device: a bounded tensor-core completion wait gave up */
     GEVO_ERR_NONFINITE = 5, /* device: a non-finite projected value was culled   */
     GEVO_ERR_SCRATCH_LIMIT = 6 /* sizes exceed gevo_bin_sort_noalloc's fixed scratch */
 } gevo_status;
@@ -299,6 +301,22 @@ gevo_status gevo_loss_l1(const gevo_layout* layout, const float* rgb, const floa
                          const float* depth, const float* target_depth, float lambda_depth,
                          float* dL_drgb, float* dL_ddepth, float* loss, void* workspace,
                          void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Learned depth prior (spec addition; the paper initialises new      */
+/* Gaussians from a cost volume + belief propagation, Section III-A)        */
+/* ---------------------------------------------------------------------- */
+
+/* C[M x N] = A[M x K] B[N x K]^T (+ bias[N]) (+ beta * C) (ReLU if relu) on the
+ * tcgen05 tensor cores: A, B BF16 row-major with K contiguous (K > 0 and lda,
+ * ldb multiples of 8, 16-byte aligned), FP32 accumulation in tensor memory, C
+ * FP32 (out_bf16 = 0) or BF16 (out_bf16 = 1) row-major.  bias: DEVICE float[N]
+ * or NULL.  workspace: any gevo workspace (its error word records
+ * GEVO_ERR_TIMEOUT if an MMA completion wait gives up).  All DEVICE. */
+gevo_status gevo_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda,
+                           const void* B, int32_t ldb, void* C, int32_t ldc, int32_t out_bf16,
+                           const float* bias, int32_t relu, float beta, void* workspace,
+                           void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Status                                                                   */

@@ -70,7 +70,28 @@ class Tuning(ctypes.Structure):
 EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin_sort",
            "gevo_render_fwd", "gevo_render_bwd", "gevo_project_bwd", "gevo_loss_l1",
            "gevo_last_error", "gevo_status_str", "gevo_version", "gevo_bin_sort_noalloc",
-           "gevo_grad2d_zero"]
+           "gevo_grad2d_zero", "gevo_gemm_bf16"]
+
+# Every symbol include/gevo_prior.h declares, with its argument kinds
+# (i: int32, I: int64, f: float, p: pointer; the last p is the stream).
+PRIOR = {
+    "gevo_conv3x3": "iiiipipppiiifpp",
+    "gevo_conv3x3_wgrad": "iiiipippIppp",
+    "gevo_relu_bwd": "Iipipipppp",
+    "gevo_maxpool2": "iiiipipp",
+    "gevo_maxpool2_bwd": "iiiipippifp",
+    "gevo_upsample2": "iiiippip",
+    "gevo_upsample2_bwd": "iiiipipp",
+    "gevo_flip3x3": "iippp",
+    "gevo_rgb_pack": "iiippp",
+    "gevo_head_fwd": "Iippppp",
+    "gevo_head_bwd": "Iippppppp",
+    "gevo_depth_target": "Ippppp",
+    "gevo_depth_l1": "Ipppppp",
+    "gevo_adam": "Ipppppffffip",
+    "gevo_to_bf16": "Ippp",
+}
+EXPORTS = EXPORTS + list(PRIOR)
 
 _lib = None
 
@@ -105,6 +126,8 @@ def load(build_if_missing: bool = True):
                                   P(Tuning), vp, vp]
     L.gevo_render_bwd.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp, vp,
                                   P(Grad2d), P(Tuning), vp, vp]
+    L.gevo_gemm_bf16.argtypes = [i32, i32, i32, vp, i32, vp, i32, vp, i32, i32, vp, i32, f32, vp, vp]
+    L.gevo_gemm_bf16.restype = ctypes.c_int
     L.gevo_grad2d_zero.argtypes = [P(Layout), i32, P(Proj), P(Grad2d), vp]
     L.gevo_grad2d_zero.restype = ctypes.c_int
     L.gevo_project_bwd.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d),
@@ -114,6 +137,10 @@ def load(build_if_missing: bool = True):
     L.gevo_status_str.argtypes = [ctypes.c_int]
     L.gevo_status_str.restype = ctypes.c_char_p
     L.gevo_version.restype = i32
+    kinds = {"i": ctypes.c_int32, "I": ctypes.c_int64, "f": ctypes.c_float, "p": vp}
+    for name, sig in PRIOR.items():
+        getattr(L, name).argtypes = [kinds[c] for c in sig]
+        getattr(L, name).restype = ctypes.c_int
     for name in ("gevo_project", "gevo_bin_sort", "gevo_render_fwd", "gevo_render_bwd",
                  "gevo_project_bwd", "gevo_loss_l1", "gevo_last_error"):
         getattr(L, name).restype = ctypes.c_int
@@ -271,6 +298,13 @@ def gevo_loss_l1(layout, rgb, target_rgb, depth, target_depth, lambda_depth, dL_
         float(lambda_depth), _p(dL_drgb), _p(dL_ddepth), _p(loss), _p(ws), _stream(stream)))
 
 
+def gevo_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, out_bf16, bias, relu, beta, ws,
+                   stream=None):
+    _check("gevo_gemm_bf16", load().gevo_gemm_bf16(
+        int(M), int(N), int(K), _p(A), int(lda), _p(B), int(ldb), _p(C), int(ldc),
+        int(bool(out_bf16)), _p(bias), int(bool(relu)), float(beta), _p(ws), _stream(stream)))
+
+
 def gevo_last_error(ws, stream=None) -> int:
     return int(load().gevo_last_error(_p(ws), _stream(stream)))
 
@@ -281,3 +315,17 @@ def gevo_status_str(code: int) -> str:
 
 def gevo_version() -> int:
     return int(load().gevo_version())
+
+
+def prior_call(name, *args, stream=None):
+    """Calls one gevo_prior.h entry point: tensors become device pointers, the
+    current stream is appended."""
+    conv = []
+    for a in args:
+        if isinstance(a, torch.Tensor):
+            conv.append(_p(a))
+        elif a is None:
+            conv.append(None)
+        else:
+            conv.append(a)
+    _check(name, getattr(load(), name)(*conv, _stream(stream)))

@@ -101,6 +101,7 @@ gevo_status gevo_last_error(void* workspace, void* stream)
     }
     if (word & gevo::kErrCapacity) return GEVO_ERR_CAPACITY;
     if (word & gevo::kErrNonFinite) return GEVO_ERR_NONFINITE;
+    if (word & gevo::kErrTimeout) return GEVO_ERR_TIMEOUT;
     return GEVO_OK;
 }
 

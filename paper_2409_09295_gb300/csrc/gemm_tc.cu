@@ -1,0 +1,352 @@
+// BF16 x BF16 -> FP32 GEMM on the 5th-generation tensor cores (tcgen05 + TMEM),
+// the contraction under the learned depth prior's convolutions (implicit GEMM:
+// rows = pixels, columns = output channels, depth = 9 x input channels).
+//
+//   C[M x N] = A[M x K] * B[N x K]^T  (+ bias[N]) (ReLU optional)
+//
+// A and B are row-major with K contiguous ("K-major").  One CTA of 128 threads
+// computes a 128 x BN tile (BN in {16, 32, 64, 128, 256}):
+//   1. every thread copies 16-byte pieces of the next 128 x 64 slice of A and
+//      BN x 64 slice of B into shared memory, arranged as the canonical
+//      no-swizzle K-major layout of 8-row x 16-byte core matrices (core
+//      matrices 128 B apart along K, 1 KB apart along M / N);
+//   2. one elected thread issues four tcgen05.mma (K = 16 each) that
+//      accumulate into a 128-lane x BN-column FP32 tile in tensor memory, then
+//      tcgen05.commit arrives on an mbarrier when they have completed;
+//   3. the CTA waits on the mbarrier (bounded: after ~1 s it records
+//      GEVO_ERR_TIMEOUT in the error word and stops issuing) before reusing
+//      the shared-memory slices;
+//   4. the epilogue reads the accumulator with tcgen05.ld (warp w owns lanes
+//      32w..32w+31 = rows) and writes FP32 or BF16 with bias and ReLU.
+#include <cuda_bf16.h>
+
+#include "gevo_internal.cuh"
+
+namespace gevo {
+
+constexpr int kGemmBM = 128;
+constexpr int kGemmBK = 64;
+constexpr long long kWaitLimit = 1ll << 22;    // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading-dimension
+// byte offset >> 4 (16-29), stride byte offset >> 4 (32-45), descriptor version
+// 1 (bit 46), no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at
+// bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :
+        : "r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true if the phase completed.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (long long it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(mbar, parity)) return true;
+    return false;
+}
+
+template <int NCOL>
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Copies rows [row0, row0 + ROWS) x columns [k0, k0 + 64) of a K-major bf16
+// matrix into the core-matrix layout at `dst`, zero-filling outside the matrix.
+template <int ROWS>
+__device__ __forceinline__ void stage_tile(const __nv_bfloat16* __restrict__ src, int ld, int nrows,
+                                           int K, int row0, int k0, unsigned char* dst)
+{
+    constexpr int CHUNKS = ROWS * (kGemmBK / 8);      // 16-byte pieces
+    for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x) {
+        const int r = c / (kGemmBK / 8);
+        const int kg = c % (kGemmBK / 8);
+        const int gr = row0 + r, gk = k0 + kg * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < nrows && gk < K)   // K is a multiple of 8, so a piece is all in or all out
+            v = *reinterpret_cast<const uint4*>(src + (size_t)gr * ld + gk);
+        const int off = (r >> 3) * 1024 + kg * 128 + (r & 7) * 16;
+        *reinterpret_cast<uint4*>(dst + off) = v;
+    }
+}
+
+// Implicit im2col of a 3x3, stride-1, zero-padded convolution over an NHWC
+// activation X[nb][H][W][C] (C a multiple of 8): row r = pixel (b, y, x),
+// column k = (tap, c) with tap = 3 ky + kx.  One 16-byte piece is 8 consecutive
+// channels of one neighbour, contiguous in NHWC.
+struct ConvA {
+    const __nv_bfloat16* X;
+    int H, W, C;
+};
+
+__device__ __forceinline__ void stage_conv_tile(const ConvA& cv, int M, int K, int row0, int k0,
+                                                unsigned char* dst)
+{
+    constexpr int CHUNKS = kGemmBM * (kGemmBK / 8);
+    for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x) {
+        const int r = c / (kGemmBK / 8);
+        const int kg = c % (kGemmBK / 8);
+        const int gr = row0 + r, gk = k0 + kg * 8;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < M && gk < K) {
+            const int tap = gk / cv.C, ch = gk - tap * cv.C;
+            const int x = gr % cv.W;
+            const int t = gr / cv.W;
+            const int y = t % cv.H, b = t / cv.H;
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            if (yy >= 0 && yy < cv.H && xx >= 0 && xx < cv.W)
+                v = *reinterpret_cast<const uint4*>(
+                    cv.X + ((size_t)(b * cv.H + yy) * cv.W + xx) * cv.C + ch);
+        }
+        const int off = (r >> 3) * 1024 + kg * 128 + (r & 7) * 16;
+        *reinterpret_cast<uint4*>(dst + off) = v;
+    }
+}
+
+template <int BN, bool CONV>
+__global__ void __launch_bounds__(128)
+k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, ConvA cv,
+            const __nv_bfloat16* __restrict__ B, int ldb, void* __restrict__ C, int ldc,
+            int out_bf16, const float* __restrict__ bias, int relu, float beta, int ksplit,
+            uint32_t* __restrict__ err)
+{
+    constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                                   // 128 x 64 bf16 = 16 KB
+    unsigned char* sB = smem + kGemmBM * kGemmBK * 2;           // BN x 64 bf16
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row0 = blockIdx.x * kGemmBM, col0 = blockIdx.y * BN;
+    const uint32_t mbar = smem_u32(&s_mbar);
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&s_tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    constexpr uint32_t idesc = idesc_bf16(kGemmBM, BN);
+    const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
+
+    uint32_t phase = 0;
+    // split-K: CTA z of ksplit handles K chunks [kc0, kc1)
+    const int nk_all = (K + kGemmBK - 1) / kGemmBK;
+    const int per = (nk_all + ksplit - 1) / ksplit;
+    const int kc0 = min(nk_all, (int)blockIdx.z * per), kc1 = min(nk_all, kc0 + per);
+    for (int kc = kc0; kc < kc1; kc++) {
+        if (CONV)
+            stage_conv_tile(cv, M, K, row0, kc * kGemmBK, sA);
+        else
+            stage_tile<kGemmBM>(A, lda, M, K, row0, kc * kGemmBK, sA);
+        stage_tile<BN>(B, ldb, N, K, col0, kc * kGemmBK, sB);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0 && !s_fail) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int k16 = 0; k16 < kGemmBK / 16; k16++) {
+                const uint64_t da = smem_desc(aBase + k16 * 256, 128, 1024);
+                const uint64_t db = smem_desc(bBase + k16 * 256, 128, 1024);
+                mma_bf16(tmem, da, db, idesc, (kc > kc0 || k16 > 0) ? 1u : 0u);
+            }
+            mma_commit(mbar);
+        }
+        // every thread waits for the MMAs to finish reading shared memory
+        if (!s_fail) {
+            if (!mbar_wait(mbar, phase)) {
+                s_fail = 1;
+                atomicOr(err, kErrTimeout);
+            }
+        }
+        phase ^= 1u;
+        __syncthreads();
+        if (s_fail) break;
+    }
+    if (s_fail) {
+        // give MMAs that may still be in flight a second bounded chance to land
+        // before the accumulator's tensor memory is released
+        mbar_wait(mbar, phase ^ 1u);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (!s_fail && kc1 > kc0) {
+        // epilogue: warp w reads accumulator lanes (rows) 32w .. 32w + 31
+        const int r = row0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16<16>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (r < M) {
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    const int c = col0 + c0 + i;
+                    if (c < N) {
+                        float x = v[i];
+                        if (ksplit > 1) {   // split-K partial: FP32 atomic accumulation
+                            atomicAdd(reinterpret_cast<float*>(C) + (size_t)r * ldc + c, x);
+                            continue;
+                        }
+                        if (bias) x += bias[c];
+                        if (out_bf16) {
+                            __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(C) + (size_t)r * ldc + c;
+                            if (beta != 0.f) x += beta * __bfloat162float(*o);
+                            if (relu) x = fmaxf(x, 0.f);
+                            *o = __float2bfloat16_rn(x);
+                        } else {
+                            float* o = reinterpret_cast<float*>(C) + (size_t)r * ldc + c;
+                            if (beta != 0.f) x += beta * *o;
+                            if (relu) x = fmaxf(x, 0.f);
+                            *o = x;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+}
+
+template <int BN, bool CONV>
+static gevo_status launch_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, ConvA cv,
+                               const __nv_bfloat16* B, int ldb, void* C, int ldc, int out_bf16,
+                               const float* bias, int relu, float beta, int ksplit, uint32_t* err,
+                               cudaStream_t st)
+{
+    const size_t smem = (size_t)(kGemmBM + BN) * kGemmBK * 2;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm_bf16<BN, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    dim3 grid((M + kGemmBM - 1) / kGemmBM, (N + BN - 1) / BN, ksplit);
+    k_gemm_bf16<BN, CONV><<<grid, 128, smem, st>>>(M, N, K, A, lda, cv, B, ldb, C, ldc, out_bf16,
+                                                   bias, relu, beta, ksplit, err);
+    GEVO_CHECK_LAUNCH();
+    return GEVO_OK;
+}
+
+template <bool CONV>
+static gevo_status gemm_dispatch(int M, int N, int K, const __nv_bfloat16* a, int lda, ConvA cv,
+                                 const __nv_bfloat16* b, int ldb, void* C, int ldc, int out_bf16,
+                                 const float* bias, int relu, float beta, int ksplit,
+                                 uint32_t* err, cudaStream_t st)
+{
+    if (N <= 16) return launch_gemm<16, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
+    if (N <= 32) return launch_gemm<32, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
+    if (N <= 64) return launch_gemm<64, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
+    if (N <= 128) return launch_gemm<128, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
+    return launch_gemm<256, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
+}
+
+gevo_status gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C,
+                      int ldc, int out_bf16, const float* bias, int relu, float beta, int ksplit,
+                      uint32_t* err, cudaStream_t st)
+{
+    ConvA cv{nullptr, 0, 0, 0};
+    return gemm_dispatch<false>(M, N, K, reinterpret_cast<const __nv_bfloat16*>(A), lda, cv,
+                                reinterpret_cast<const __nv_bfloat16*>(B), ldb, C, ldc, out_bf16,
+                                bias, relu, beta, ksplit, err, st);
+}
+
+gevo_status conv3x3_bf16(int nb, int H, int W, int Cin, const void* X, int Cout, const void* Wt,
+                         void* Y, int ldy, int out_bf16, const float* bias, int relu, float beta,
+                         uint32_t* err, cudaStream_t st)
+{
+    ConvA cv{reinterpret_cast<const __nv_bfloat16*>(X), H, W, Cin};
+    return gemm_dispatch<true>(nb * H * W, Cout, 9 * Cin, nullptr, 0, cv,
+                               reinterpret_cast<const __nv_bfloat16*>(Wt), 9 * Cin, Y, ldy,
+                               out_bf16, bias, relu, beta, 1, err, st);
+}
+
+}  // namespace gevo
+
+extern "C" gevo_status gevo_gemm_bf16(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda,
+                                      const void* B, int32_t ldb, void* C, int32_t ldc,
+                                      int32_t out_bf16, const float* bias, int32_t relu, float beta,
+                                      void* workspace, void* stream)
+{
+    if (M < 0 || N < 0 || K <= 0 || !A || !B || !C || !workspace || K % 8 != 0 || lda % 8 != 0 ||
+        ldb % 8 != 0 || lda < K || ldb < K || ldc < N || !gevo_aligned(A, 16) ||
+        !gevo_aligned(B, 16))
+        return GEVO_ERR_INVALID;
+    if (M == 0 || N == 0) return GEVO_OK;
+    return gevo::gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, out_bf16, bias, relu, beta, 1,
+                           reinterpret_cast<uint32_t*>(workspace), (cudaStream_t)stream);
+}

@@ -25,6 +25,7 @@ constexpr float kLn2 = 0.6931471805599453f;
 // Bits of the sticky device error word.
 constexpr uint32_t kErrCapacity = 1u << 0;
 constexpr uint32_t kErrNonFinite = 1u << 1;
+constexpr uint32_t kErrTimeout = 1u << 2;    // a bounded device wait gave up
 
 // Workspace layout (offsets in bytes from the 256-byte aligned base).
 struct WsLayout {

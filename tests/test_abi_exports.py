@@ -12,9 +12,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "gevo.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gevo_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in ("gevo.h", "gevo_prior.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(gevo_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -58,3 +61,21 @@ def test_layout_and_workspace_host_calls():
         _abi.gevo_layout_init([0], [10])
     assert _abi.gevo_status_str(2) == "duplicate capacity exceeded"
     assert _abi.gevo_version() == 1
+
+
+def _prior_kinds():
+    src = open(os.path.join(ROOT, "include", "gevo_prior.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"gevo_status (gevo_\w+)\((.*?)\);", src, flags=re.S):
+        kinds = ""
+        for a in m.group(2).split(","):
+            a = a.strip()
+            kinds += "p" if "*" in a else {"int32_t": "i", "int64_t": "I", "float": "f"}[a.split()[0]]
+        out[m.group(1)] = kinds
+    return out
+
+
+def test_prior_binding_signatures_match_header():
+    from paper_2409_09295_gb300 import _abi
+    assert _abi.PRIOR == _prior_kinds()
