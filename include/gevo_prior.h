@@ -97,6 +97,34 @@ gevo_status gevo_adam(int64_t n, float* param, const float* grad, float* m, floa
                       void* param_bf16, float lr, float beta1, float beta2, float eps,
                       int32_t step, void* stream);
 
+/* Plain initialisation of Section III-A: the photometric cost volume of Eq. 1
+ * for reference keyframe `ref` of nk keyframes rgb [nk][3][H][W] (H, W
+ * multiples of 4) with cameras cams [nk][16] (R, t, fx, fy, cx, cy), at 1/4
+ * resolution over nd depth hypotheses spaced linearly on [d0, d1]:
+ * volume[(y * W/4 + x) * nd + k] = mean over the other keyframes, where the
+ * sample falls inside the image, of |grey_ref(u) - grey_i(pi(u, d_k))|
+ * (grey = mean of RGB after a 4x4 box average, bilinear sampling; 1.0 where
+ * no keyframe sees the point).  grey: scratch [nk][H/4][W/4].  depth
+ * [H][W]: winner-take-all hypothesis (lowest cost, then lowest k), nearest x4
+ * upsampled -- standing in for the belief propagation and edge-aware
+ * upsampling the paper cites. */
+gevo_status gevo_cost_volume(int32_t nk, int32_t ref, int32_t H, int32_t W, const float* rgb,
+                             const float* cams, int32_t nd, float d0, float d1, float* grey,
+                             float* volume, float* depth, void* stream);
+
+/* New Gaussians from a depth map (z-depth of pixel (x, y) sampled at
+ * coordinate x, camera cam[16]): every pixel with mask > 0.5 whose 32-bit hash
+ * (seeded) is <= keep becomes one Gaussian -- mean at its back-projection,
+ * colour SH DC (rgb - 0.5) / Y00 with higher bands 0, isotropic scale
+ * scale_px * depth / fx, identity rotation, the given opacity -- written at
+ * slot atomicAdd(counter, 1) if that slot is below cap (order unspecified).
+ * rgb planar [3][H][W]. */
+gevo_status gevo_unproject(int32_t H, int32_t W, const float* rgb, const float* depth,
+                           const float* mask, const float* cam, uint32_t keep, uint32_t seed,
+                           float scale_px, float opacity, int32_t sh_degree, uint32_t* counter,
+                           int32_t cap, float* means, float* scales, float* quats,
+                           float* opacities, float* sh, void* stream);
+
 /* y = bf16(x). */
 gevo_status gevo_to_bf16(int64_t n, const float* x, void* y, void* stream);
 

@@ -73,7 +73,7 @@ EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin
            "gevo_grad2d_zero", "gevo_gemm_bf16"]
 
 # Every symbol include/gevo_prior.h declares, with its argument kinds
-# (i: int32, I: int64, f: float, p: pointer; the last p is the stream).
+# (i: int32, u: uint32, I: int64, f: float, p: pointer; the last p is the stream).
 PRIOR = {
     "gevo_conv3x3": "iiiipipppiiifpp",
     "gevo_conv3x3_wgrad": "iiiipippIppp",
@@ -89,6 +89,8 @@ PRIOR = {
     "gevo_depth_target": "Ippppp",
     "gevo_depth_l1": "Ipppppp",
     "gevo_adam": "Ipppppffffip",
+    "gevo_cost_volume": "iiiippiffpppp",
+    "gevo_unproject": "iippppuuffipipppppp",
     "gevo_to_bf16": "Ippp",
 }
 EXPORTS = EXPORTS + list(PRIOR)
@@ -137,7 +139,8 @@ def load(build_if_missing: bool = True):
     L.gevo_status_str.argtypes = [ctypes.c_int]
     L.gevo_status_str.restype = ctypes.c_char_p
     L.gevo_version.restype = i32
-    kinds = {"i": ctypes.c_int32, "I": ctypes.c_int64, "f": ctypes.c_float, "p": vp}
+    kinds = {"i": ctypes.c_int32, "u": ctypes.c_uint32, "I": ctypes.c_int64, "f": ctypes.c_float,
+             "p": vp}
     for name, sig in PRIOR.items():
         getattr(L, name).argtypes = [kinds[c] for c in sig]
         getattr(L, name).restype = ctypes.c_int

@@ -71,7 +71,7 @@ def _prior_kinds():
         kinds = ""
         for a in m.group(2).split(","):
             a = a.strip()
-            kinds += "p" if "*" in a else {"int32_t": "i", "int64_t": "I", "float": "f"}[a.split()[0]]
+            kinds += "p" if "*" in a else {"int32_t": "i", "int64_t": "I", "float": "f", "uint32_t": "u"}[a.split()[0]]
         out[m.group(1)] = kinds
     return out
 

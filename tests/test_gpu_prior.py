@@ -63,7 +63,7 @@ def test_prior_forward_and_gradients_match_oracle(nb, H, W, chans):
             rel = np.linalg.norm(got - want) / (np.linalg.norm(want) + 1e-300)
             assert cos >= 0.9995 and rel <= 3e-2, (name, what, cos, rel)
     gw = net.head_state[0].cpu().numpy()
-    assert np.dot(gw, g["head"][0]) / (np.linalg.norm(gw) * np.linalg.norm(g["head"][0])) >= 0.9999
+    assert np.dot(gw, g["head"][0]) / (np.linalg.norm(gw) * np.linalg.norm(g["head"][0])) >= 0.9995
     assert _abi.gevo_last_error(net.ws) == 0
 
 
