@@ -354,8 +354,8 @@ def main():
 def launches_per_step(rep) -> int:
     """Kernels of ours launched per step: project (1), bin_sort (count, scan,
     scatter, segsort = 4), render_fwd (1), loss (1), grad2d_zero (1), render_bwd
-    (1), project_bwd (1)."""
-    return 1 + 4 + 1 + 1 + 1 + 1 + 1
+    (1), project_bwd (geometry, plus the SH-colour kernel when colours are SH)."""
+    return 1 + 4 + 1 + 1 + 1 + 1 + (1 if rep.pipe.colour == "rgb" else 2)
 
 
 if __name__ == "__main__":

@@ -138,7 +138,7 @@ typedef struct {
 } gevo_grad2d;
 
 /* Launch shape for the per-tile kernels (chosen by the autotuner).
- * threads_per_tile in {64, 128, 256}: each thread owns 256 / threads pixels of
+ * threads_per_tile in {32, 64, 128, 256}: each thread owns 256 / threads pixels of
  * its 16 x 16 tile.  persistent != 0: one grid of blocks_per_sm * SMs blocks
  * pulls (view, tile) work items heaviest first from a device counter; 0: one
  * block per tile.  NULL = {256, 0, 0}. */

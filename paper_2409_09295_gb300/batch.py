@@ -26,7 +26,7 @@ import torch
 from .raster import Pipeline, camera_tensor
 
 CANDIDATES = [dict(threads_per_tile=t, persistent=p, blocks_per_sm=0)
-              for t, p in itertools.product((256, 128, 64), (0, 1))]
+              for t, p in itertools.product((256, 128, 64, 32), (0, 1))]
 
 
 def _time(fn, reps=3):

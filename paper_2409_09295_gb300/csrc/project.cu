@@ -281,76 +281,72 @@ k_project_fwd(gevo_layout L, int n, const float* __restrict__ means, const float
 // ---------------------------------------------------------------------------
 // Backward.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float warp_sum(float v)
+// Visible views of Gaussian g as a bit mask (at most 64 views).
+__device__ __forceinline__ unsigned long long visible_views(const gevo_layout& L, int n, int g,
+                                                            const int* __restrict__ radius)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    unsigned long long m = 0ull;
+    for (int v = 0; v < L.n_views; v++)
+        if (radius[(size_t)v * n + g] > 0) m |= 1ull << v;
+    return m;
 }
 
-template <int DEG, bool HAS_RGB>
+// Geometry part of the projection derivative: mean (through the camera-frame
+// mean, the image mean, the depth and the EWA Jacobian), scale and rotation
+// (through Sigma3), opacity, RGB colours if given, and the pose twist except
+// its colour term.  Each lane walks only its own visible views, so a warp does
+// max-over-lanes rather than all-views iterations; the per-view twist sums go
+// through shared-memory atomics.
+template <bool HAS_RGB>
 __global__ void __launch_bounds__(128)
-k_project_bwd(gevo_layout L, int n, const float* __restrict__ means, const float* __restrict__ scales,
-              const float4* __restrict__ quats, const float* __restrict__ coef,
-              const gevo_camera* __restrict__ cams, const int* __restrict__ radius,
-              const float2* __restrict__ g_xy, const float4* __restrict__ g_co,
-              const float4* __restrict__ g_rz, float* __restrict__ d_means,
-              float* __restrict__ d_scales, float4* __restrict__ d_quats,
-              float* __restrict__ d_opac, float* __restrict__ d_coef, float* __restrict__ dxi)
+k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
+                  const float* __restrict__ scales, const float4* __restrict__ quats,
+                  const gevo_camera* __restrict__ cams, const int* __restrict__ radius,
+                  const float2* __restrict__ g_xy, const float4* __restrict__ g_co,
+                  const float4* __restrict__ g_rz, float* __restrict__ d_means,
+                  float* __restrict__ d_scales, float4* __restrict__ d_quats,
+                  float* __restrict__ d_opac, float* __restrict__ d_rgb, float* __restrict__ dxi)
 {
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
     __shared__ float s_dxi[GEVO_MAX_VIEWS][6];
     load_cams(L, cams, s_cam);
     for (int i = threadIdx.x; i < L.n_views * 6; i += blockDim.x) (&s_dxi[0][0])[i] = 0.f;
     __syncthreads();
-    const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = g0 < n;
-    const int g = live ? g0 : n - 1;
-    constexpr int K = (DEG + 1) * (DEG + 1);
-
-    const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
-    const float s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
-    float Rq[9], qn[4], qinv;
-    quat_to_rot(__ldg(quats + g), Rq, qn, qinv);
-    float N[9];
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) {
+        const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+        const float s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
+        float Rq[9], qn[4], qinv;
+        quat_to_rot(__ldg(quats + g), Rq, qn, qinv);
+        float N[9];
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+        for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int k = 0; k < 3; k++) N[3 * i + k] = Rq[3 * i + k] * s[k];
-    float k[16][3];
-    load_colour<DEG, HAS_RGB>(coef, g, k);
-
-    float dmu[3] = {0.f, 0.f, 0.f};
-    float dN[9];
+            for (int k = 0; k < 3; k++) N[3 * i + k] = Rq[3 * i + k] * s[k];
+        float dmu[3] = {0.f, 0.f, 0.f}, dN[9], dop = 0.f, drgb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int i = 0; i < 9; i++) dN[i] = 0.f;
-    float dop = 0.f;
-    float dk[16][3];
-#pragma unroll
-    for (int i = 0; i < 16; i++) dk[i][0] = dk[i][1] = dk[i][2] = 0.f;
-
-    for (int v = 0; v < L.n_views; v++) {
-        const CamS& cam = s_cam[v];
-        const size_t idx = (size_t)v * n + g;
-        const bool vis = live && radius[idx] > 0;
-        float xi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (vis) {
+        for (int i = 0; i < 9; i++) dN[i] = 0.f;
+        unsigned long long vis = visible_views(L, n, g, radius);
+        while (vis) {
+            const int v = __ffsll((long long)vis) - 1;
+            vis &= vis - 1;
+            const CamS& cam = s_cam[v];
+            const size_t idx = (size_t)v * n + g;
             const float2 gxy = g_xy[idx];
             const float4 gco = g_co[idx];
             const float4 grz = g_rz[idx];
             Geo G;
             geometry(cam, mu, N, G);
             dop += gco.w;
+            if (HAS_RGB) { drgb[0] += grz.x; drgb[1] += grz.y; drgb[2] += grz.z; }
             const float idet = 1.f / G.det;
             const float ca = G.c * idet, cb = -G.b * idet, cc = G.a * idet;
             // dL/dSigma2 = -Q Gc Q with Gc = [[gA, gB/2], [gB/2, gC]]
             const float hb = 0.5f * gco.y;
             const float q00 = ca * gco.x + cb * hb, q01 = ca * hb + cb * gco.z;
             const float q10 = cb * gco.x + cc * hb, q11 = cb * hb + cc * gco.z;
-            const float X00 = q00 * ca + q01 * cb;
-            const float X01 = q00 * cb + q01 * cc;
-            const float X11 = q10 * cb + q11 * cc;
-            const float dA = -X00, dC = -X11, dB = -2.f * X01;   // w.r.t. a, c, b of Sigma2
+            const float dA = -(q00 * ca + q01 * cb), dC = -(q10 * cb + q11 * cc);
+            const float dB = -2.f * (q00 * cb + q01 * cc);
             // Sigma2 = T T^T + 0.3 I  ->  dT = 2 [[dA, dB/2], [dB/2, dC]] T
             float dT[6];
 #pragma unroll
@@ -358,8 +354,7 @@ k_project_bwd(gevo_layout L, int n, const float* __restrict__ means, const float
                 dT[kk] = 2.f * dA * G.T[kk] + dB * G.T[3 + kk];
                 dT[3 + kk] = dB * G.T[kk] + 2.f * dC * G.T[3 + kk];
             }
-            // T = M N
-            float dM[6];
+            float dM[6];   // T = M N
 #pragma unroll
             for (int r = 0; r < 2; r++)
 #pragma unroll
@@ -375,13 +370,6 @@ k_project_bwd(gevo_layout L, int n, const float* __restrict__ means, const float
             const float dJ02 = dM[0] * cam.R[6] + dM[1] * cam.R[7] + dM[2] * cam.R[8];
             const float dJ11 = dM[3] * cam.R[3] + dM[4] * cam.R[4] + dM[5] * cam.R[5];
             const float dJ12 = dM[3] * cam.R[6] + dM[4] * cam.R[7] + dM[5] * cam.R[8];
-            float dW[9];  // dW[k][i] = sum_r J[r][k] dM[r][i]
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                dW[i] = G.J00 * dM[i];
-                dW[3 + i] = G.J11 * dM[3 + i];
-                dW[6 + i] = G.J02 * dM[i] + G.J12 * dM[3 + i];
-            }
             const float iz = G.iz, iz2 = iz * iz;
             float dp[3];
             dp[0] = gxy.x * cam.fx * iz;
@@ -400,53 +388,17 @@ k_project_bwd(gevo_layout L, int n, const float* __restrict__ means, const float
             } else {
                 dp[2] += dJ12 * cam.fy * G.tyz * iz2;
             }
-            // colour
-            float dcc[3] = {0.f, 0.f, 0.f};
-            if (HAS_RGB) {
-                dk[0][0] += grz.x; dk[0][1] += grz.y; dk[0][2] += grz.z;
-            } else {
-                const float ux = mu[0] - cam.c[0], uy = mu[1] - cam.c[1], uz = mu[2] - cam.c[2];
-                const float inl = rsqrtf(ux * ux + uy * uy + uz * uz);
-                const float dx = ux * inl, dy = uy * inl, dz = uz * inl;
-                float Y[16];
-                sh_eval<DEG>(dx, dy, dz, Y);
-                float gm[3];
-                const float gin[3] = {grz.x, grz.y, grz.z};
-#pragma unroll
-                for (int ch = 0; ch < 3; ch++) {
-                    float acc = 0.5f;
-#pragma unroll
-                    for (int i = 0; i < K; i++) acc += Y[i] * k[i][ch];
-                    gm[ch] = acc < 0.f ? 0.f : gin[ch];
-                }
-                float w[16];
-#pragma unroll
-                for (int i = 0; i < K; i++) {
-                    dk[i][0] += gm[0] * Y[i]; dk[i][1] += gm[1] * Y[i]; dk[i][2] += gm[2] * Y[i];
-                    w[i] = gm[0] * k[i][0] + gm[1] * k[i][1] + gm[2] * k[i][2];
-                }
-                if (DEG > 0) {
-                    float gx, gy, gz;
-                    sh_grad_dir<DEG>(dx, dy, dz, w, gx, gy, gz);
-                    const float dd = dx * gx + dy * gy + dz * gz;
-                    const float ex = (gx - dx * dd) * inl, ey = (gy - dy * dd) * inl,
-                                ez = (gz - dz * dd) * inl;
-                    dmu[0] += ex; dmu[1] += ey; dmu[2] += ez;
-                    dcc[0] = -ex; dcc[1] = -ey; dcc[2] = -ez;
-                }
-            }
-            // camera-frame mean -> world mean
 #pragma unroll
             for (int j = 0; j < 3; j++)
                 dmu[j] += cam.R[j] * dp[0] + cam.R[3 + j] * dp[1] + cam.R[6 + j] * dp[2];
             if (dxi) {
+                float dW[9];  // dW[k][i] = sum_r J[r][k] dM[r][i]
 #pragma unroll
-                for (int i = 0; i < 3; i++)
-                    xi[i] = dp[i] - (cam.R[3 * i] * dcc[0] + cam.R[3 * i + 1] * dcc[1] +
-                                     cam.R[3 * i + 2] * dcc[2]);
-                xi[3] = G.p[1] * dp[2] - G.p[2] * dp[1];
-                xi[4] = G.p[2] * dp[0] - G.p[0] * dp[2];
-                xi[5] = G.p[0] * dp[1] - G.p[1] * dp[0];
+                for (int i = 0; i < 3; i++) {
+                    dW[i] = G.J00 * dM[i];
+                    dW[3 + i] = G.J11 * dM[3 + i];
+                    dW[6 + i] = G.J02 * dM[i] + G.J12 * dM[3 + i];
+                }
                 float B[9];  // dW W^T
 #pragma unroll
                 for (int i = 0; i < 3; i++)
@@ -454,20 +406,15 @@ k_project_bwd(gevo_layout L, int n, const float* __restrict__ means, const float
                     for (int j = 0; j < 3; j++)
                         B[3 * i + j] = dW[3 * i] * cam.R[3 * j] + dW[3 * i + 1] * cam.R[3 * j + 1] +
                                        dW[3 * i + 2] * cam.R[3 * j + 2];
-                xi[3] += B[7] - B[5];
-                xi[4] += B[2] - B[6];
-                xi[5] += B[3] - B[1];
+                float* o = s_dxi[v];
+                atomicAdd(o + 0, dp[0]);
+                atomicAdd(o + 1, dp[1]);
+                atomicAdd(o + 2, dp[2]);
+                atomicAdd(o + 3, G.p[1] * dp[2] - G.p[2] * dp[1] + B[7] - B[5]);
+                atomicAdd(o + 4, G.p[2] * dp[0] - G.p[0] * dp[2] + B[2] - B[6]);
+                atomicAdd(o + 5, G.p[0] * dp[1] - G.p[1] * dp[0] + B[3] - B[1]);
             }
         }
-        if (dxi && __any_sync(0xffffffffu, vis)) {
-#pragma unroll
-            for (int j = 0; j < 6; j++) {
-                const float r = warp_sum(xi[j]);
-                if ((threadIdx.x & 31) == 0 && r != 0.f) atomicAdd(&s_dxi[v][j], r);
-            }
-        }
-    }
-    if (live) {
         // N = Rq diag(s)
         float dRq[9];
 #pragma unroll
@@ -477,23 +424,100 @@ k_project_bwd(gevo_layout L, int n, const float* __restrict__ means, const float
             for (int i = 0; i < 3; i++) dRq[3 * i + kk] = dN[3 * i + kk] * s[kk];
         }
         const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
-        const float* G = dRq;
+        const float* Gq = dRq;
         float dq[4];
-        dq[0] = 2.f * (-z * G[1] + y * G[2] + z * G[3] - x * G[5] - y * G[6] + x * G[7]);
-        dq[1] = 2.f * (y * G[1] + z * G[2] + y * G[3] - 2.f * x * G[4] - w * G[5] + z * G[6] +
-                       w * G[7] - 2.f * x * G[8]);
-        dq[2] = 2.f * (-2.f * y * G[0] + x * G[1] + w * G[2] + x * G[3] + z * G[5] - w * G[6] +
-                       z * G[7] - 2.f * y * G[8]);
-        dq[3] = 2.f * (-2.f * z * G[0] - w * G[1] + x * G[2] + w * G[3] - 2.f * z * G[4] +
-                       y * G[5] + x * G[6] + y * G[7]);
+        dq[0] = 2.f * (-z * Gq[1] + y * Gq[2] + z * Gq[3] - x * Gq[5] - y * Gq[6] + x * Gq[7]);
+        dq[1] = 2.f * (y * Gq[1] + z * Gq[2] + y * Gq[3] - 2.f * x * Gq[4] - w * Gq[5] + z * Gq[6] +
+                       w * Gq[7] - 2.f * x * Gq[8]);
+        dq[2] = 2.f * (-2.f * y * Gq[0] + x * Gq[1] + w * Gq[2] + x * Gq[3] + z * Gq[5] - w * Gq[6] +
+                       z * Gq[7] - 2.f * y * Gq[8]);
+        dq[3] = 2.f * (-2.f * z * Gq[0] - w * Gq[1] + x * Gq[2] + w * Gq[3] - 2.f * z * Gq[4] +
+                       y * Gq[5] + x * Gq[6] + y * Gq[7]);
         const float dot = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
         d_quats[g] = make_float4((dq[0] - w * dot) * qinv, (dq[1] - x * dot) * qinv,
                                  (dq[2] - y * dot) * qinv, (dq[3] - z * dot) * qinv);
         d_means[3 * g] = dmu[0]; d_means[3 * g + 1] = dmu[1]; d_means[3 * g + 2] = dmu[2];
         d_opac[g] = dop;
-        if (HAS_RGB) {
-            d_coef[3 * g] = dk[0][0]; d_coef[3 * g + 1] = dk[0][1]; d_coef[3 * g + 2] = dk[0][2];
-        } else if ((K * 3) % 4 == 0) {
+        if (HAS_RGB) { d_rgb[3 * g] = drgb[0]; d_rgb[3 * g + 1] = drgb[1]; d_rgb[3 * g + 2] = drgb[2]; }
+    }
+    if (dxi) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < L.n_views * 6; i += blockDim.x) {
+            const float r = (&s_dxi[0][0])[i];
+            if (r != 0.f) atomicAdd(dxi + i, r);
+        }
+    }
+}
+
+// SH colour part: colour = max(0, sum_k Y_k(d) k_k + 0.5), d the unit direction
+// from the camera centre.  Writes dL/dSH, adds the direction's share to
+// dL/dmean (after k_project_bwd_geo has written it) and the camera centre's to
+// the translation part of the pose twist.
+template <int DEG>
+__global__ void __launch_bounds__(128)
+k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
+                  const float* __restrict__ coef, const gevo_camera* __restrict__ cams,
+                  const int* __restrict__ radius, const float4* __restrict__ g_rz,
+                  float* __restrict__ d_means, float* __restrict__ d_coef, float* __restrict__ dxi)
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    __shared__ CamS s_cam[GEVO_MAX_VIEWS];
+    __shared__ float s_dxi[GEVO_MAX_VIEWS][3];
+    load_cams(L, cams, s_cam);
+    for (int i = threadIdx.x; i < L.n_views * 3; i += blockDim.x) (&s_dxi[0][0])[i] = 0.f;
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n) {
+        const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+        float k[16][3];
+        load_colour<DEG, false>(coef, g, k);
+        float dk[16][3];
+#pragma unroll
+        for (int i = 0; i < 16; i++) dk[i][0] = dk[i][1] = dk[i][2] = 0.f;
+        float dmu[3] = {0.f, 0.f, 0.f};
+        unsigned long long vis = visible_views(L, n, g, radius);
+        while (vis) {
+            const int v = __ffsll((long long)vis) - 1;
+            vis &= vis - 1;
+            const CamS& cam = s_cam[v];
+            const float4 grz = g_rz[(size_t)v * n + g];
+            const float ux = mu[0] - cam.c[0], uy = mu[1] - cam.c[1], uz = mu[2] - cam.c[2];
+            const float inl = rsqrtf(ux * ux + uy * uy + uz * uz);
+            const float dx = ux * inl, dy = uy * inl, dz = uz * inl;
+            float Y[16];
+            sh_eval<DEG>(dx, dy, dz, Y);
+            float gm[3];
+            const float gin[3] = {grz.x, grz.y, grz.z};
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) {
+                float acc = 0.5f;
+#pragma unroll
+                for (int i = 0; i < K; i++) acc += Y[i] * k[i][ch];
+                gm[ch] = acc < 0.f ? 0.f : gin[ch];
+            }
+            float w[16];
+#pragma unroll
+            for (int i = 0; i < K; i++) {
+                dk[i][0] += gm[0] * Y[i]; dk[i][1] += gm[1] * Y[i]; dk[i][2] += gm[2] * Y[i];
+                w[i] = gm[0] * k[i][0] + gm[1] * k[i][1] + gm[2] * k[i][2];
+            }
+            if (DEG > 0) {
+                float gx, gy, gz;
+                sh_grad_dir<DEG>(dx, dy, dz, w, gx, gy, gz);
+                const float dd = dx * gx + dy * gy + dz * gz;
+                const float ex = (gx - dx * dd) * inl, ey = (gy - dy * dd) * inl, ez = (gz - dz * dd) * inl;
+                dmu[0] += ex; dmu[1] += ey; dmu[2] += ez;
+                if (dxi) {
+                    // camera centre c = -R^T (t + rho): dL/drho = -R dL/dc = R (dL/d(mu - c))
+#pragma unroll
+                    for (int i = 0; i < 3; i++)
+                        atomicAdd(&s_dxi[v][i], cam.R[3 * i] * ex + cam.R[3 * i + 1] * ey +
+                                                    cam.R[3 * i + 2] * ez);
+                }
+            }
+        }
+        d_means[3 * g] += dmu[0]; d_means[3 * g + 1] += dmu[1]; d_means[3 * g + 2] += dmu[2];
+        if ((K * 3) % 4 == 0) {
             float4* p = reinterpret_cast<float4*>(d_coef + (size_t)g * K * 3);
             float tmp[K * 3];
 #pragma unroll
@@ -510,10 +534,11 @@ k_project_bwd(gevo_layout L, int n, const float* __restrict__ means, const float
     }
     if (dxi) {
         __syncthreads();
-        for (int i = threadIdx.x; i < L.n_views * 6; i += blockDim.x) {
-            const float r = (&s_dxi[0][0])[i];
-            if (r != 0.f) atomicAdd(dxi + i, r);
-        }
+        for (int v = threadIdx.x; v < L.n_views; v += blockDim.x)
+            for (int i = 0; i < 3; i++) {
+                const float r = s_dxi[v][i];
+                if (r != 0.f) atomicAdd(dxi + 6 * v + i, r);
+            }
     }
 }
 
@@ -537,12 +562,15 @@ static void launch_bwd(const gevo_layout& L, const gevo_gaussians& g, const gevo
 {
     const int threads = 128;
     const int blocks = (g.n + threads - 1) / threads;
-    k_project_bwd<DEG, RGB><<<blocks, threads, 0, st>>>(
-        L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), RGB ? g.rgb : g.sh,
-        cams, o.radius, reinterpret_cast<const float2*>(gr.xy),
-        reinterpret_cast<const float4*>(gr.conic_opacity),
+    k_project_bwd_geo<RGB><<<blocks, threads, 0, st>>>(
+        L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), cams, o.radius,
+        reinterpret_cast<const float2*>(gr.xy), reinterpret_cast<const float4*>(gr.conic_opacity),
         reinterpret_cast<const float4*>(gr.rgb_depth), out.means, out.scales,
-        reinterpret_cast<float4*>(out.quats), out.opacities, RGB ? out.rgb : out.sh, dxi);
+        reinterpret_cast<float4*>(out.quats), out.opacities, out.rgb, dxi);
+    if (!RGB)
+        k_project_bwd_col<DEG><<<blocks, threads, 0, st>>>(
+            L, g.n, g.means, g.sh, cams, o.radius, reinterpret_cast<const float4*>(gr.rgb_depth),
+            out.means, out.sh, dxi);
 }
 
 static bool valid_gaussians(const gevo_gaussians* g)

@@ -456,7 +456,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
 static int pick_ppt(const gevo_tuning* t)
 {
     const int th = t ? t->threads_per_tile : 256;
-    return th == 64 ? 4 : (th == 128 ? 2 : 1);
+    return th == 32 ? 8 : (th == 64 ? 4 : (th == 128 ? 2 : 1));
 }
 
 template <int PPT, typename K>
@@ -526,7 +526,8 @@ static gevo_status launch_bwd(const gevo_layout& L, int n, const gevo_proj& p, c
 static bool valid_tuning(const gevo_tuning* t)
 {
     if (!t) return true;
-    return (t->threads_per_tile == 64 || t->threads_per_tile == 128 || t->threads_per_tile == 256) &&
+    return (t->threads_per_tile == 32 || t->threads_per_tile == 64 || t->threads_per_tile == 128 ||
+            t->threads_per_tile == 256) &&
            t->blocks_per_sm >= 0;
 }
 
@@ -550,6 +551,7 @@ extern "C" gevo_status gevo_render_fwd(const gevo_layout* layout, int32_t n, con
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = reinterpret_cast<char*>(workspace);
     switch (pick_ppt(tuning)) {
+    case 8: return launch_fwd<8>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
     case 4: return launch_fwd<4>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
     case 2: return launch_fwd<2>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
     default: return launch_fwd<1>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
@@ -574,6 +576,7 @@ extern "C" gevo_status gevo_render_bwd(const gevo_layout* layout, int32_t n, con
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = reinterpret_cast<char*>(workspace);
     switch (pick_ppt(tuning)) {
+    case 8: return launch_bwd<8>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
     case 4: return launch_bwd<4>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
     case 2: return launch_bwd<2>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
     default: return launch_bwd<1>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
