@@ -69,7 +69,7 @@ def lib():
             L.orc_render_fwd.argtypes = [i32, i32, _P(d), _P(d), _P(d), _P(d), _P(d),
                                          _P(u32), _P(u32), _P(d),
                                          _P(d), _P(d), _P(d), _P(i32), _P(i32), _P(d), _P(i32),
-                                         _P(u64)]
+                                         _P(u64), _P(d), _P(d)]
             L.orc_render_bwd.argtypes = [i32, i32, _P(d), _P(d), _P(d), _P(d), _P(d),
                                          _P(u32), _P(u32), _P(d),
                                          _P(d), _P(d), _P(d),
@@ -205,9 +205,11 @@ def bin_f32(sizes, xy32, radius, depth32, capacity=None):
 # ---------------------------------------------------------------------------
 # Step 5 / 6: blending of one view and its derivative.
 # ---------------------------------------------------------------------------
-def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0)):
+def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0), pix_err=None):
     """rec: dict with xy[N,2], conic[N,3], opacity[N], rgb[N,3], depth[N] (float64).
-    ranges_view: this view's [tiles,2] ranges (positions into vals)."""
+    ranges_view: this view's [tiles,2] ranges (positions into vals).
+    pix_err: optional per-pixel error e(u) [H,W]; then out["gauss_err"][g] is the
+    per-Gaussian rendering error E(g) = sum_u w(g, u) e(u) of Eq. 5."""
     P = W * H
     xy, conic, opac, rgb, depth = (_f64(rec["xy"]), _f64(rec["conic"]), _f64(rec["opacity"]),
                                    _f64(rec["rgb"]), _f64(rec["depth"]))
@@ -220,13 +222,22 @@ def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0)):
                n_contrib=np.zeros((H, W), np.int32), n_eval=np.zeros((H, W), np.int32),
                wsum=np.zeros((H, W)), fragile=np.zeros((H, W), np.int32),
                sig=np.zeros((H, W), np.uint64))
+    n = rec["xy"].shape[0]
+    pe = None
+    if pix_err is not None:
+        pe = _f64(np.asarray(pix_err, np.float64).reshape(H, W))
+        out["gauss_err"] = np.zeros(max(n, 1))
     lib().orc_render_fwd(W, H, _ptr(xy, np.float64), _ptr(conic, np.float64),
                          _ptr(opac, np.float64), _ptr(rgb, np.float64), _ptr(depth, np.float64),
                          _ptr(vals, np.uint32), _ptr(rv, np.uint32), _ptr(bgv, np.float64),
                          _ptr(out["rgb"], np.float64), _ptr(out["depth"], np.float64),
                          _ptr(out["T"], np.float64), _ptr(out["n_contrib"], np.int32),
                          _ptr(out["n_eval"], np.int32), _ptr(out["wsum"], np.float64),
-                         _ptr(out["fragile"], np.int32), _ptr(out["sig"], np.uint64))
+                         _ptr(out["fragile"], np.int32), _ptr(out["sig"], np.uint64),
+                         _ptr(pe, np.float64) if pe is not None else None,
+                         _ptr(out["gauss_err"], np.float64) if pe is not None else None)
+    if pe is not None:
+        out["gauss_err"] = out["gauss_err"][:n]
     del P
     return out
 
@@ -324,10 +335,42 @@ def loss_l1(rgb, target_rgb, depth=None, target_depth=None, lambda_depth=0.0):
 
 
 # ---------------------------------------------------------------------------
+# Active set of the global stage (Section III-B2): E_t = {g : max_k E_k(g) > eps}
+# with E_k(g) the per-Gaussian rendering error of Eq. 5 in keyframe k, united
+# with the newly inserted Gaussians (A_t = M~_t u E_t).
+# ---------------------------------------------------------------------------
+def pixel_error(rgb, target_rgb):
+    """Per-pixel error e(u) = |R(u) - C(u)| of Eq. 5, read as the mean over the
+    three colour channels of the absolute difference (the L1 loss's per-pixel
+    term).  rgb, target_rgb: [3, H, W]."""
+    return np.abs(np.asarray(rgb, np.float64) - np.asarray(target_rgb, np.float64)).mean(axis=0)
+
+
+def active_set(gauss_err, eps, force=None):
+    """gauss_err: [K, n] E_k(g) over the window's keyframes.  Returns the boolean
+    mask max_k E_k(g) > eps (strict), or-ed with `force` (the inserted
+    Gaussians), and the ascending list of its indices."""
+    e = np.asarray(gauss_err, np.float64)
+    act = e.max(axis=0) > eps if e.shape[0] > 0 else np.zeros(e.shape[1], bool)
+    if force is not None:
+        act = act | np.asarray(force, bool)
+    return act, np.nonzero(act)[0].astype(np.uint32)
+
+
+def mask_grad2d(g2d, active):
+    """The 2-D record gradients of an active-set backward: rows of inactive
+    Gaussians are zero, rows of active ones are the full backward's."""
+    a = np.asarray(active, bool)
+    return {k: np.where(a.reshape((-1,) + (1,) * (np.ndim(v) - 1)), v, 0.0) for k, v in g2d.items()}
+
+
+# ---------------------------------------------------------------------------
 # Whole chain over views (steps 1-7), FP64, binning in binary32.
 # ---------------------------------------------------------------------------
-def render_views(g, cams, bg=(0.0, 0.0, 0.0)):
-    """Forward over all views.  Returns (per-view outputs, projections, binning)."""
+def render_views(g, cams, bg=(0.0, 0.0, 0.0), pix_errs=None):
+    """Forward over all views.  Returns (per-view outputs, projections, binning).
+    pix_errs: optional list over views of per-pixel errors e(u) [H,W]; each
+    view's output then carries gauss_err (E_k(g) of Eq. 5)."""
     V = len(cams)
     projs = [project(g, cam) for cam in cams]
     sizes = [(int(c["W"]), int(c["H"])) for c in cams]
@@ -342,7 +385,8 @@ def render_views(g, cams, bg=(0.0, 0.0, 0.0)):
         nt = tiles_of(W, H)
         rec = dict(xy=projs[v]["xy"], conic=projs[v]["conic"], opacity=projs[v]["opacity"],
                    rgb=projs[v]["rgb"], depth=projs[v]["depth"])
-        outs.append(render_fwd(W, H, rec, b["vals"], b["ranges"][base:base + nt], bg))
+        outs.append(render_fwd(W, H, rec, b["vals"], b["ranges"][base:base + nt], bg,
+                               None if pix_errs is None else pix_errs[v]))
         base += nt
     return outs, projs, b
 

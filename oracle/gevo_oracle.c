@@ -398,8 +398,13 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
                     const double* rgb, const double* depth,
                     const uint32_t* vals, const uint32_t* ranges, const double* bg,
                     double* out_rgb, double* out_depth, double* out_T, int32_t* n_contrib,
-                    int32_t* n_eval, double* wsum, int32_t* fragile, uint64_t* sig)
+                    int32_t* n_eval, double* wsum, int32_t* fragile, uint64_t* sig,
+                    const double* pix_err, double* gauss_err)
 {
+    /* pix_err / gauss_err (both NULL or both set): the per-Gaussian rendering
+     * error of Section III-B2 (Eq. 5), E(g) += w(g, u) e(u) summed over the
+     * pixels u, w(g, u) the blending weight alpha T of g at u and e(u) the
+     * per-pixel error; gauss_err is indexed by Gaussian id. */
     const int32_t tiles_x = (W + ORC_TILE - 1) / ORC_TILE;
     const size_t P = (size_t)W * H;
     for (int32_t py = 0; py < H; py++)
@@ -428,6 +433,7 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
                 if (fabs(Tn - ORC_T_STOP) <= 1e-3 * ORC_T_STOP) frag = 1;
                 if (Tn < ORC_T_STOP) { h = mix64(h, 0xFFFFFFFF00000000ULL | (i - s)); break; }
                 const double w = alpha * T;
+                if (gauss_err) gauss_err[g] += w * pix_err[pix];
                 for (int ch = 0; ch < 3; ch++) C[ch] += w * rgb[3*g+ch];
                 Dd += w * depth[g];
                 ws += w;
