@@ -285,6 +285,8 @@ def main():
     plain_line = {"evals_per_s": (E_fwd + E_bwd) / (pms / 1e3), "views_per_s": V / (pms / 1e3),
                   "ms_per_step": pms}
 
+    active_line = active_set_section(rep, target_rgb, target_depth, flush, stage_ms)
+
     # ---- rooflines (algorithmic work per launch / live event time) ---------------------
     pk = peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -337,7 +339,7 @@ def main():
             "plain": plain_line, "speedup_vs_plain": value / plain_line["evals_per_s"],
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": None, "roofline": roof, "clocks": clk,
+            "gpu_launches": None, "roofline": roof, "clocks": clk, "active_set": active_line,
             "wall_s_timed": wall1 - wall0}
     line["gpu_launches"] = launches_per_step(rep) * args.steps
 
@@ -349,6 +351,75 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def active_set_section(rep, target_rgb, target_depth, flush, stage_ms, reps=10):
+    """The active-set path of the global stage (Section III-B2) on the same
+    workload: the loss with the per-pixel error, the reverse walk accumulating
+    E_k(g) (Eq. 5), the active set at the threshold that keeps the 15% of the
+    Gaussians the views see with the highest error (Section IV-C reports active
+    sets under 15% of the map; in this dense synthetic room most Gaussians are
+    hidden from every view and never blended, so a share of the whole map would
+    keep every visible one), and the masked reverse walk and projection backward,
+    each timed alone (CUDA events, L2 flushed before each launch)."""
+    import torch
+
+    from paper_2409_09295_gb300 import _abi
+    pipe = rep.pipe
+    pipe.alloc_active()
+    tb = rep.tuning_bwd
+
+    def timed(fn, before=None):
+        """Mean device time of fn captured in a CUDA graph (no host work inside
+        the timed region)."""
+        for _ in range(2):
+            if before:
+                before()
+            fn()
+        torch.cuda.synchronize()
+        gph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gph):
+            fn()
+        ms = 0.0
+        for _ in range(reps):
+            if before:
+                before()
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            gph.replay()
+            e.record()
+            e.synchronize()
+            ms += s.elapsed_time(e)
+        return ms / reps
+
+    def walk(error, masked):
+        _abi.gevo_render_bwd_active(
+            pipe.layout, pipe.n, pipe.proj, pipe.vals, pipe.ranges, rep.bg, pipe.T_final,
+            pipe.n_contrib, pipe.dL_drgb, pipe.dL_ddepth, None,
+            pipe.pix_err if error else None, pipe.gauss_err if error else None,
+            pipe.active if masked else None, pipe.grad2d, pipe.ws, tb)
+
+    rep.replay()
+    ms = {"loss_err": timed(lambda: pipe.loss_l1_err(target_rgb, target_depth, 1.0))}
+    ms["render_bwd_full"] = timed(lambda: walk(False, False), before=pipe.grad2d_zero)
+    ms["render_bwd_error"] = timed(lambda: walk(True, False),
+                                   before=lambda: (pipe.grad2d_zero(), pipe.gauss_err.zero_()))
+    N = pipe.n
+    emax = pipe.gauss_err.view(pipe.V, N).max(dim=0).values.float().cpu()
+    seen = emax[emax > 0]            # Gaussians that some keyframe blends at all
+    eps = float(torch.kthvalue(seen, max(1, int(0.85 * seen.numel()))).values) if seen.numel() else 0.0
+    ms["active_set"] = timed(lambda: pipe.active_set(eps))
+    active = int(pipe.active_counts[0].item())
+    ms["render_bwd_masked"] = timed(lambda: walk(False, True), before=pipe.grad2d_zero)
+    ms["project_bwd_masked"] = timed(lambda: pipe.project_bwd_active(rep.g, rep.camt))
+    full = ms["render_bwd_full"] + stage_ms["project_bwd"]
+    masked = ms["render_bwd_masked"] + ms["project_bwd_masked"]
+    return {"active": active, "frac": active / N, "seen": int(seen.numel()), "eps": eps, "ms": ms,
+            "full_ms": {"render_bwd": stage_ms["render_bwd"], "project_bwd": stage_ms["project_bwd"]},
+            "backward_speedup": full / masked,
+            "note": "E_k from the step's own render vs the stop-gradient targets; eps = 85th "
+                    "percentile of max_k E_k(g) over the Gaussians some view blends (seen)"}
 
 
 def launches_per_step(rep) -> int:

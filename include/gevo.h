@@ -303,6 +303,78 @@ gevo_status gevo_loss_l1(const gevo_layout* layout, const float* rgb, const floa
                          void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Active set of the global stage (Section III-B2, Eq. 5)                   */
+/* ---------------------------------------------------------------------- */
+/* The global stage optimises only an active subset A_t = M~_t u E_t of the
+ * map: the newly inserted Gaussians and E_t = {g : max_k E_k(g) > eps} over
+ * the window's keyframes k, with the per-Gaussian rendering error
+ *     E_k(g) = sum_u w(g, u) e_k(u),
+ * w(g, u) = alpha T the blending weight of g at pixel u and e_k(u) the
+ * per-pixel error |R - C_k|(u), read as the mean over the three colour
+ * channels of the absolute difference.  Section IV-C states the active set
+ * holds under 15% of the map and that a rasterizer specialised to it would cut
+ * latency; these four calls are that path. */
+
+/* gevo_loss_l1 plus the per-pixel error: pix_err[pix_base[v] + p] =
+ * (|dr| + |dg| + |db|) / 3 of rgb - target_rgb (DEVICE float[total_pixels],
+ * written).  Same loss and gradients as gevo_loss_l1. */
+gevo_status gevo_loss_l1_err(const gevo_layout* layout, const float* rgb,
+                             const float* target_rgb, const float* depth,
+                             const float* target_depth, float lambda_depth, float* dL_drgb,
+                             float* dL_ddepth, float* loss, float* pix_err, void* workspace,
+                             void* stream);
+
+/* gevo_render_bwd with two optional additions, fused into the same reverse
+ * walk (one kernel):
+ *  - pix_err != NULL (DEVICE float[total_pixels], e.g. from gevo_loss_l1_err):
+ *    gauss_err[v * n + g] += sum over view v's pixels u of w(g, u) pix_err[u]
+ *    (E_k(g) of Eq. 5; DEVICE float[n_views * n], accumulated -- clear it
+ *    first; rows of culled entries are never touched).  gauss_err must be
+ *    non-NULL iff pix_err is.
+ *  - active != NULL (DEVICE uint32[(n + 31) / 32], bit g % 32 of word g / 32
+ *    set = Gaussian g active): rows of *out of inactive Gaussians are not
+ *    touched; active rows get exactly what gevo_render_bwd gives them (the
+ *    inactive Gaussians still occlude and are still blended).  Inactive list
+ *    entries only recover T and the suffix colour, so the walk costs less in
+ *    proportion to the inactive share.  An all-zero mask with pix_err gives
+ *    the error pass alone.
+ * Everything else as gevo_render_bwd. */
+gevo_status gevo_render_bwd_active(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                                   const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                                   const float* T_final, const uint32_t* n_contrib,
+                                   const float* dL_drgb, const float* dL_ddepth,
+                                   const float* dL_dT, const float* pix_err, float* gauss_err,
+                                   const uint32_t* active, gevo_grad2d* out,
+                                   const gevo_tuning* tuning, void* workspace, void* stream);
+
+/* Words of the `counts` argument of gevo_active_set for n Gaussians. */
+#define GEVO_ACTIVE_COUNT_WORDS(n) (((size_t)(n) + 1023) / 1024 + 1)
+
+/* Active set: Gaussian g is active iff gauss_err[k * n + g] > eps for some
+ * k < n_views (strict), or bit g of `force` is set (force: DEVICE
+ * uint32[(n + 31) / 32] or NULL -- the newly inserted Gaussians).  Writes
+ * active (DEVICE uint32[(n + 31) / 32], the bit mask; bits >= n are 0),
+ * active_list (DEVICE uint32[n]: the active indices in ascending order in
+ * its first counts[0] entries) and counts (DEVICE uint32
+ * [GEVO_ACTIVE_COUNT_WORDS(n)]: counts[0] = number of active Gaussians, the
+ * rest scratch).  Three kernels, no host synchronisation. */
+gevo_status gevo_active_set(int32_t n_views, int32_t n, const float* gauss_err, float eps,
+                            const uint32_t* force, uint32_t* active, uint32_t* active_list,
+                            uint32_t* counts, void* stream);
+
+/* gevo_project_bwd restricted to the Gaussians active_list[0 .. counts[0])
+ * (the outputs of gevo_active_set): their rows of *out are written exactly as
+ * gevo_project_bwd writes them; other rows are not touched.  dxi (nullable)
+ * is the pose gradient through the listed Gaussians only: with a grad2d from
+ * gevo_render_bwd_active, the derivative with the inactive Gaussians' records
+ * held fixed. */
+gevo_status gevo_project_bwd_active(const gevo_layout* layout, const gevo_gaussians* g,
+                                    const gevo_camera* cams, const gevo_proj* proj,
+                                    const gevo_grad2d* grad2d, const uint32_t* active_list,
+                                    const uint32_t* counts, gevo_gaussian_grads* out, float* dxi,
+                                    void* workspace, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Learned depth prior (spec addition; the paper initialises new      */
 /* Gaussians from a cost volume + belief propagation, Section III-A)        */
 /* ---------------------------------------------------------------------- */

@@ -70,7 +70,8 @@ class Tuning(ctypes.Structure):
 EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin_sort",
            "gevo_render_fwd", "gevo_render_bwd", "gevo_project_bwd", "gevo_loss_l1",
            "gevo_last_error", "gevo_status_str", "gevo_version", "gevo_bin_sort_noalloc",
-           "gevo_grad2d_zero", "gevo_gemm_bf16"]
+           "gevo_grad2d_zero", "gevo_gemm_bf16", "gevo_loss_l1_err", "gevo_render_bwd_active",
+           "gevo_active_set", "gevo_project_bwd_active"]
 
 # Every symbol include/gevo_prior.h declares, with its argument kinds
 # (i: int32, u: uint32, I: int64, f: float, p: pointer; the last p is the stream).
@@ -135,6 +136,12 @@ def load(build_if_missing: bool = True):
     L.gevo_project_bwd.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d),
                                    P(GaussianGrads), vp, vp, vp]
     L.gevo_loss_l1.argtypes = [P(Layout), vp, vp, vp, vp, f32, vp, vp, vp, vp, vp]
+    L.gevo_loss_l1_err.argtypes = [P(Layout), vp, vp, vp, vp, f32, vp, vp, vp, vp, vp, vp]
+    L.gevo_render_bwd_active.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp,
+                                         vp, vp, vp, vp, P(Grad2d), P(Tuning), vp, vp]
+    L.gevo_active_set.argtypes = [i32, i32, vp, f32, vp, vp, vp, vp, vp]
+    L.gevo_project_bwd_active.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d), vp, vp,
+                                          P(GaussianGrads), vp, vp, vp]
     L.gevo_last_error.argtypes = [vp, vp]
     L.gevo_status_str.argtypes = [ctypes.c_int]
     L.gevo_status_str.restype = ctypes.c_char_p
@@ -145,7 +152,8 @@ def load(build_if_missing: bool = True):
         getattr(L, name).argtypes = [kinds[c] for c in sig]
         getattr(L, name).restype = ctypes.c_int
     for name in ("gevo_project", "gevo_bin_sort", "gevo_render_fwd", "gevo_render_bwd",
-                 "gevo_project_bwd", "gevo_loss_l1", "gevo_last_error"):
+                 "gevo_project_bwd", "gevo_loss_l1", "gevo_last_error", "gevo_loss_l1_err",
+                 "gevo_render_bwd_active", "gevo_active_set", "gevo_project_bwd_active"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -271,6 +279,31 @@ def gevo_render_bwd(layout, n, proj: dict, vals, ranges, bg, T_final, n_contrib,
         ctypes.byref(tu) if tu is not None else None, _p(ws), _stream(stream)))
 
 
+def gevo_render_bwd_active(layout, n, proj: dict, vals, ranges, bg, T_final, n_contrib, dL_drgb,
+                           dL_ddepth, dL_dT, pix_err, gauss_err, active, grad2d: dict, ws,
+                           tuning=None, stream=None):
+    P_ = proj_struct(proj)
+    G2 = grad2d_struct(grad2d)
+    bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    tu = tuning_struct(tuning)
+    _check("gevo_render_bwd_active", load().gevo_render_bwd_active(
+        ctypes.byref(layout), int(n), ctypes.byref(P_), _p(vals), _p(ranges), bgv, _p(T_final),
+        _p(n_contrib), _p(dL_drgb), _p(dL_ddepth), _p(dL_dT), _p(pix_err), _p(gauss_err),
+        _p(active), ctypes.byref(G2), ctypes.byref(tu) if tu is not None else None, _p(ws),
+        _stream(stream)))
+
+
+def gevo_active_set(n_views, n, gauss_err, eps, force, active, active_list, counts, stream=None):
+    _check("gevo_active_set", load().gevo_active_set(
+        int(n_views), int(n), _p(gauss_err), float(eps), _p(force), _p(active), _p(active_list),
+        _p(counts), _stream(stream)))
+
+
+def active_count_words(n: int) -> int:
+    """GEVO_ACTIVE_COUNT_WORDS(n) of include/gevo.h."""
+    return (int(n) + 1023) // 1024 + 1
+
+
 def gevo_grad2d_zero(layout, n, proj: dict, grad2d: dict, stream=None):
     P_ = proj_struct(proj)
     G2 = grad2d_struct(grad2d)
@@ -292,6 +325,29 @@ def gevo_project_bwd(layout, g: dict, cams, proj: dict, grad2d: dict, out: dict,
     _check("gevo_project_bwd", load().gevo_project_bwd(
         ctypes.byref(layout), ctypes.byref(G), _p(cams), ctypes.byref(P_), ctypes.byref(G2),
         ctypes.byref(O), _p(dxi), _p(ws), _stream(stream)))
+
+
+def gevo_project_bwd_active(layout, g: dict, cams, proj: dict, grad2d: dict, active_list, counts,
+                            out: dict, dxi, ws, stream=None):
+    G = gaussians_struct(g)
+    P_ = proj_struct(proj)
+    G2 = grad2d_struct(grad2d)
+    O = GaussianGrads()
+    O.means, O.scales, O.quats, O.opacities = (_p(out["means"]), _p(out["scales"]),
+                                               _p(out["quats"]), _p(out["opacities"]))
+    O.sh = _p(out.get("sh"))
+    O.rgb = _p(out.get("rgb"))
+    _check("gevo_project_bwd_active", load().gevo_project_bwd_active(
+        ctypes.byref(layout), ctypes.byref(G), _p(cams), ctypes.byref(P_), ctypes.byref(G2),
+        _p(active_list), _p(counts), ctypes.byref(O), _p(dxi), _p(ws), _stream(stream)))
+
+
+def gevo_loss_l1_err(layout, rgb, target_rgb, depth, target_depth, lambda_depth, dL_drgb,
+                     dL_ddepth, loss, pix_err, ws=None, stream=None):
+    _check("gevo_loss_l1_err", load().gevo_loss_l1_err(
+        ctypes.byref(layout), _p(rgb), _p(target_rgb), _p(depth), _p(target_depth),
+        float(lambda_depth), _p(dL_drgb), _p(dL_ddepth), _p(loss), _p(pix_err), _p(ws),
+        _stream(stream)))
 
 
 def gevo_loss_l1(layout, rgb, target_rgb, depth, target_depth, lambda_depth, dL_drgb, dL_ddepth,

@@ -77,6 +77,51 @@ k_loss_l1(gevo_layout L, const float4* __restrict__ rgb, const float4* __restric
     }
 }
 
+// The same loss with the per-pixel error e(u) = (|dr| + |dg| + |db|) / 3 of the
+// rendering-error criterion (Section III-B2, Eq. 5): one thread per pixel reads
+// its three channels, so e(u) needs no second pass.
+__global__ void __launch_bounds__(256)
+k_loss_l1_err(gevo_layout L, const float* __restrict__ rgb, const float* __restrict__ trgb,
+              const float* __restrict__ d, const float* __restrict__ td, float lambda,
+              float* __restrict__ g_rgb, float* __restrict__ g_d, float* __restrict__ loss,
+              float* __restrict__ pix_err)
+{
+    const int v = blockIdx.y;
+    const size_t P = (size_t)L.width[v] * L.height[v];
+    const size_t base = (size_t)L.pix_base[v];
+    const float sc = 1.f / (3.f * (float)P);
+    const float sd = lambda / (float)P;
+    const float* a = rgb + 3 * base;
+    const float* b = trgb + 3 * base;
+    float* g = g_rgb + 3 * base;
+    float acc = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < P;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float e0 = a[i] - b[i], e1 = a[P + i] - b[P + i], e2 = a[2 * P + i] - b[2 * P + i];
+        const float s = fabsf(e0) + fabsf(e1) + fabsf(e2);
+        acc += sc * s;
+        g[i] = sc * (float)((e0 > 0.f) - (e0 < 0.f));
+        g[P + i] = sc * (float)((e1 > 0.f) - (e1 < 0.f));
+        g[2 * P + i] = sc * (float)((e2 > 0.f) - (e2 < 0.f));
+        pix_err[base + i] = s * (1.f / 3.f);
+        if (lambda != 0.f) {
+            const float e = d[base + i] - td[base + i];
+            acc += sd * fabsf(e);
+            g_d[base + i] = sd * (float)((e > 0.f) - (e < 0.f));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float s_acc[8];
+    if ((threadIdx.x & 31) == 0) s_acc[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_acc[w];
+        atomicAdd(loss + v, t);
+    }
+}
+
 }  // namespace gevo
 
 using namespace gevo;
@@ -110,6 +155,30 @@ extern "C" gevo_status gevo_loss_l1(const gevo_layout* layout, const float* rgb,
         reinterpret_cast<const float4*>(depth), reinterpret_cast<const float4*>(target_depth),
         lambda_depth, reinterpret_cast<float4*>(dL_drgb), reinterpret_cast<float4*>(dL_ddepth), loss,
         vec_ok);
+    GEVO_CHECK_LAUNCH();
+    return GEVO_OK;
+}
+
+extern "C" gevo_status gevo_loss_l1_err(const gevo_layout* layout, const float* rgb,
+                                        const float* target_rgb, const float* depth,
+                                        const float* target_depth, float lambda_depth,
+                                        float* dL_drgb, float* dL_ddepth, float* loss,
+                                        float* pix_err, void* workspace, void* stream)
+{
+    (void)workspace;
+    if (!layout || layout->n_views < 1 || !rgb || !target_rgb || !dL_drgb || !loss || !pix_err)
+        return GEVO_ERR_INVALID;
+    if (lambda_depth != 0.f && (!depth || !target_depth || !dL_ddepth)) return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(loss, 0, sizeof(float) * layout->n_views, st) != cudaSuccess)
+        return GEVO_ERR_CUDA;
+    int64_t maxP = 0;
+    for (int v = 0; v < layout->n_views; v++)
+        maxP = std::max(maxP, (int64_t)layout->width[v] * layout->height[v]);
+    const int bx = (int)std::min<int64_t>((maxP + 255) / 256, (int64_t)sm_count() * 4);
+    dim3 grid(bx, layout->n_views);
+    k_loss_l1_err<<<grid, 256, 0, st>>>(*layout, rgb, target_rgb, depth, target_depth, lambda_depth,
+                                        dL_drgb, dL_ddepth, loss, pix_err);
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }

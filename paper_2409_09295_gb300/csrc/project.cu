@@ -305,14 +305,18 @@ k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
                   const float2* __restrict__ g_xy, const float4* __restrict__ g_co,
                   const float4* __restrict__ g_rz, float* __restrict__ d_means,
                   float* __restrict__ d_scales, float4* __restrict__ d_quats,
-                  float* __restrict__ d_opac, float* __restrict__ d_rgb, float* __restrict__ dxi)
+                  float* __restrict__ d_opac, float* __restrict__ d_rgb, float* __restrict__ dxi,
+                  const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count)
 {
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
     __shared__ float s_dxi[GEVO_MAX_VIEWS][6];
+    const int total = list ? (int)*list_count : n;
+    if ((int)(blockIdx.x * blockDim.x) >= total) return;   // whole block: before any barrier
     load_cams(L, cams, s_cam);
     for (int i = threadIdx.x; i < L.n_views * 6; i += blockDim.x) (&s_dxi[0][0])[i] = 0.f;
     __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = t < total ? (list ? (int)list[t] : t) : n;
     if (g < n) {
         const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
         const float s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
@@ -458,15 +462,19 @@ __global__ void __launch_bounds__(128)
 k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
                   const float* __restrict__ coef, const gevo_camera* __restrict__ cams,
                   const int* __restrict__ radius, const float4* __restrict__ g_rz,
-                  float* __restrict__ d_means, float* __restrict__ d_coef, float* __restrict__ dxi)
+                  float* __restrict__ d_means, float* __restrict__ d_coef, float* __restrict__ dxi,
+                  const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
     __shared__ float s_dxi[GEVO_MAX_VIEWS][3];
+    const int total = list ? (int)*list_count : n;
+    if ((int)(blockIdx.x * blockDim.x) >= total) return;   // whole block: before any barrier
     load_cams(L, cams, s_cam);
     for (int i = threadIdx.x; i < L.n_views * 3; i += blockDim.x) (&s_dxi[0][0])[i] = 0.f;
     __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = t < total ? (list ? (int)list[t] : t) : n;
     if (g < n) {
         const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
         float k[16][3];
@@ -558,7 +566,8 @@ static void launch_fwd(const gevo_layout& L, const gevo_gaussians& g, const gevo
 template <int DEG, bool RGB>
 static void launch_bwd(const gevo_layout& L, const gevo_gaussians& g, const gevo_camera* cams,
                        const gevo_proj& o, const gevo_grad2d& gr, const gevo_gaussian_grads& out,
-                       float* dxi, cudaStream_t st)
+                       float* dxi, cudaStream_t st, const uint32_t* list = nullptr,
+                       const uint32_t* list_count = nullptr)
 {
     const int threads = 128;
     const int blocks = (g.n + threads - 1) / threads;
@@ -566,11 +575,11 @@ static void launch_bwd(const gevo_layout& L, const gevo_gaussians& g, const gevo
         L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), cams, o.radius,
         reinterpret_cast<const float2*>(gr.xy), reinterpret_cast<const float4*>(gr.conic_opacity),
         reinterpret_cast<const float4*>(gr.rgb_depth), out.means, out.scales,
-        reinterpret_cast<float4*>(out.quats), out.opacities, out.rgb, dxi);
+        reinterpret_cast<float4*>(out.quats), out.opacities, out.rgb, dxi, list, list_count);
     if (!RGB)
         k_project_bwd_col<DEG><<<blocks, threads, 0, st>>>(
             L, g.n, g.means, g.sh, cams, o.radius, reinterpret_cast<const float4*>(gr.rgb_depth),
-            out.means, out.sh, dxi);
+            out.means, out.sh, dxi, list, list_count);
 }
 
 static bool valid_gaussians(const gevo_gaussians* g)
@@ -618,10 +627,11 @@ extern "C" gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussi
     return GEVO_OK;
 }
 
-extern "C" gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
-                                        const gevo_camera* cams, const gevo_proj* proj,
-                                        const gevo_grad2d* grad2d, gevo_gaussian_grads* out,
-                                        float* dxi, void* workspace, void* stream)
+static gevo_status project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
+                               const gevo_camera* cams, const gevo_proj* proj,
+                               const gevo_grad2d* grad2d, gevo_gaussian_grads* out, float* dxi,
+                               void* workspace, void* stream, const uint32_t* list,
+                               const uint32_t* list_count)
 {
     if (!layout || layout->n_views < 1 || !valid_gaussians(g) || !cams || !proj || !proj->radius ||
         !grad2d || !grad2d->xy || !grad2d->conic_opacity || !grad2d->rgb_depth || !out ||
@@ -638,16 +648,37 @@ extern "C" gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_ga
     if (dxi && cudaMemsetAsync(dxi, 0, sizeof(float) * 6 * layout->n_views, st) != cudaSuccess)
         return GEVO_ERR_CUDA;
     if (g->n == 0) return GEVO_OK;
+    const gevo_layout& L = *layout;
     if (g->rgb) {
-        launch_bwd<0, true>(*layout, *g, cams, *proj, *grad2d, *out, dxi, st);
+        launch_bwd<0, true>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count);
     } else {
         switch (g->sh_degree) {
-        case 0: launch_bwd<0, false>(*layout, *g, cams, *proj, *grad2d, *out, dxi, st); break;
-        case 1: launch_bwd<1, false>(*layout, *g, cams, *proj, *grad2d, *out, dxi, st); break;
-        case 2: launch_bwd<2, false>(*layout, *g, cams, *proj, *grad2d, *out, dxi, st); break;
-        default: launch_bwd<3, false>(*layout, *g, cams, *proj, *grad2d, *out, dxi, st); break;
+        case 0: launch_bwd<0, false>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count); break;
+        case 1: launch_bwd<1, false>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count); break;
+        case 2: launch_bwd<2, false>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count); break;
+        default: launch_bwd<3, false>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count); break;
         }
     }
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
+}
+
+extern "C" gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
+                                        const gevo_camera* cams, const gevo_proj* proj,
+                                        const gevo_grad2d* grad2d, gevo_gaussian_grads* out,
+                                        float* dxi, void* workspace, void* stream)
+{
+    return project_bwd(layout, g, cams, proj, grad2d, out, dxi, workspace, stream, nullptr, nullptr);
+}
+
+extern "C" gevo_status gevo_project_bwd_active(const gevo_layout* layout, const gevo_gaussians* g,
+                                               const gevo_camera* cams, const gevo_proj* proj,
+                                               const gevo_grad2d* grad2d,
+                                               const uint32_t* active_list, const uint32_t* counts,
+                                               gevo_gaussian_grads* out, float* dxi,
+                                               void* workspace, void* stream)
+{
+    if (!active_list || !counts) return GEVO_ERR_INVALID;
+    return project_bwd(layout, g, cams, proj, grad2d, out, dxi, workspace, stream, active_list,
+                       counts);
 }

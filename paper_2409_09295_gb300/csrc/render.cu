@@ -270,7 +270,49 @@ __device__ __forceinline__ float warp_reduce10(const float v[10], int& slot)
     return x;
 }
 
-template <int PPT, bool DD, bool DT>
+// The same transpose-reduction for 11 values (the 10 gradient sums and the
+// error weight of Eq. 5) padded to 12: 13 shuffles.  Slot (h16 ? 6 : 0) +
+// (h8 ? 3 : 0) + local on the even lanes with local < 3.
+__device__ __forceinline__ float warp_reduce12(const float v[12], int& slot)
+{
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+    float r[6];
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        const float keep = h16 ? v[6 + i] : v[i];
+        const float send = h16 ? v[i] : v[6 + i];
+        r[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float q[4];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float keep = h8 ? r[3 + i] : r[i];
+        const float send = h8 ? r[i] : r[3 + i];
+        q[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    q[3] = 0.f;
+    float u[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const float keep = h4 ? q[2 + i] : q[i];
+        const float send = h4 ? q[i] : q[2 + i];
+        u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    const float keep = h2 ? u[1] : u[0];
+    const float send = h2 ? u[0] : u[1];
+    float x = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    const int local = (h4 ? 2 : 0) + (h2 ? 1 : 0);
+    const bool valid = !(lane & 1) && local < 3;
+    slot = valid ? (h16 ? 6 : 0) + (h8 ? 3 : 0) + local : -1;
+    return x;
+}
+
+// EXT adds the per-Gaussian error of Eq. 5 (pix_err -> gauss_err) and the
+// active-set mask: inactive entries (a warp-uniform property, the entry is the
+// same for the whole warp) only recover T and the suffix colour.
+template <int PPT, bool DD, bool DT, bool EXT>
 __global__ void __launch_bounds__(256 / PPT)
 k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
              const float4* __restrict__ rz, const uint32_t* __restrict__ vals,
@@ -279,7 +321,8 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
              const float* __restrict__ dL_drgb, const float* __restrict__ dL_dd,
              const float* __restrict__ dL_dT, float2* __restrict__ g_xy, float4* __restrict__ g_co,
              float4* __restrict__ g_rz, const uint32_t* __restrict__ order, uint32_t* queue,
-             int n_items)
+             int n_items, const float* __restrict__ pix_err, float* __restrict__ gauss_err,
+             const uint32_t* __restrict__ active)
 {
     constexpr int NT = 256 / PPT;
     constexpr int NW = NT / 32;
@@ -288,7 +331,8 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     __shared__ float4 s_rz[kBatch];
     __shared__ float4 s_box[kBatch];
     __shared__ uint32_t s_id[kBatch];
-    __shared__ float s_g[kBatch][10];
+    constexpr int NG = EXT ? 11 : 10;   // per-entry sums: 10 gradients (+ the error weight)
+    __shared__ float s_g[kBatch][NG];
     __shared__ uint32_t s_item;
     __shared__ uint32_t s_max[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -320,7 +364,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
         const float fpx = (float)px;
 
         float T[PPT], S0[PPT], S1[PPT], S2[PPT], SD[PPT];
-        float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gTT[PPT];
+        float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gTT[PPT], pe[PPT];
         uint32_t last[PPT];
         uint32_t mymax = 0;
 #pragma unroll
@@ -336,9 +380,10 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 gC0[k] = g3[pix]; gC1[k] = g3[P + pix]; gC2[k] = g3[2 * P + pix];
                 gD[k] = DD ? dL_dd[gp] : 0.f;
                 gTT[k] = DT ? dL_dT[gp] * T[k] : 0.f;
+                pe[k] = (EXT && pix_err) ? pix_err[gp] : 0.f;
             } else {
                 T[k] = 1.f; last[k] = 0u;
-                gC0[k] = gC1[k] = gC2[k] = gD[k] = gTT[k] = 0.f;
+                gC0[k] = gC1[k] = gC2[k] = gD[k] = gTT[k] = pe[k] = 0.f;
             }
             mymax = max(mymax, last[k]);
         }
@@ -360,13 +405,15 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 const size_t gid = vbase + id;
                 const float2 m = xy[gid];
                 const float4 c = co[gid];
-                s_id[j] = id;
+                // ids are < 2^31 (n is an int32): the top bit marks inactive entries
+                const bool inactive = EXT && active && !((__ldg(active + (id >> 5)) >> (id & 31)) & 1u);
+                s_id[j] = id | (inactive ? 0x80000000u : 0u);
                 s_xy[j] = m;
                 s_co[j] = prescale(c);
                 s_rz[j] = rz[gid];
                 s_box[j] = alpha_box(m, c);
 #pragma unroll
-                for (int q = 0; q < 10; q++) s_g[j][q] = 0.f;
+                for (int q = 0; q < NG; q++) s_g[j][q] = 0.f;
             }
             __syncthreads();
             const float wx0 = (float)x0, wx1 = (float)(x0 + kTile - 1);
@@ -396,8 +443,32 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 }
                 if (!__any_sync(0xffffffffu, any)) continue;
                 const float4 r = s_rz[j];
+                const bool act = !EXT || !(s_id[j] >> 31);
+                if (EXT && !act) {
+                    // inactive: transmittance and suffix colour only (+ the error weight)
+                    float a_e = 0.f;
+#pragma unroll
+                    for (int k = 0; k < PPT; k++) {
+                        if (!use[k]) continue;
+                        const float alpha = al[k];
+                        const float om = 1.f - alpha;
+                        const float Ti = T[k] * __frcp_rn(om);
+                        T[k] = Ti;
+                        a_e += alpha * Ti * pe[k];
+                        S0[k] = alpha * r.x + om * S0[k];
+                        S1[k] = alpha * r.y + om * S1[k];
+                        S2[k] = alpha * r.z + om * S2[k];
+                        if (DD) SD[k] = alpha * r.w + om * SD[k];
+                    }
+                    if (pix_err) {
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) a_e += __shfl_xor_sync(0xffffffffu, a_e, o);
+                        if ((threadIdx.x & 31) == 0 && a_e != 0.f) atomicAdd(&s_g[j][NG - 1], a_e);
+                    }
+                    continue;
+                }
                 float a_xy0 = 0.f, a_xy1 = 0.f, a_ca = 0.f, a_cb = 0.f, a_cc = 0.f, a_o = 0.f;
-                float a_r = 0.f, a_g = 0.f, a_b = 0.f, a_z = 0.f;
+                float a_r = 0.f, a_g = 0.f, a_b = 0.f, a_z = 0.f, a_e = 0.f;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     if (!use[k]) continue;
@@ -408,6 +479,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     const float Ti = T[k] * inv;
                     T[k] = Ti;
                     const float w = alpha * Ti;
+                    if (EXT) a_e += w * pe[k];
                     float dLda = gC0[k] * (r.x - S0[k]) + gC1[k] * (r.y - S1[k]) +
                                  gC2[k] * (r.z - S2[k]);
                     if (DD) dLda += gD[k] * (r.w - SD[k]);
@@ -430,7 +502,13 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                         a_xy1 += sc * (2.f * c.z * dy + c.y * dx);
                     }
                 }
-                {
+                if (EXT) {
+                    const float vals12[12] = {a_xy0, a_xy1, a_ca, a_cb, a_cc, a_o,
+                                              a_r,   a_g,   a_b,  a_z,  a_e,  0.f};
+                    int slot;
+                    const float tot = warp_reduce12(vals12, slot);
+                    if (slot >= 0 && slot < NG && tot != 0.f) atomicAdd(&s_g[j][slot], tot);
+                } else {
                     const float vals10[10] = {a_xy0, a_xy1, a_ca, a_cb, a_cc, a_o, a_r, a_g, a_b, a_z};
                     int slot;
                     const float tot = warp_reduce10(vals10, slot);
@@ -440,11 +518,13 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
             __syncthreads();
             for (int j = tid; j < nb; j += NT) {
                 const float* gg = s_g[j];
+                if (EXT && pix_err && gg[NG - 1] != 0.f)
+                    atomicAdd(gauss_err + vbase + (s_id[j] & 0x7FFFFFFFu), gg[NG - 1]);
                 bool nz = false;
 #pragma unroll
                 for (int q = 0; q < 10; q++) nz = nz || gg[q] != 0.f;
                 if (!nz) continue;
-                const size_t gid = vbase + s_id[j];
+                const size_t gid = vbase + (EXT ? (s_id[j] & 0x7FFFFFFFu) : s_id[j]);
                 atomicAdd(g_xy + gid, make_float2(gg[0], gg[1]));
                 atomicAdd(g_co + gid, make_float4(gg[2], gg[3], gg[4], gg[5]));
                 atomicAdd(g_rz + gid, make_float4(gg[6], gg[7], gg[8], gg[9]));
@@ -495,12 +575,20 @@ static gevo_status launch_fwd(const gevo_layout& L, int n, const gevo_proj& p, c
     return GEVO_OK;
 }
 
+template <int PPT, bool EXT>
+static auto pick_bwd(bool dd, bool dt)
+{
+    return dd ? (dt ? k_render_bwd<PPT, true, true, EXT> : k_render_bwd<PPT, true, false, EXT>)
+              : (dt ? k_render_bwd<PPT, false, true, EXT> : k_render_bwd<PPT, false, false, EXT>);
+}
+
 template <int PPT>
 static gevo_status launch_bwd(const gevo_layout& L, int n, const gevo_proj& p, const uint32_t* vals,
                               const uint32_t* ranges, const float* bg, const float* Tf,
                               const uint32_t* nc, const float* gC, const float* gD, const float* gT,
                               const gevo_grad2d& out, const gevo_tuning* t, char* ws,
-                              cudaStream_t st)
+                              cudaStream_t st, const float* pix_err = nullptr,
+                              float* gauss_err = nullptr, const uint32_t* active = nullptr)
 {
     const WsLayout w = ws_layout(L, n, 0);
     const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + w.tile_order);
@@ -509,16 +597,16 @@ static gevo_status launch_bwd(const gevo_layout& L, int n, const gevo_proj& p, c
     if (t && t->persistent) {
         queue = reinterpret_cast<uint32_t*>(ws + w.err) + kQueueBwd;
         if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GEVO_ERR_CUDA;
-        grid = std::min(grid, persistent_grid<PPT>(k_render_bwd<PPT, true, false>, t));
     }
-    auto kern = gD ? (gT ? k_render_bwd<PPT, true, true> : k_render_bwd<PPT, true, false>)
-                   : (gT ? k_render_bwd<PPT, false, true> : k_render_bwd<PPT, false, false>);
+    const bool ext = pix_err || active;
+    auto kern = ext ? pick_bwd<PPT, true>(gD, gT) : pick_bwd<PPT, false>(gD, gT);
+    if (queue) grid = std::min(grid, persistent_grid<PPT>(kern, t));
     kern<<<grid, 256 / PPT, 0, st>>>(
         L, n, reinterpret_cast<const float2*>(p.xy), reinterpret_cast<const float4*>(p.conic_opacity),
         reinterpret_cast<const float4*>(p.rgb_depth), vals, reinterpret_cast<const uint2*>(ranges),
         bg[0], bg[1], bg[2], Tf, nc, gC, gD, gT, reinterpret_cast<float2*>(out.xy),
         reinterpret_cast<float4*>(out.conic_opacity), reinterpret_cast<float4*>(out.rgb_depth),
-        order, queue, L.total_tiles);
+        order, queue, L.total_tiles, pix_err, gauss_err, active);
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }
@@ -580,6 +668,33 @@ extern "C" gevo_status gevo_render_bwd(const gevo_layout* layout, int32_t n, con
     case 4: return launch_bwd<4>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
     case 2: return launch_bwd<2>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
     default: return launch_bwd<1>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st);
+    }
+}
+
+extern "C" gevo_status gevo_render_bwd_active(const gevo_layout* layout, int32_t n,
+                                              const gevo_proj* proj, const uint32_t* vals,
+                                              const uint32_t* ranges, const float* bg,
+                                              const float* T_final, const uint32_t* n_contrib,
+                                              const float* dL_drgb, const float* dL_ddepth,
+                                              const float* dL_dT, const float* pix_err,
+                                              float* gauss_err, const uint32_t* active,
+                                              gevo_grad2d* out, const gevo_tuning* tuning,
+                                              void* workspace, void* stream)
+{
+    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+        !proj->rgb_depth || !proj->radius || !vals || !ranges || !bg || !T_final || !n_contrib ||
+        !dL_drgb || !out || !out->xy || !out->conic_opacity || !out->rgb_depth || !workspace ||
+        !gevo_aligned(workspace, 256) || !valid_tuning(tuning) || !gevo_aligned(ranges, 8) ||
+        !gevo_aligned(out->conic_opacity, 16) || !gevo_aligned(out->rgb_depth, 16) ||
+        !gevo_aligned(out->xy, 8) || (pix_err == nullptr) != (gauss_err == nullptr))
+        return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = reinterpret_cast<char*>(workspace);
+    switch (pick_ppt(tuning)) {
+    case 8: return launch_bwd<8>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active);
+    case 4: return launch_bwd<4>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active);
+    case 2: return launch_bwd<2>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active);
+    default: return launch_bwd<1>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active);
     }
 }
 

@@ -144,6 +144,57 @@ class Pipeline:
         abi.gevo_project_bwd(self.layout, g, cams, self.proj, self.grad2d, self.grads,
                              self.dxi if want_dxi else None, self.ws)
 
+    # ---- active set of the global stage (Section III-B2, Eq. 5) --------------------
+    def alloc_active(self):
+        """Buffers of the active-set path (allocated on first use)."""
+        if getattr(self, "pix_err", None) is not None:
+            return
+        dev, f32, u32 = self.device, torch.float32, torch.int32
+        self.pix_err = torch.zeros(self.P, dtype=f32, device=dev)
+        self.gauss_err = torch.zeros(max(self.V * self.n, 1), dtype=f32, device=dev)
+        nw = max((self.n + 31) // 32, 1)
+        self.active = torch.zeros(nw, dtype=u32, device=dev)
+        self.active_list = torch.zeros(max(self.n, 1), dtype=u32, device=dev)
+        self.active_counts = torch.zeros(abi.active_count_words(self.n), dtype=u32, device=dev)
+
+    def loss_l1_err(self, target_rgb, target_depth=None, lambda_depth=0.0):
+        """loss_l1 that also writes the per-pixel error e(u) into self.pix_err."""
+        self.alloc_active()
+        abi.gevo_loss_l1_err(self.layout, self.rgb, target_rgb,
+                             self.depth if lambda_depth else None,
+                             target_depth if lambda_depth else None, lambda_depth, self.dL_drgb,
+                             self.dL_ddepth if lambda_depth else None, self.loss, self.pix_err,
+                             self.ws)
+
+    def render_bwd_active(self, dL_drgb, dL_ddepth=None, dL_dT=None, bg=(0.0, 0.0, 0.0),
+                          error=True, masked=True, tuning=None, zero=True):
+        """Reverse walk that accumulates E_k(g) into self.gauss_err (error=True;
+        cleared first) and/or writes only the rows of active Gaussians
+        (masked=True, using self.active)."""
+        self.alloc_active()
+        if zero:
+            self.grad2d_zero()
+        if error:
+            self.gauss_err.zero_()
+        abi.gevo_render_bwd_active(self.layout, self.n, self.proj, self.vals, self.ranges, bg,
+                                   self.T_final, self.n_contrib, dL_drgb, dL_ddepth, dL_dT,
+                                   self.pix_err if error else None,
+                                   self.gauss_err if error else None,
+                                   self.active if masked else None, self.grad2d, self.ws,
+                                   tuning or self.tuning)
+
+    def active_set(self, eps, force=None):
+        """Active mask, list and count from self.gauss_err (Eq. 5 threshold eps),
+        or-ed with the bit mask `force` (the newly inserted Gaussians)."""
+        self.alloc_active()
+        abi.gevo_active_set(self.V, self.n, self.gauss_err, eps, force, self.active,
+                            self.active_list, self.active_counts)
+
+    def project_bwd_active(self, g, cams, want_dxi=True):
+        abi.gevo_project_bwd_active(self.layout, g, cams, self.proj, self.grad2d,
+                                    self.active_list, self.active_counts, self.grads,
+                                    self.dxi if want_dxi else None, self.ws)
+
     # ---- composites ------------------------------------------------------------------
     def forward(self, g, cams, bg=(0.0, 0.0, 0.0), n_eval=False):
         self.project(g, cams)
