@@ -69,7 +69,8 @@ def lib():
             L.orc_render_fwd.argtypes = [i32, i32, _P(d), _P(d), _P(d), _P(d), _P(d),
                                          _P(u32), _P(u32), _P(d),
                                          _P(d), _P(d), _P(d), _P(i32), _P(i32), _P(d), _P(i32),
-                                         _P(u64), _P(d), _P(d)]
+                                         _P(u64), _P(d), _P(d), _P(ctypes.c_uint8), _P(i32), _P(d),
+                                         _P(d)]
             L.orc_render_bwd.argtypes = [i32, i32, _P(d), _P(d), _P(d), _P(d), _P(d),
                                          _P(u32), _P(u32), _P(d),
                                          _P(d), _P(d), _P(d),
@@ -83,7 +84,8 @@ def lib():
 
 
 _CT = {np.float64: ctypes.c_double, np.int32: ctypes.c_int32, np.uint32: ctypes.c_uint32,
-       np.uint64: ctypes.c_uint64, np.float32: ctypes.c_float, np.int64: ctypes.c_int64}
+       np.uint64: ctypes.c_uint64, np.float32: ctypes.c_float, np.int64: ctypes.c_int64,
+       np.uint8: ctypes.c_uint8}
 
 
 def _ptr(a, dtype):
@@ -205,11 +207,15 @@ def bin_f32(sizes, xy32, radius, depth32, capacity=None):
 # ---------------------------------------------------------------------------
 # Step 5 / 6: blending of one view and its derivative.
 # ---------------------------------------------------------------------------
-def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0), pix_err=None):
+def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0), pix_err=None, active=None):
     """rec: dict with xy[N,2], conic[N,3], opacity[N], rgb[N,3], depth[N] (float64).
     ranges_view: this view's [tiles,2] ranges (positions into vals).
     pix_err: optional per-pixel error e(u) [H,W]; then out["gauss_err"][g] is the
-    per-Gaussian rendering error E(g) = sum_u w(g, u) e(u) of Eq. 5."""
+    per-Gaussian rendering error E(g) = sum_u w(g, u) e(u) of Eq. 5.
+    active: optional boolean mask over Gaussians; then out["act_last"] [H,W]
+    (1 + list position of the last blended active entry, 0 if none),
+    out["act_T"] [H,W] (transmittance right after it) and out["act_rest"]
+    [H,W,4] (colour incl. T_final bg, and depth, blended behind it)."""
     P = W * H
     xy, conic, opac, rgb, depth = (_f64(rec["xy"]), _f64(rec["conic"]), _f64(rec["opacity"]),
                                    _f64(rec["rgb"]), _f64(rec["depth"]))
@@ -227,6 +233,14 @@ def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0), pix_err=None):
     if pix_err is not None:
         pe = _f64(np.asarray(pix_err, np.float64).reshape(H, W))
         out["gauss_err"] = np.zeros(max(n, 1))
+    act = None
+    if active is not None:
+        act = np.ascontiguousarray(np.asarray(active, bool).astype(np.uint8))
+        if act.size == 0:
+            act = np.zeros(1, np.uint8)
+        out["act_last"] = np.zeros((H, W), np.int32)
+        out["act_T"] = np.zeros((H, W))
+        out["act_rest"] = np.zeros((H, W, 4))
     lib().orc_render_fwd(W, H, _ptr(xy, np.float64), _ptr(conic, np.float64),
                          _ptr(opac, np.float64), _ptr(rgb, np.float64), _ptr(depth, np.float64),
                          _ptr(vals, np.uint32), _ptr(rv, np.uint32), _ptr(bgv, np.float64),
@@ -235,7 +249,11 @@ def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0), pix_err=None):
                          _ptr(out["n_eval"], np.int32), _ptr(out["wsum"], np.float64),
                          _ptr(out["fragile"], np.int32), _ptr(out["sig"], np.uint64),
                          _ptr(pe, np.float64) if pe is not None else None,
-                         _ptr(out["gauss_err"], np.float64) if pe is not None else None)
+                         _ptr(out["gauss_err"], np.float64) if pe is not None else None,
+                         _ptr(act, np.uint8) if act is not None else None,
+                         _ptr(out["act_last"], np.int32) if act is not None else None,
+                         _ptr(out["act_T"], np.float64) if act is not None else None,
+                         _ptr(out["act_rest"], np.float64) if act is not None else None)
     if pe is not None:
         out["gauss_err"] = out["gauss_err"][:n]
     del P

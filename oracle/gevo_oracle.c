@@ -399,12 +399,18 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
                     const uint32_t* vals, const uint32_t* ranges, const double* bg,
                     double* out_rgb, double* out_depth, double* out_T, int32_t* n_contrib,
                     int32_t* n_eval, double* wsum, int32_t* fragile, uint64_t* sig,
-                    const double* pix_err, double* gauss_err)
+                    const double* pix_err, double* gauss_err,
+                    const uint8_t* active, int32_t* act_last, double* act_T, double* act_rest)
 {
     /* pix_err / gauss_err (both NULL or both set): the per-Gaussian rendering
      * error of Section III-B2 (Eq. 5), E(g) += w(g, u) e(u) summed over the
      * pixels u, w(g, u) the blending weight alpha T of g at u and e(u) the
-     * per-pixel error; gauss_err is indexed by Gaussian id. */
+     * per-pixel error; gauss_err is indexed by Gaussian id.
+     * active (NULL or one byte per Gaussian) with act_last / act_T / act_rest:
+     * per pixel, 1 + the list position of the last blended entry of an active
+     * Gaussian (0 if none), the transmittance right after it (1 if none), and
+     * the colour (3 channels, plus T_final bg) and depth blended behind it
+     * (act_rest[4 * pix + c]; 0 if none). */
     const int32_t tiles_x = (W + ORC_TILE - 1) / ORC_TILE;
     const size_t P = (size_t)W * H;
     for (int32_t py = 0; py < H; py++)
@@ -413,7 +419,8 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
             const int32_t tile = (py / ORC_TILE) * tiles_x + (px / ORC_TILE);
             const uint32_t s = ranges[2*tile], e = ranges[2*tile+1];
             double T = 1.0, C[3] = {0, 0, 0}, Dd = 0.0, ws = 0.0;
-            int32_t last = 0, ne = 0, frag = 0;
+            int32_t last = 0, ne = 0, frag = 0, la = 0;
+            double Ta = 1.0, Ca[3] = {0, 0, 0}, Da = 0.0;   /* colour, depth through the last active entry */
             uint64_t h = 0x1234567ULL;
             for (uint32_t i = s; i < e; i++) {
                 const uint32_t g = vals[i];
@@ -439,6 +446,12 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
                 ws += w;
                 T = Tn;
                 last = (int32_t)(i - s + 1);
+                if (active && active[g]) {
+                    la = last;
+                    Ta = T;
+                    for (int ch = 0; ch < 3; ch++) Ca[ch] = C[ch];
+                    Da = Dd;
+                }
                 h = mix64(h, ((uint64_t)(og > ORC_ALPHA_MAX) << 40) | ((uint64_t)g << 8) | 1u);
             }
             for (int ch = 0; ch < 3; ch++) out_rgb[ch * P + pix] = C[ch] + T * bg[ch];
@@ -449,6 +462,16 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
             if (wsum) wsum[pix] = ws;
             if (fragile) fragile[pix] = frag;
             if (sig) sig[pix] = mix64(h, (uint64_t)last);
+            if (active) {
+                /* what lies behind the last active entry: the whole colour
+                 * minus what was blended up to it (exact in the reals; the
+                 * CUDA path sums the part behind on its own) */
+                act_last[pix] = la;
+                act_T[pix] = la ? Ta : 1.0;
+                for (int ch = 0; ch < 3; ch++)
+                    act_rest[4 * pix + ch] = la ? (C[ch] - Ca[ch]) + T * bg[ch] : 0.0;
+                act_rest[4 * pix + 3] = la ? Dd - Da : 0.0;
+            }
         }
 }
 

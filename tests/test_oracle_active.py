@@ -124,3 +124,54 @@ def test_mask_grad2d_zeroes_inactive_rows_only():
     m = oracle.mask_grad2d(g, [True, False, True])
     np.testing.assert_array_equal(m["xy"], [[1, 1], [0, 0], [1, 1]])
     np.testing.assert_array_equal(m["opacity"], [1.0, 0.0, 3.0])
+
+
+def test_active_walk_start_state_by_hand():
+    # three Gaussians of alpha 0.5 stacked on the centre pixel, the middle one
+    # active: weights 0.5, 0.25, 0.125, T_final = 0.125; the walk starts after
+    # entry 2 with T = 0.25 and colour behind = 0.125 c_3 + 0.125 bg.
+    rec = _records([[8.0, 8.0]] * 3, [[0.01, 0.0, 0.01]] * 3, [0.5, 0.5, 0.5],
+                   [[1, 0, 0], [0, 1, 0], [0, 0, 1]], [1.0, 2.0, 3.0])
+    bg = (0.2, 0.4, 0.6)
+    n = 3
+    b = oracle.bin_f32([(16, 16)], rec["xy"][None].astype(np.float32), np.full((1, n), 16, np.int32),
+                       rec["depth"][None].astype(np.float32))
+    out = oracle.render_fwd(16, 16, rec, b["vals"], b["ranges"], bg, active=[False, True, False])
+    assert out["act_last"][8, 8] == 2
+    assert out["act_T"][8, 8] == 0.25
+    np.testing.assert_allclose(out["act_rest"][8, 8], [0.125 * 0.2, 0.125 * 0.4, 0.125 + 0.125 * 0.6,
+                                                       0.125 * 3.0], rtol=1e-14)
+    # all active: the walk starts at n_contrib with T_final and only the background behind
+    out = oracle.render_fwd(16, 16, rec, b["vals"], b["ranges"], bg, active=[True] * 3)
+    np.testing.assert_array_equal(out["act_last"], out["n_contrib"])
+    np.testing.assert_array_equal(out["act_T"], out["T"])
+    for ch in range(3):
+        np.testing.assert_allclose(out["act_rest"][..., ch], out["T"] * bg[ch], atol=1e-15)
+    assert (out["act_rest"][..., 3] == 0).all()
+    # none active: nothing to walk
+    out = oracle.render_fwd(16, 16, rec, b["vals"], b["ranges"], bg, active=[False] * 3)
+    assert (out["act_last"] == 0).all() and (out["act_T"] == 1).all() and (out["act_rest"] == 0).all()
+
+
+def test_active_walk_state_where_nothing_blends_behind():
+    # pixels whose last blended entry is active: the walk starts at n_contrib
+    # with T_final and only the background behind; and it never starts behind
+    # a pixel's last blended entry.
+    sizes = [(32, 32)]
+    n = 150
+    rec = scenes.random_records(sizes, n, seed=12, sigma_px=(1.0, 5.0))
+    r = dict(xy=rec["xy"][0].astype(np.float64), conic=rec["conic"][0].astype(np.float64),
+             opacity=rec["opacity"].astype(np.float64), rgb=rec["rgb"][0].astype(np.float64),
+             depth=rec["depth"][0].astype(np.float64))
+    act = np.random.default_rng(13).uniform(size=n) < 0.3
+    b = oracle.bin_f32(sizes, rec["xy"], rec["radius"], rec["depth"])
+    bg = (0.3, 0.2, 0.1)
+    out = oracle.render_fwd(32, 32, r, b["vals"], b["ranges"], bg, active=act)
+    sel = (out["act_last"] == out["n_contrib"]) & (out["act_last"] > 0)
+    assert sel.sum() > 10
+    np.testing.assert_array_equal(out["act_T"][sel], out["T"][sel])
+    for ch in range(3):
+        np.testing.assert_allclose(out["act_rest"][..., ch][sel], out["T"][sel] * bg[ch], rtol=1e-12)
+    assert (out["act_rest"][..., 3][sel] == 0).all()
+    assert (out["act_last"] <= out["n_contrib"]).all()
+    assert ((out["act_last"] > 0) | (out["act_T"] == 1)).all()
