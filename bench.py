@@ -393,12 +393,13 @@ def active_set_section(rep, target_rgb, target_depth, flush, stage_ms, reps=10):
             ms += s.elapsed_time(e)
         return ms / reps
 
-    def walk(error, masked):
+    def walk(error, masked, from_state=False):
         _abi.gevo_render_bwd_active(
             pipe.layout, pipe.n, pipe.proj, pipe.vals, pipe.ranges, rep.bg, pipe.T_final,
             pipe.n_contrib, pipe.dL_drgb, pipe.dL_ddepth, None,
             pipe.pix_err if error else None, pipe.gauss_err if error else None,
-            pipe.active if masked else None, pipe.grad2d, pipe.ws, tb)
+            pipe.active if masked else None, pipe.grad2d, pipe.ws, tb,
+            state=pipe.act_state if from_state else None)
 
     rep.replay()
     ms = {"loss_err": timed(lambda: pipe.loss_l1_err(target_rgb, target_depth, 1.0))}
@@ -412,12 +413,17 @@ def active_set_section(rep, target_rgb, target_depth, flush, stage_ms, reps=10):
     ms["active_set"] = timed(lambda: pipe.active_set(eps))
     active = int(pipe.active_counts[0].item())
     ms["render_bwd_masked"] = timed(lambda: walk(False, True), before=pipe.grad2d_zero)
+    ms["render_fwd"] = timed(lambda: pipe.render_fwd(rep.bg, tuning=rep.tuning_fwd))
+    ms["render_fwd_active"] = timed(lambda: pipe.render_fwd_active(rep.bg, tuning=rep.tuning_fwd))
+    ms["render_bwd_from_state"] = timed(lambda: walk(False, True, True), before=pipe.grad2d_zero)
     ms["project_bwd_masked"] = timed(lambda: pipe.project_bwd_active(rep.g, rep.camt))
     full = ms["render_bwd_full"] + stage_ms["project_bwd"]
-    masked = ms["render_bwd_masked"] + ms["project_bwd_masked"]
+    masked = (ms["render_fwd_active"] - ms["render_fwd"]) + ms["render_bwd_from_state"] + \
+        ms["project_bwd_masked"]
     return {"active": active, "frac": active / N, "seen": int(seen.numel()), "eps": eps, "ms": ms,
             "full_ms": {"render_bwd": stage_ms["render_bwd"], "project_bwd": stage_ms["project_bwd"]},
             "backward_speedup": full / masked,
+            "backward_speedup_whole_lists": full / (ms["render_bwd_masked"] + ms["project_bwd_masked"]),
             "note": "E_k from the step's own render vs the stop-gradient targets; eps = 85th "
                     "percentile of max_k E_k(g) over the Gaussians some view blends (seen)"}
 

@@ -324,8 +324,32 @@ gevo_status gevo_loss_l1_err(const gevo_layout* layout, const float* rgb,
                              float* dL_ddepth, float* loss, float* pix_err, void* workspace,
                              void* stream);
 
-/* gevo_render_bwd with two optional additions, fused into the same reverse
- * walk (one kernel):
+/* Where the reverse walk of an active-set backward starts, per pixel (DEVICE,
+ * planes of total_pixels, written by gevo_render_fwd_active):
+ *   last[p]  1 + list position of the last blended entry of an active
+ *            Gaussian, 0 if the pixel blends none;
+ *   T[p]     transmittance right after that entry (1 if none);
+ *   rest[p]  float4: colour blended behind that entry plus T_final bg, and
+ *            depth blended behind it (0 if none); 16-byte aligned. */
+typedef struct {
+    uint32_t* last;
+    float* T;
+    float* rest;
+} gevo_active_state;
+
+/* gevo_render_fwd (same outputs, same values) that also fills *state for the
+ * active set `active` (bit mask as in gevo_render_bwd_active).  With it the
+ * reverse walk skips every list entry behind a pixel's last active entry:
+ * their only effect on the active Gaussians' gradients is through the
+ * transmittance and the colour behind, which *state carries. */
+gevo_status gevo_render_fwd_active(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                                   const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                                   float* rgb, float* depth, float* T_final, uint32_t* n_contrib,
+                                   const uint32_t* active, gevo_active_state* state,
+                                   const gevo_tuning* tuning, void* workspace, void* stream);
+
+/* gevo_render_bwd with optional additions, fused into the same reverse walk
+ * (one kernel):
  *  - pix_err != NULL (DEVICE float[total_pixels], e.g. from gevo_loss_l1_err):
  *    gauss_err[v * n + g] += sum over view v's pixels u of w(g, u) pix_err[u]
  *    (E_k(g) of Eq. 5; DEVICE float[n_views * n], accumulated -- clear it
@@ -338,14 +362,20 @@ gevo_status gevo_loss_l1_err(const gevo_layout* layout, const float* rgb,
  *    entries only recover T and the suffix colour, so the walk costs less in
  *    proportion to the inactive share.  An all-zero mask with pix_err gives
  *    the error pass alone.
+ *  - state != NULL (requires active, and pix_err == NULL; from
+ *    gevo_render_fwd_active with the same mask): each pixel's walk starts at
+ *    its last active entry instead of n_contrib - 1.  Active rows get the same
+ *    gradients up to rounding (the colour behind comes from the forward pass
+ *    instead of the walk).
  * Everything else as gevo_render_bwd. */
 gevo_status gevo_render_bwd_active(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
                                    const uint32_t* vals, const uint32_t* ranges, const float* bg,
                                    const float* T_final, const uint32_t* n_contrib,
                                    const float* dL_drgb, const float* dL_ddepth,
                                    const float* dL_dT, const float* pix_err, float* gauss_err,
-                                   const uint32_t* active, gevo_grad2d* out,
-                                   const gevo_tuning* tuning, void* workspace, void* stream);
+                                   const uint32_t* active, const gevo_active_state* state,
+                                   gevo_grad2d* out, const gevo_tuning* tuning, void* workspace,
+                                   void* stream);
 
 /* Words of the `counts` argument of gevo_active_set for n Gaussians. */
 #define GEVO_ACTIVE_COUNT_WORDS(n) (((size_t)(n) + 1023) / 1024 + 1)

@@ -61,6 +61,10 @@ class Grad2d(ctypes.Structure):
                 ("rgb_depth", ctypes.c_void_p)]
 
 
+class ActiveState(ctypes.Structure):
+    _fields_ = [("last", ctypes.c_void_p), ("T", ctypes.c_void_p), ("rest", ctypes.c_void_p)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("threads_per_tile", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32)]
@@ -71,7 +75,7 @@ EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin
            "gevo_render_fwd", "gevo_render_bwd", "gevo_project_bwd", "gevo_loss_l1",
            "gevo_last_error", "gevo_status_str", "gevo_version", "gevo_bin_sort_noalloc",
            "gevo_grad2d_zero", "gevo_gemm_bf16", "gevo_loss_l1_err", "gevo_render_bwd_active",
-           "gevo_active_set", "gevo_project_bwd_active"]
+           "gevo_active_set", "gevo_project_bwd_active", "gevo_render_fwd_active"]
 
 # Every symbol include/gevo_prior.h declares, with its argument kinds
 # (i: int32, u: uint32, I: int64, f: float, p: pointer; the last p is the stream).
@@ -138,7 +142,10 @@ def load(build_if_missing: bool = True):
     L.gevo_loss_l1.argtypes = [P(Layout), vp, vp, vp, vp, f32, vp, vp, vp, vp, vp]
     L.gevo_loss_l1_err.argtypes = [P(Layout), vp, vp, vp, vp, f32, vp, vp, vp, vp, vp, vp]
     L.gevo_render_bwd_active.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp,
-                                         vp, vp, vp, vp, P(Grad2d), P(Tuning), vp, vp]
+                                         vp, vp, vp, vp, P(ActiveState), P(Grad2d), P(Tuning), vp,
+                                         vp]
+    L.gevo_render_fwd_active.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp,
+                                         vp, P(ActiveState), P(Tuning), vp, vp]
     L.gevo_active_set.argtypes = [i32, i32, vp, f32, vp, vp, vp, vp, vp]
     L.gevo_project_bwd_active.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d), vp, vp,
                                           P(GaussianGrads), vp, vp, vp]
@@ -153,7 +160,8 @@ def load(build_if_missing: bool = True):
         getattr(L, name).restype = ctypes.c_int
     for name in ("gevo_project", "gevo_bin_sort", "gevo_render_fwd", "gevo_render_bwd",
                  "gevo_project_bwd", "gevo_loss_l1", "gevo_last_error", "gevo_loss_l1_err",
-                 "gevo_render_bwd_active", "gevo_active_set", "gevo_project_bwd_active"):
+                 "gevo_render_bwd_active", "gevo_active_set", "gevo_project_bwd_active",
+                 "gevo_render_fwd_active"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -279,18 +287,38 @@ def gevo_render_bwd(layout, n, proj: dict, vals, ranges, bg, T_final, n_contrib,
         ctypes.byref(tu) if tu is not None else None, _p(ws), _stream(stream)))
 
 
+def active_state_struct(state):
+    """dict(last, T, rest) of device tensors -> gevo_active_state (None -> None)."""
+    if state is None:
+        return None
+    return ActiveState(_p(state["last"]), _p(state["T"]), _p(state["rest"]))
+
+
+def gevo_render_fwd_active(layout, n, proj: dict, vals, ranges, bg, rgb, depth, T_final,
+                           n_contrib, active, state: dict, ws, tuning=None, stream=None):
+    P_ = proj_struct(proj)
+    bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    tu = tuning_struct(tuning)
+    S = active_state_struct(state)
+    _check("gevo_render_fwd_active", load().gevo_render_fwd_active(
+        ctypes.byref(layout), int(n), ctypes.byref(P_), _p(vals), _p(ranges), bgv, _p(rgb),
+        _p(depth), _p(T_final), _p(n_contrib), _p(active), ctypes.byref(S),
+        ctypes.byref(tu) if tu is not None else None, _p(ws), _stream(stream)))
+
+
 def gevo_render_bwd_active(layout, n, proj: dict, vals, ranges, bg, T_final, n_contrib, dL_drgb,
                            dL_ddepth, dL_dT, pix_err, gauss_err, active, grad2d: dict, ws,
-                           tuning=None, stream=None):
+                           tuning=None, stream=None, state=None):
     P_ = proj_struct(proj)
     G2 = grad2d_struct(grad2d)
     bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
     tu = tuning_struct(tuning)
+    S = active_state_struct(state)
     _check("gevo_render_bwd_active", load().gevo_render_bwd_active(
         ctypes.byref(layout), int(n), ctypes.byref(P_), _p(vals), _p(ranges), bgv, _p(T_final),
         _p(n_contrib), _p(dL_drgb), _p(dL_ddepth), _p(dL_dT), _p(pix_err), _p(gauss_err),
-        _p(active), ctypes.byref(G2), ctypes.byref(tu) if tu is not None else None, _p(ws),
-        _stream(stream)))
+        _p(active), ctypes.byref(S) if S is not None else None, ctypes.byref(G2),
+        ctypes.byref(tu) if tu is not None else None, _p(ws), _stream(stream)))
 
 
 def gevo_active_set(n_views, n, gauss_err, eps, force, active, active_list, counts, stream=None):

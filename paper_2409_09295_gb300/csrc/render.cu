@@ -80,20 +80,31 @@ __device__ __forceinline__ void tile_of(const gevo_layout& L, int tile, int& v, 
     y0 = (local / tx) * kTile;
 }
 
-template <int PPT, bool COUNT>
+// ACT: also record, per pixel, where the reverse walk of an active-set
+// backward has to start: 1 + the list position of the last blended entry of an
+// active Gaussian (0 if none), the transmittance right after it, and the colour
+// (with T_final bg) and depth blended behind it.  The colour is summed in two
+// parts, up to the last active entry and since it, so that the part behind
+// needs no difference of two sums; the bookkeeping runs only at active
+// entries (a warp-uniform branch), and the pixel colour is the sum of the two
+// parts.
+template <int PPT, bool COUNT, bool ACT>
 __global__ void __launch_bounds__(256 / PPT)
 k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
              const float4* __restrict__ rz, const uint32_t* __restrict__ vals,
              const uint2* __restrict__ ranges, float bg0, float bg1, float bg2,
              float* __restrict__ out_rgb, float* __restrict__ out_d, float* __restrict__ out_T,
              uint32_t* __restrict__ out_nc, uint32_t* __restrict__ out_ne,
-             const uint32_t* __restrict__ order, uint32_t* queue, int n_items)
+             const uint32_t* __restrict__ order, uint32_t* queue, int n_items,
+             const uint32_t* __restrict__ active, uint32_t* __restrict__ act_last,
+             float* __restrict__ act_T, float4* __restrict__ act_rest)
 {
     constexpr int NT = 256 / PPT;
     __shared__ float2 s_xy[kBatch];
     __shared__ float4 s_co[kBatch];
     __shared__ float4 s_rz[kBatch];
     __shared__ float4 s_box[kBatch];
+    __shared__ uint32_t s_act[ACT ? kBatch : 1];
     __shared__ uint32_t s_item;
     const int tid = threadIdx.x;
     const int wrow0 = ((tid & ~31) >> 4) * PPT;   // first tile row of this warp
@@ -122,13 +133,15 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
         const size_t vbase = (size_t)v * n;
 
         float T[PPT], C0[PPT], C1[PPT], C2[PPT], Dp[PPT];
-        uint32_t last[PPT], cnt[PPT];
+        float B0[PPT], B1[PPT], B2[PPT], BD[PPT], Ta[PPT];   // colour, depth through the last active entry
+        uint32_t last[PPT], cnt[PPT], la[PPT];
         bool done[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
             T[k] = 1.f; C0[k] = C1[k] = C2[k] = Dp[k] = 0.f;
             last[k] = 0u; cnt[k] = 0u;
             done[k] = !(px < W && py0 + k < H);
+            if (ACT) { B0[k] = B1[k] = B2[k] = BD[k] = 0.f; Ta[k] = 1.f; la[k] = 0u; }
         }
         const float fpx = (float)px;
 
@@ -139,13 +152,15 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
             if (__syncthreads_and(mine)) break;
             const int nb = (int)min((uint32_t)kBatch, rg.y - b);
             for (int j = tid; j < nb; j += NT) {
-                const size_t id = vbase + vals[b + j];
+                const uint32_t gid = vals[b + j];
+                const size_t id = vbase + gid;
                 const float2 m = xy[id];
                 const float4 c = co[id];
                 s_xy[j] = m;
                 s_co[j] = prescale(c);
                 s_rz[j] = rz[id];
                 s_box[j] = alpha_box(m, c);
+                if (ACT) s_act[j] = (__ldg(active + (gid >> 5)) >> (gid & 31)) & 1u;
             }
             __syncthreads();
             const float wx0 = (float)x0, wx1 = (float)(x0 + kTile - 1);
@@ -194,6 +209,24 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     T[k] = bl ? Tn : T[k];
                     last[k] = bl ? pos1 : last[k];
                 }
+                if (ACT && s_act[j]) {
+                    // an active entry: move the part since the previous one
+                    // into the part up to here (C holds the part since)
+#pragma unroll
+                    for (int k = 0; k < PPT; k++) {
+                        const bool at = last[k] == pos1;   // blended right here
+                        B0[k] = at ? __fadd_rn(B0[k], C0[k]) : B0[k];
+                        B1[k] = at ? __fadd_rn(B1[k], C1[k]) : B1[k];
+                        B2[k] = at ? __fadd_rn(B2[k], C2[k]) : B2[k];
+                        BD[k] = at ? __fadd_rn(BD[k], Dp[k]) : BD[k];
+                        C0[k] = at ? 0.f : C0[k];
+                        C1[k] = at ? 0.f : C1[k];
+                        C2[k] = at ? 0.f : C2[k];
+                        Dp[k] = at ? 0.f : Dp[k];
+                        Ta[k] = at ? T[k] : Ta[k];
+                        la[k] = at ? pos1 : la[k];
+                    }
+                }
             }
         }
 #pragma unroll
@@ -201,11 +234,23 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
             const int py = py0 + k;
             if (px < W && py < H) {
                 const size_t pix = (size_t)py * W + px;
+                const size_t gp = (size_t)L.pix_base[v] + pix;
+                if (ACT) {
+                    // C, Dp hold the part behind the last active entry
+                    act_last[gp] = la[k];
+                    act_T[gp] = Ta[k];
+                    act_rest[gp] = la[k] ? make_float4(__fmaf_rn(T[k], bg0, C0[k]), __fmaf_rn(T[k], bg1, C1[k]),
+                                                       __fmaf_rn(T[k], bg2, C2[k]), Dp[k])
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+                    C0[k] = __fadd_rn(B0[k], C0[k]);
+                    C1[k] = __fadd_rn(B1[k], C1[k]);
+                    C2[k] = __fadd_rn(B2[k], C2[k]);
+                    Dp[k] = __fadd_rn(BD[k], Dp[k]);
+                }
                 float* rgb = out_rgb + 3 * (size_t)L.pix_base[v];
                 rgb[pix] = __fmaf_rn(T[k], bg0, C0[k]);
                 rgb[P + pix] = __fmaf_rn(T[k], bg1, C1[k]);
                 rgb[2 * P + pix] = __fmaf_rn(T[k], bg2, C2[k]);
-                const size_t gp = (size_t)L.pix_base[v] + pix;
                 out_d[gp] = Dp[k];
                 out_T[gp] = T[k];
                 out_nc[gp] = last[k];
@@ -322,7 +367,8 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
              const float* __restrict__ dL_dT, float2* __restrict__ g_xy, float4* __restrict__ g_co,
              float4* __restrict__ g_rz, const uint32_t* __restrict__ order, uint32_t* queue,
              int n_items, const float* __restrict__ pix_err, float* __restrict__ gauss_err,
-             const uint32_t* __restrict__ active)
+             const uint32_t* __restrict__ active, const uint32_t* __restrict__ act_last,
+             const float* __restrict__ act_T, const float4* __restrict__ act_rest)
 {
     constexpr int NT = 256 / PPT;
     constexpr int NW = NT / 32;
@@ -381,6 +427,19 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 gD[k] = DD ? dL_dd[gp] : 0.f;
                 gTT[k] = DT ? dL_dT[gp] * T[k] : 0.f;
                 pe[k] = (EXT && pix_err) ? pix_err[gp] : 0.f;
+                if (EXT && act_last) {
+                    // start at the last active entry: what lies behind it is
+                    // summarised by the transmittance after it and the colour
+                    // and depth blended behind it
+                    last[k] = act_last[gp];
+                    if (last[k]) {
+                        const float Ta = act_T[gp];
+                        const float4 q = act_rest[gp];
+                        T[k] = Ta;
+                        S0[k] = __fdiv_rn(q.x, Ta); S1[k] = __fdiv_rn(q.y, Ta);
+                        S2[k] = __fdiv_rn(q.z, Ta); SD[k] = __fdiv_rn(q.w, Ta);
+                    }
+                }
             } else {
                 T[k] = 1.f; last[k] = 0u;
                 gC0[k] = gC1[k] = gC2[k] = gD[k] = gTT[k] = pe[k] = 0.f;
@@ -555,7 +614,8 @@ template <int PPT>
 static gevo_status launch_fwd(const gevo_layout& L, int n, const gevo_proj& p, const uint32_t* vals,
                               const uint32_t* ranges, const float* bg, float* rgb, float* depth,
                               float* Tf, uint32_t* nc, uint32_t* ne, const gevo_tuning* t,
-                              char* ws, cudaStream_t st)
+                              char* ws, cudaStream_t st, const uint32_t* active = nullptr,
+                              const gevo_active_state* as = nullptr)
 {
     const WsLayout w = ws_layout(L, n, 0);
     const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + w.tile_order);
@@ -564,13 +624,16 @@ static gevo_status launch_fwd(const gevo_layout& L, int n, const gevo_proj& p, c
     if (t && t->persistent) {
         queue = reinterpret_cast<uint32_t*>(ws + w.err) + kQueueFwd;
         if (cudaMemsetAsync(queue, 0, 4, st) != cudaSuccess) return GEVO_ERR_CUDA;
-        grid = std::min(grid, persistent_grid<PPT>(k_render_fwd<PPT, false>, t));
     }
-    auto kern = ne ? k_render_fwd<PPT, true> : k_render_fwd<PPT, false>;
+    auto kern = as ? k_render_fwd<PPT, false, true>
+                   : (ne ? k_render_fwd<PPT, true, false> : k_render_fwd<PPT, false, false>);
+    if (queue) grid = std::min(grid, persistent_grid<PPT>(kern, t));
     kern<<<grid, 256 / PPT, 0, st>>>(
         L, n, reinterpret_cast<const float2*>(p.xy), reinterpret_cast<const float4*>(p.conic_opacity),
         reinterpret_cast<const float4*>(p.rgb_depth), vals, reinterpret_cast<const uint2*>(ranges),
-        bg[0], bg[1], bg[2], rgb, depth, Tf, nc, ne, order, queue, L.total_tiles);
+        bg[0], bg[1], bg[2], rgb, depth, Tf, nc, ne, order, queue, L.total_tiles, active,
+        as ? as->last : nullptr, as ? as->T : nullptr,
+        as ? reinterpret_cast<float4*>(as->rest) : nullptr);
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }
@@ -588,7 +651,9 @@ static gevo_status launch_bwd(const gevo_layout& L, int n, const gevo_proj& p, c
                               const uint32_t* nc, const float* gC, const float* gD, const float* gT,
                               const gevo_grad2d& out, const gevo_tuning* t, char* ws,
                               cudaStream_t st, const float* pix_err = nullptr,
-                              float* gauss_err = nullptr, const uint32_t* active = nullptr)
+                              float* gauss_err = nullptr, const uint32_t* active = nullptr,
+                              const uint32_t* act_last = nullptr, const float* act_T = nullptr,
+                              const float* act_rest = nullptr)
 {
     const WsLayout w = ws_layout(L, n, 0);
     const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + w.tile_order);
@@ -606,7 +671,8 @@ static gevo_status launch_bwd(const gevo_layout& L, int n, const gevo_proj& p, c
         reinterpret_cast<const float4*>(p.rgb_depth), vals, reinterpret_cast<const uint2*>(ranges),
         bg[0], bg[1], bg[2], Tf, nc, gC, gD, gT, reinterpret_cast<float2*>(out.xy),
         reinterpret_cast<float4*>(out.conic_opacity), reinterpret_cast<float4*>(out.rgb_depth),
-        order, queue, L.total_tiles, pix_err, gauss_err, active);
+        order, queue, L.total_tiles, pix_err, gauss_err, active, act_last, act_T,
+        reinterpret_cast<const float4*>(act_rest));
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }
@@ -646,6 +712,31 @@ extern "C" gevo_status gevo_render_fwd(const gevo_layout* layout, int32_t n, con
     }
 }
 
+extern "C" gevo_status gevo_render_fwd_active(const gevo_layout* layout, int32_t n,
+                                              const gevo_proj* proj, const uint32_t* vals,
+                                              const uint32_t* ranges, const float* bg, float* rgb,
+                                              float* depth, float* T_final, uint32_t* n_contrib,
+                                              const uint32_t* active, gevo_active_state* state,
+                                              const gevo_tuning* tuning, void* workspace,
+                                              void* stream)
+{
+    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+        !proj->rgb_depth || !vals || !ranges || !bg || !rgb || !depth || !T_final || !n_contrib ||
+        !active || !state || !state->last || !state->T || !state->rest || !workspace ||
+        !gevo_aligned(workspace, 256) || !valid_tuning(tuning) || !gevo_aligned(ranges, 8) ||
+        !gevo_aligned(proj->conic_opacity, 16) || !gevo_aligned(proj->rgb_depth, 16) ||
+        !gevo_aligned(proj->xy, 8) || !gevo_aligned(state->rest, 16))
+        return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = reinterpret_cast<char*>(workspace);
+    switch (pick_ppt(tuning)) {
+    case 8: return launch_fwd<8>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, nullptr, tuning, ws, st, active, state);
+    case 4: return launch_fwd<4>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, nullptr, tuning, ws, st, active, state);
+    case 2: return launch_fwd<2>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, nullptr, tuning, ws, st, active, state);
+    default: return launch_fwd<1>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, nullptr, tuning, ws, st, active, state);
+    }
+}
+
 extern "C" gevo_status gevo_render_bwd(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
                                        const uint32_t* vals, const uint32_t* ranges,
                                        const float* bg, const float* T_final,
@@ -678,8 +769,9 @@ extern "C" gevo_status gevo_render_bwd_active(const gevo_layout* layout, int32_t
                                               const float* dL_drgb, const float* dL_ddepth,
                                               const float* dL_dT, const float* pix_err,
                                               float* gauss_err, const uint32_t* active,
-                                              gevo_grad2d* out, const gevo_tuning* tuning,
-                                              void* workspace, void* stream)
+                                              const gevo_active_state* state, gevo_grad2d* out,
+                                              const gevo_tuning* tuning, void* workspace,
+                                              void* stream)
 {
     if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
         !proj->rgb_depth || !proj->radius || !vals || !ranges || !bg || !T_final || !n_contrib ||
@@ -688,13 +780,19 @@ extern "C" gevo_status gevo_render_bwd_active(const gevo_layout* layout, int32_t
         !gevo_aligned(out->conic_opacity, 16) || !gevo_aligned(out->rgb_depth, 16) ||
         !gevo_aligned(out->xy, 8) || (pix_err == nullptr) != (gauss_err == nullptr))
         return GEVO_ERR_INVALID;
+    if (state && (!active || pix_err || !state->last || !state->T || !state->rest ||
+                  !gevo_aligned(state->rest, 16)))
+        return GEVO_ERR_INVALID;
+    const uint32_t* al = state ? state->last : nullptr;
+    const float* aT = state ? state->T : nullptr;
+    const float* ar = state ? state->rest : nullptr;
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = reinterpret_cast<char*>(workspace);
     switch (pick_ppt(tuning)) {
-    case 8: return launch_bwd<8>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active);
-    case 4: return launch_bwd<4>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active);
-    case 2: return launch_bwd<2>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active);
-    default: return launch_bwd<1>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active);
+    case 8: return launch_bwd<8>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active, al, aT, ar);
+    case 4: return launch_bwd<4>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active, al, aT, ar);
+    case 2: return launch_bwd<2>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active, al, aT, ar);
+    default: return launch_bwd<1>(*layout, n, *proj, vals, ranges, bg, T_final, n_contrib, dL_drgb, dL_ddepth, dL_dT, *out, tuning, ws, st, pix_err, gauss_err, active, al, aT, ar);
     }
 }
 

@@ -156,6 +156,9 @@ class Pipeline:
         self.active = torch.zeros(nw, dtype=u32, device=dev)
         self.active_list = torch.zeros(max(self.n, 1), dtype=u32, device=dev)
         self.active_counts = torch.zeros(abi.active_count_words(self.n), dtype=u32, device=dev)
+        self.act_state = dict(last=torch.zeros(self.P, dtype=u32, device=dev),
+                              T=torch.ones(self.P, dtype=f32, device=dev),
+                              rest=torch.zeros(self.P, 4, dtype=f32, device=dev))
 
     def loss_l1_err(self, target_rgb, target_depth=None, lambda_depth=0.0):
         """loss_l1 that also writes the per-pixel error e(u) into self.pix_err."""
@@ -166,11 +169,20 @@ class Pipeline:
                              self.dL_ddepth if lambda_depth else None, self.loss, self.pix_err,
                              self.ws)
 
+    def render_fwd_active(self, bg=(0.0, 0.0, 0.0), tuning=None):
+        """render_fwd that also records where an active-set reverse walk starts
+        (self.act_state), for the mask in self.active."""
+        self.alloc_active()
+        abi.gevo_render_fwd_active(self.layout, self.n, self.proj, self.vals, self.ranges, bg,
+                                   self.rgb, self.depth, self.T_final, self.n_contrib, self.active,
+                                   self.act_state, self.ws, tuning or self.tuning)
+
     def render_bwd_active(self, dL_drgb, dL_ddepth=None, dL_dT=None, bg=(0.0, 0.0, 0.0),
-                          error=True, masked=True, tuning=None, zero=True):
+                          error=True, masked=True, tuning=None, zero=True, from_state=False):
         """Reverse walk that accumulates E_k(g) into self.gauss_err (error=True;
         cleared first) and/or writes only the rows of active Gaussians
-        (masked=True, using self.active)."""
+        (masked=True, using self.active); from_state=True starts each pixel at
+        its last active entry (after render_fwd_active; needs masked, not error)."""
         self.alloc_active()
         if zero:
             self.grad2d_zero()
@@ -181,7 +193,8 @@ class Pipeline:
                                    self.pix_err if error else None,
                                    self.gauss_err if error else None,
                                    self.active if masked else None, self.grad2d, self.ws,
-                                   tuning or self.tuning)
+                                   tuning or self.tuning,
+                                   state=self.act_state if from_state else None)
 
     def active_set(self, eps, force=None):
         """Active mask, list and count from self.gauss_err (Eq. 5 threshold eps),

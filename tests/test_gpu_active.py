@@ -179,6 +179,97 @@ def test_masked_reverse_walk_staged(tuning, frac):
 
 
 # --------------------------------------------------------------------------
+# the forward pass that records where an active-set walk starts, and the walk
+# from there
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("tuning", TUNINGS, ids=["ppt1", "ppt4_persistent", "ppt8_persistent"])
+def test_render_fwd_active_state(tuning):
+    sizes = [(96, 80), (53, 37)]
+    n = 2500
+    bg = (0.1, 0.2, 0.3)
+    rec, b, pipe = _staged(sizes, n, seed=80)
+    act = np.random.default_rng(81).uniform(size=n) < 0.15
+    pipe.render_fwd(bg, tuning=tuning)
+    plain = {k: _np(getattr(pipe, k)).copy() for k in ("rgb", "depth", "T_final", "n_contrib")}
+    pipe.alloc_active()
+    pipe.active.copy_(torch.from_numpy(_bits(act).view(np.int32)).to(pipe.device))
+    pipe.render_fwd_active(bg, tuning=tuning)
+    torch.cuda.synchronize()
+    # same decisions bit for bit; the colour is summed in two parts (up to the
+    # last active entry and since), so it may differ in the last bits
+    for k in ("T_final", "n_contrib"):
+        np.testing.assert_array_equal(_np(getattr(pipe, k)), plain[k], err_msg=k)
+    np.testing.assert_allclose(_np(pipe.rgb), plain["rgb"], atol=1e-6, rtol=0)
+    np.testing.assert_allclose(_np(pipe.depth), plain["depth"], atol=1e-5, rtol=1e-6)
+    base = 0
+    for v, (W, H) in enumerate(sizes):
+        nt = tiles_of(W, H)
+        o = oracle.render_fwd(W, H, records_for_oracle(rec, v), b["vals"], b["ranges"][base:base + nt], bg,
+                              active=act)
+        base += nt
+        ok = o["fragile"] == 0
+        la = _np(pipe.view_plane(pipe.act_state["last"], v))
+        np.testing.assert_array_equal(la[ok], o["act_last"][ok])
+        assert (la[ok] > 0).mean() > 0.3
+        Ta = _np(pipe.view_plane(pipe.act_state["T"], v))
+        np.testing.assert_allclose(Ta[ok], o["act_T"][ok], atol=1e-5, rtol=0)
+        p0, p1 = pipe.pix_base[v], pipe.pix_base[v + 1]
+        rest = _np(pipe.act_state["rest"])[p0:p1].reshape(H, W, 4)
+        np.testing.assert_allclose(rest[ok], o["act_rest"][ok], atol=1e-5, rtol=0)
+
+
+@pytest.mark.parametrize("tuning", TUNINGS, ids=["ppt1", "ppt4_persistent", "ppt8_persistent"])
+@pytest.mark.parametrize("frac", [0.15, 0.0, 1.0])
+def test_masked_walk_from_forward_state(tuning, frac):
+    sizes = [(96, 80), (53, 37)]
+    n = 2000
+    bg = (0.2, 0.1, 0.4)
+    rec, b, pipe = _staged(sizes, n, seed=90)
+    act = np.random.default_rng(91).uniform(size=n) < frac
+    pipe.alloc_active()
+    pipe.active.copy_(torch.from_numpy(_bits(act).view(np.int32)).to(pipe.device))
+    pipe.render_fwd_active(bg, tuning=tuning)
+    pe, gC = _fragile_free_inputs(rec, b, pipe, sizes, bg, seed=92)
+    gD = np.random.default_rng(93).normal(size=pipe.P).astype(np.float32)
+    gT = np.random.default_rng(94).normal(size=pipe.P).astype(np.float32)
+    base = 0
+    for v, (W, H) in enumerate(sizes):         # fragile pixels carry no gradient
+        nt = tiles_of(W, H)
+        o = oracle.render_fwd(W, H, records_for_oracle(rec, v), b["vals"], b["ranges"][base:base + nt], bg)
+        fr = o["fragile"].reshape(-1) != 0
+        p0, p1 = pipe.pix_base[v], pipe.pix_base[v + 1]
+        gD[p0:p1][fr] = 0.0
+        gT[p0:p1][fr] = 0.0
+        base += nt
+    dev = pipe.device
+    tC, tD, tT = (torch.from_numpy(x).to(dev) for x in (gC, gD, gT))
+    pipe.render_bwd_active(tC, tD, tT, bg=bg, error=False, masked=True, tuning=tuning, from_state=True)
+    torch.cuda.synchronize()
+    base = 0
+    for v, (W, H) in enumerate(sizes):
+        nt = tiles_of(W, H)
+        p0, p1 = pipe.pix_base[v], pipe.pix_base[v + 1]
+        g = oracle.mask_grad2d(oracle.render_bwd(W, H, records_for_oracle(rec, v), b["vals"],
+                                                 b["ranges"][base:base + nt],
+                                                 gC[3 * p0:3 * p1].reshape(3, H, W), gD[p0:p1].reshape(H, W),
+                                                 gT[p0:p1].reshape(H, W), bg), act)
+        base += nt
+        sl = slice(v * n, (v + 1) * n)
+        gxy = _np(pipe.grad2d["xy"])[sl]
+        gco = _np(pipe.grad2d["conic_opacity"])[sl]
+        grz = _np(pipe.grad2d["rgb_depth"])[sl]
+        vis = rec["radius"][v] > 0
+        a = vis & act
+        if a.any():
+            grad_close(gxy[a], g["xy"][a], f"v{v} dxy")
+            grad_close(gco[a, :3], g["conic"][a], f"v{v} dconic")
+            grad_close(gco[a, 3], g["opacity"][a], f"v{v} dopacity")
+            grad_close(grz[a, :3], g["rgb"][a], f"v{v} drgb")
+            grad_close(grz[a, 3], g["depth"][a], f"v{v} ddepth")
+        assert (gxy[vis & ~act] == 0).all() and (gco[vis & ~act] == 0).all() and (grz[vis & ~act] == 0).all()
+
+
+# --------------------------------------------------------------------------
 # active set: bit mask, ascending list and count, bit-exact
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [1, 31, 32, 1000, 1025, 70001, 2_500_000])
@@ -336,6 +427,13 @@ def test_active_chain_end_to_end():
     pipe.render_bwd_active(tC, error=False, masked=True)
     pipe.project_bwd_active(g, camt)
     torch.cuda.synchronize()
+    full_walk = {k: _np(t).copy() for k, t in pipe.grads.items()}, _np(pipe.dxi).copy()
+    # the specialised path: forward records the walk's start, the walk skips
+    # everything behind each pixel's last active entry
+    pipe.render_fwd_active()
+    pipe.render_bwd_active(tC, error=False, masked=True, from_state=True)
+    pipe.project_bwd_active(g, camt)
+    torch.cuda.synchronize()
     assert int(_np(pipe.active_counts)[0]) == lst.size and 0 < lst.size < n
     np.testing.assert_array_equal(_np(pipe.active_list)[:lst.size].view(np.uint32), lst)
     acc = oracle.grads_like(scene)
@@ -345,4 +443,6 @@ def test_active_chain_end_to_end():
         oracle.project_bwd(scene, cam, projs[v]["radius"], oracle.mask_grad2d(g2ds[v], act), acc, dxi[v])
     for k in acc:
         grad_close(_np(pipe.grads[k])[act], acc[k][act], k)
+        grad_close(full_walk[0][k][act], acc[k][act], k + " (whole lists)")
     grad_close(_np(pipe.dxi), dxi, "dxi")
+    grad_close(full_walk[1], dxi, "dxi (whole lists)")
