@@ -70,7 +70,7 @@ def lib():
                                          _P(u32), _P(u32), _P(d),
                                          _P(d), _P(d), _P(d), _P(i32), _P(i32), _P(d), _P(i32),
                                          _P(u64), _P(d), _P(d), _P(ctypes.c_uint8), _P(i32), _P(d),
-                                         _P(d)]
+                                         _P(d), _P(i32)]
             L.orc_render_bwd.argtypes = [i32, i32, _P(d), _P(d), _P(d), _P(d), _P(d),
                                          _P(u32), _P(u32), _P(d),
                                          _P(d), _P(d), _P(d),
@@ -226,6 +226,7 @@ def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0), pix_err=None, a
     bgv = _f64(np.asarray(bg, np.float64))
     out = dict(rgb=np.zeros((3, H, W)), depth=np.zeros((H, W)), T=np.zeros((H, W)),
                n_contrib=np.zeros((H, W), np.int32), n_eval=np.zeros((H, W), np.int32),
+               n_blend=np.zeros((H, W), np.int32),
                wsum=np.zeros((H, W)), fragile=np.zeros((H, W), np.int32),
                sig=np.zeros((H, W), np.uint64))
     n = rec["xy"].shape[0]
@@ -253,7 +254,8 @@ def render_fwd(W, H, rec, vals, ranges_view, bg=(0.0, 0.0, 0.0), pix_err=None, a
                          _ptr(act, np.uint8) if act is not None else None,
                          _ptr(out["act_last"], np.int32) if act is not None else None,
                          _ptr(out["act_T"], np.float64) if act is not None else None,
-                         _ptr(out["act_rest"], np.float64) if act is not None else None)
+                         _ptr(out["act_rest"], np.float64) if act is not None else None,
+                         _ptr(out["n_blend"], np.int32))
     if pe is not None:
         out["gauss_err"] = out["gauss_err"][:n]
     del P

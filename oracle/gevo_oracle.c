@@ -400,7 +400,8 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
                     double* out_rgb, double* out_depth, double* out_T, int32_t* n_contrib,
                     int32_t* n_eval, double* wsum, int32_t* fragile, uint64_t* sig,
                     const double* pix_err, double* gauss_err,
-                    const uint8_t* active, int32_t* act_last, double* act_T, double* act_rest)
+                    const uint8_t* active, int32_t* act_last, double* act_T, double* act_rest,
+                    int32_t* n_blend)
 {
     /* pix_err / gauss_err (both NULL or both set): the per-Gaussian rendering
      * error of Section III-B2 (Eq. 5), E(g) += w(g, u) e(u) summed over the
@@ -419,7 +420,7 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
             const int32_t tile = (py / ORC_TILE) * tiles_x + (px / ORC_TILE);
             const uint32_t s = ranges[2*tile], e = ranges[2*tile+1];
             double T = 1.0, C[3] = {0, 0, 0}, Dd = 0.0, ws = 0.0;
-            int32_t last = 0, ne = 0, frag = 0, la = 0;
+            int32_t last = 0, ne = 0, frag = 0, la = 0, nbl = 0;
             double Ta = 1.0, Ca[3] = {0, 0, 0}, Da = 0.0;   /* colour, depth through the last active entry */
             uint64_t h = 0x1234567ULL;
             for (uint32_t i = s; i < e; i++) {
@@ -446,6 +447,7 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
                 ws += w;
                 T = Tn;
                 last = (int32_t)(i - s + 1);
+                nbl++;
                 if (active && active[g]) {
                     la = last;
                     Ta = T;
@@ -459,6 +461,7 @@ void orc_render_fwd(int32_t W, int32_t H, const double* xy, const double* conic,
             out_T[pix] = T;
             n_contrib[pix] = last;
             if (n_eval) n_eval[pix] = ne;
+            if (n_blend) n_blend[pix] = nbl;
             if (wsum) wsum[pix] = ws;
             if (fragile) fragile[pix] = frag;
             if (sig) sig[pix] = mix64(h, (uint64_t)last);

@@ -297,6 +297,7 @@ def test_stacked_opaque_gaussians_and_stop_rule():
     assert out["depth"][8, 8] == pytest.approx(0.99 * 1.0 + 0.009 * 2.0, rel=1e-12)
     assert out["n_contrib"][8, 8] == 2
     assert out["n_eval"][8, 8] == 3
+    assert out["n_blend"][8, 8] == 2
 
 
 def test_skipped_entries_before_last_blend_are_counted():
@@ -306,6 +307,7 @@ def test_skipped_entries_before_last_blend_are_counted():
     out, _ = _render(16, 16, rec)
     assert out["n_contrib"][4, 4] == 2
     assert out["n_eval"][4, 4] == 2
+    assert out["n_blend"][4, 4] == 1   # the skipped front entry is walked, not blended
 
 
 def test_partition_of_unity_and_constant_colour():
