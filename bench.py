@@ -149,7 +149,13 @@ def run_reference(args, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-FLOP_FWD, FLOP_BWD = 24, 71   # FP32 FLOPs per evaluated list entry (FMA = 2)
+# Algorithmic FP32 FLOPs (FMA = 2; ex2 and rcp on the MUFU not counted).  Every
+# examined list entry costs the offset and power (10) and alpha = min(0.99,
+# o G) (2); a blended entry adds, in the forward, T (1 - alpha), alpha T and the
+# colour + depth sums (11) and, in the reverse walk, T recovery, weight,
+# dL/dalpha, suffix update, colour / depth / opacity / conic / mean terms and
+# the sum of its 10 gradient values over pixels (49).
+FLOP_EXAMINE, FLOP_BLEND_FWD, FLOP_BLEND_BWD = 12, 11, 49
 
 
 def main():
@@ -190,7 +196,7 @@ def main():
     torch.cuda.empty_cache()
 
     rep = BatchedReplay(g, cams, target_rgb, target_depth, lambda_depth=1.0)
-    E_fwd, E_bwd = rep.eval_counts()
+    E_fwd, E_bwd, B = rep.eval_counts(blended=True)
     rep.capture()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     nst = len(rep.stages())
@@ -303,9 +309,9 @@ def main():
     work = {  # (bound, algorithmic amount per launch, unit)
         "project": ("hbm", param_b * N + 48 * vis + 8 * (VN - vis), "GB/s"),
         "bin_sort": ("hbm", 24 * VN + 4 * vis + 28 * D + 16 * rep.pipe.T, "GB/s"),
-        "render_fwd": ("alu", FLOP_FWD * E_fwd, "TFLOP/s"),
+        "render_fwd": ("alu", FLOP_EXAMINE * E_fwd + FLOP_BLEND_FWD * B, "TFLOP/s"),
         "loss": ("hbm", 48 * P + 4 * VN + 40 * vis, "GB/s"),
-        "render_bwd": ("alu", FLOP_BWD * E_bwd, "TFLOP/s"),
+        "render_bwd": ("alu", FLOP_EXAMINE * E_bwd + FLOP_BLEND_BWD * B, "TFLOP/s"),
         "project_bwd": ("hbm", 2 * param_b * N + 4 * VN + 40 * vis, "GB/s"),
     }
     kernels = {"project": "k_project_fwd", "bin_sort": "k_count_smem+k_scan+k_scatter_smem+k_segsort",
@@ -331,6 +337,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "views": V, "gaussians": int(g["means"].shape[0]),
                        "duplicates": rep.n_dup, "evals_fwd": E_fwd, "evals_bwd": E_bwd,
+                       "blended": B,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed (256 MB write) between timed steps",
                        "tuning_fwd": rep.tuning_fwd, "tuning_bwd": rep.tuning_bwd,

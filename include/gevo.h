@@ -248,6 +248,15 @@ gevo_status gevo_render_fwd(const gevo_layout* layout, int32_t n, const gevo_pro
                             uint32_t* n_eval, const gevo_tuning* tuning, void* workspace,
                             void* stream);
 
+/* gevo_render_fwd with n_eval and, in n_blend (DEVICE uint32[total_pixels],
+ * written), the number of entries each pixel blends: the counts the work of
+ * the blend and of its reverse walk is measured in. */
+gevo_status gevo_render_fwd_counts(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
+                                   const uint32_t* vals, const uint32_t* ranges, const float* bg,
+                                   float* rgb, float* depth, float* T_final, uint32_t* n_contrib,
+                                   uint32_t* n_eval, uint32_t* n_blend, const gevo_tuning* tuning,
+                                   void* workspace, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Stage a6: reverse walk                                                   */
 /* ---------------------------------------------------------------------- */

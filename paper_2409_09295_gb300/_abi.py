@@ -75,7 +75,8 @@ EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin
            "gevo_render_fwd", "gevo_render_bwd", "gevo_project_bwd", "gevo_loss_l1",
            "gevo_last_error", "gevo_status_str", "gevo_version", "gevo_bin_sort_noalloc",
            "gevo_grad2d_zero", "gevo_gemm_bf16", "gevo_loss_l1_err", "gevo_render_bwd_active",
-           "gevo_active_set", "gevo_project_bwd_active", "gevo_render_fwd_active"]
+           "gevo_active_set", "gevo_project_bwd_active", "gevo_render_fwd_active",
+           "gevo_render_fwd_counts"]
 
 # Every symbol include/gevo_prior.h declares, with its argument kinds
 # (i: int32, u: uint32, I: int64, f: float, p: pointer; the last p is the stream).
@@ -144,6 +145,8 @@ def load(build_if_missing: bool = True):
     L.gevo_render_bwd_active.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp,
                                          vp, vp, vp, vp, P(ActiveState), P(Grad2d), P(Tuning), vp,
                                          vp]
+    L.gevo_render_fwd_counts.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp,
+                                         vp, vp, P(Tuning), vp, vp]
     L.gevo_render_fwd_active.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp,
                                          vp, P(ActiveState), P(Tuning), vp, vp]
     L.gevo_active_set.argtypes = [i32, i32, vp, f32, vp, vp, vp, vp, vp]
@@ -161,7 +164,7 @@ def load(build_if_missing: bool = True):
     for name in ("gevo_project", "gevo_bin_sort", "gevo_render_fwd", "gevo_render_bwd",
                  "gevo_project_bwd", "gevo_loss_l1", "gevo_last_error", "gevo_loss_l1_err",
                  "gevo_render_bwd_active", "gevo_active_set", "gevo_project_bwd_active",
-                 "gevo_render_fwd_active"):
+                 "gevo_render_fwd_active", "gevo_render_fwd_counts"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -292,6 +295,17 @@ def active_state_struct(state):
     if state is None:
         return None
     return ActiveState(_p(state["last"]), _p(state["T"]), _p(state["rest"]))
+
+
+def gevo_render_fwd_counts(layout, n, proj: dict, vals, ranges, bg, rgb, depth, T_final,
+                           n_contrib, n_eval, n_blend, ws, tuning=None, stream=None):
+    P_ = proj_struct(proj)
+    bgv = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    tu = tuning_struct(tuning)
+    _check("gevo_render_fwd_counts", load().gevo_render_fwd_counts(
+        ctypes.byref(layout), int(n), ctypes.byref(P_), _p(vals), _p(ranges), bgv, _p(rgb),
+        _p(depth), _p(T_final), _p(n_contrib), _p(n_eval), _p(n_blend),
+        ctypes.byref(tu) if tu is not None else None, _p(ws), _stream(stream)))
 
 
 def gevo_render_fwd_active(layout, n, proj: dict, vals, ranges, bg, rgb, depth, T_final,

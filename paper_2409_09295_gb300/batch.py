@@ -23,6 +23,7 @@ import itertools
 
 import torch
 
+from . import _abi
 from .raster import Pipeline, camera_tensor
 
 CANDIDATES = [dict(threads_per_tile=t, persistent=p, blocks_per_sm=0)
@@ -169,15 +170,20 @@ class BatchedReplay:
             if events is not None:
                 events[i + 1].record()
 
-    def eval_counts(self):
+    def eval_counts(self, blended=False):
         """(E_fwd, E_bwd): list entries examined by the blend (including skips and
-        the stopping entry) and entries walked by the backward (sum of n_contrib)."""
+        the stopping entry) and entries walked by the backward (sum of n_contrib);
+        with blended=True also B, the entries blended."""
         p = self.pipe
         p.project(self.g, self.camt)
         p.bin_sort()
-        p.render_fwd(self.bg, n_eval=True, tuning=self.tuning_fwd)
+        nb = torch.zeros_like(p.n_eval)
+        _abi.gevo_render_fwd_counts(p.layout, p.n, p.proj, p.vals, p.ranges, self.bg, p.rgb,
+                                    p.depth, p.T_final, p.n_contrib, p.n_eval, nb, p.ws,
+                                    self.tuning_fwd)
         torch.cuda.synchronize()
-        return int(p.n_eval.sum(dtype=torch.int64)), int(p.n_contrib.sum(dtype=torch.int64))
+        out = (int(p.n_eval.sum(dtype=torch.int64)), int(p.n_contrib.sum(dtype=torch.int64)))
+        return out + (int(nb.sum(dtype=torch.int64)),) if blended else out
 
 
 class PlainReplay:

@@ -97,7 +97,8 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
              uint32_t* __restrict__ out_nc, uint32_t* __restrict__ out_ne,
              const uint32_t* __restrict__ order, uint32_t* queue, int n_items,
              const uint32_t* __restrict__ active, uint32_t* __restrict__ act_last,
-             float* __restrict__ act_T, float4* __restrict__ act_rest)
+             float* __restrict__ act_T, float4* __restrict__ act_rest,
+             uint32_t* __restrict__ out_nb)
 {
     constexpr int NT = 256 / PPT;
     __shared__ float2 s_xy[kBatch];
@@ -134,12 +135,12 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
 
         float T[PPT], C0[PPT], C1[PPT], C2[PPT], Dp[PPT];
         float B0[PPT], B1[PPT], B2[PPT], BD[PPT], Ta[PPT];   // colour, depth through the last active entry
-        uint32_t last[PPT], cnt[PPT], la[PPT];
+        uint32_t last[PPT], cnt[PPT], la[PPT], nbl[PPT];
         bool done[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
             T[k] = 1.f; C0[k] = C1[k] = C2[k] = Dp[k] = 0.f;
-            last[k] = 0u; cnt[k] = 0u;
+            last[k] = 0u; cnt[k] = 0u; nbl[k] = 0u;
             done[k] = !(px < W && py0 + k < H);
             if (ACT) { B0[k] = B1[k] = B2[k] = BD[k] = 0.f; Ta[k] = 1.f; la[k] = 0u; }
         }
@@ -208,6 +209,7 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     Dp[k] = __fmaf_rn(w, r.w, Dp[k]);
                     T[k] = bl ? Tn : T[k];
                     last[k] = bl ? pos1 : last[k];
+                    if (COUNT) nbl[k] += bl ? 1u : 0u;
                 }
                 if (ACT && s_act[j]) {
                     // an active entry: move the part since the previous one
@@ -254,7 +256,10 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 out_d[gp] = Dp[k];
                 out_T[gp] = T[k];
                 out_nc[gp] = last[k];
-                if (COUNT) out_ne[gp] = cnt[k];
+                if (COUNT) {
+                    out_ne[gp] = cnt[k];
+                    if (out_nb) out_nb[gp] = nbl[k];
+                }
             }
         }
     }
@@ -526,7 +531,12 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     }
                     continue;
                 }
-                float a_xy0 = 0.f, a_xy1 = 0.f, a_ca = 0.f, a_cb = 0.f, a_cc = 0.f, a_o = 0.f;
+                // A thread's pixels share the column, so dx is the same for all
+                // of them: the conic and mean gradients are linear in the
+                // per-pixel dp = dL/dalpha * alpha with coefficients in 1, dy,
+                // dy^2, so the pixel loop keeps three moments and the
+                // coefficients are applied once per entry.
+                float m0 = 0.f, m1 = 0.f, m2 = 0.f, a_o = 0.f;
                 float a_r = 0.f, a_g = 0.f, a_b = 0.f, a_z = 0.f, a_e = 0.f;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
@@ -539,28 +549,37 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     T[k] = Ti;
                     const float w = alpha * Ti;
                     if (EXT) a_e += w * pe[k];
-                    float dLda = gC0[k] * (r.x - S0[k]) + gC1[k] * (r.y - S1[k]) +
-                                 gC2[k] * (r.z - S2[k]);
-                    if (DD) dLda += gD[k] * (r.w - SD[k]);
+                    // colour behind minus this entry's colour, shared by dL/dalpha
+                    // and the suffix update S <- S + alpha (c - S)
+                    const float d0 = r.x - S0[k], d1 = r.y - S1[k], d2 = r.z - S2[k];
+                    const float dD = DD ? r.w - SD[k] : 0.f;
+                    float dLda = gC0[k] * d0 + gC1[k] * d1 + gC2[k] * d2;
+                    if (DD) dLda += gD[k] * dD;
                     dLda = dLda * Ti;
                     if (DT) dLda -= gTT[k] * inv;
-                    S0[k] = alpha * r.x + om * S0[k];
-                    S1[k] = alpha * r.y + om * S1[k];
-                    S2[k] = alpha * r.z + om * S2[k];
-                    if (DD) SD[k] = alpha * r.w + om * SD[k];
+                    S0[k] += alpha * d0;
+                    S1[k] += alpha * d1;
+                    S2[k] += alpha * d2;
+                    if (DD) SD[k] += alpha * dD;
                     a_r += gC0[k] * w; a_g += gC1[k] * w; a_b += gC2[k] * w;
                     if (DD) a_z += gD[k] * w;
                     if (__fmul_rn(c.w, G[k]) <= kAlphaMax) {
                         a_o += dLda * G[k];
                         const float dp = dLda * alpha;
-                        a_ca += -0.5f * dx * dx * dp;
-                        a_cb += -dx * dy * dp;
-                        a_cc += -0.5f * dy * dy * dp;
-                        const float sc = dp * kLn2;
-                        a_xy0 += sc * (2.f * c.x * dx + c.y * dy);
-                        a_xy1 += sc * (2.f * c.z * dy + c.y * dx);
+                        const float t = dp * dy;
+                        m0 += dp;
+                        m1 += t;
+                        m2 += t * dy;
                     }
                 }
+                // d alpha / d(a, b, c) = alpha (-dx^2 / 2, -dx dy, -dy^2 / 2);
+                // d alpha / d(mean) = alpha ln2 (2 a' dx + b' dy, 2 c' dy + b' dx)
+                // with the pre-scaled conic (a', b', c')
+                const float a_ca = -0.5f * dx * dx * m0;
+                const float a_cb = -dx * m1;
+                const float a_cc = -0.5f * m2;
+                const float a_xy0 = kLn2 * (2.f * c.x * dx * m0 + c.y * m1);
+                const float a_xy1 = kLn2 * (2.f * c.z * m1 + c.y * dx * m0);
                 if (EXT) {
                     const float vals12[12] = {a_xy0, a_xy1, a_ca, a_cb, a_cc, a_o,
                                               a_r,   a_g,   a_b,  a_z,  a_e,  0.f};
@@ -615,7 +634,7 @@ static gevo_status launch_fwd(const gevo_layout& L, int n, const gevo_proj& p, c
                               const uint32_t* ranges, const float* bg, float* rgb, float* depth,
                               float* Tf, uint32_t* nc, uint32_t* ne, const gevo_tuning* t,
                               char* ws, cudaStream_t st, const uint32_t* active = nullptr,
-                              const gevo_active_state* as = nullptr)
+                              const gevo_active_state* as = nullptr, uint32_t* nb = nullptr)
 {
     const WsLayout w = ws_layout(L, n, 0);
     const uint32_t* order = reinterpret_cast<const uint32_t*>(ws + w.tile_order);
@@ -633,7 +652,7 @@ static gevo_status launch_fwd(const gevo_layout& L, int n, const gevo_proj& p, c
         reinterpret_cast<const float4*>(p.rgb_depth), vals, reinterpret_cast<const uint2*>(ranges),
         bg[0], bg[1], bg[2], rgb, depth, Tf, nc, ne, order, queue, L.total_tiles, active,
         as ? as->last : nullptr, as ? as->T : nullptr,
-        as ? reinterpret_cast<float4*>(as->rest) : nullptr);
+        as ? reinterpret_cast<float4*>(as->rest) : nullptr, nb);
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }
@@ -709,6 +728,31 @@ extern "C" gevo_status gevo_render_fwd(const gevo_layout* layout, int32_t n, con
     case 4: return launch_fwd<4>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
     case 2: return launch_fwd<2>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
     default: return launch_fwd<1>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st);
+    }
+}
+
+extern "C" gevo_status gevo_render_fwd_counts(const gevo_layout* layout, int32_t n,
+                                              const gevo_proj* proj, const uint32_t* vals,
+                                              const uint32_t* ranges, const float* bg, float* rgb,
+                                              float* depth, float* T_final, uint32_t* n_contrib,
+                                              uint32_t* n_eval, uint32_t* n_blend,
+                                              const gevo_tuning* tuning, void* workspace,
+                                              void* stream)
+{
+    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+        !proj->rgb_depth || !vals || !ranges || !bg || !rgb || !depth || !T_final || !n_contrib ||
+        !n_eval || !n_blend || !workspace || !gevo_aligned(workspace, 256) ||
+        !valid_tuning(tuning) || !gevo_aligned(ranges, 8) ||
+        !gevo_aligned(proj->conic_opacity, 16) || !gevo_aligned(proj->rgb_depth, 16) ||
+        !gevo_aligned(proj->xy, 8))
+        return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = reinterpret_cast<char*>(workspace);
+    switch (pick_ppt(tuning)) {
+    case 8: return launch_fwd<8>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st, nullptr, nullptr, n_blend);
+    case 4: return launch_fwd<4>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st, nullptr, nullptr, n_blend);
+    case 2: return launch_fwd<2>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st, nullptr, nullptr, n_blend);
+    default: return launch_fwd<1>(*layout, n, *proj, vals, ranges, bg, rgb, depth, T_final, n_contrib, n_eval, tuning, ws, st, nullptr, nullptr, n_blend);
     }
 }
 

@@ -119,8 +119,17 @@ def test_render_fwd_staged_1e5(tuning):
     sizes = [(96, 80), (53, 37)]
     rec, b, pipe = _staged(sizes, 2500, seed=50)
     bg = (0.1, 0.2, 0.3)
+    n_blend = torch.zeros_like(pipe.n_eval)
+    from paper_2409_09295_gb300 import _abi
+    _abi.gevo_render_fwd_counts(pipe.layout, pipe.n, pipe.proj, pipe.vals, pipe.ranges, bg, pipe.rgb,
+                                pipe.depth, pipe.T_final, pipe.n_contrib, pipe.n_eval, n_blend, pipe.ws,
+                                tuning)
+    torch.cuda.synchronize()
+    counted = {k: _np(getattr(pipe, k)).copy() for k in ("rgb", "n_contrib", "n_eval")}
     pipe.render_fwd(bg, n_eval=True, tuning=tuning)
     torch.cuda.synchronize()
+    for k, want in counted.items():   # the counting variant renders the same image
+        np.testing.assert_array_equal(_np(getattr(pipe, k)), want, err_msg=k)
     base = 0
     for v, (W, H) in enumerate(sizes):
         nt = tiles_of(W, H)
@@ -128,6 +137,7 @@ def test_render_fwd_staged_1e5(tuning):
         base += nt
         ok = o["fragile"] == 0
         assert ok.mean() > 0.97
+        np.testing.assert_array_equal(_np(pipe.view_plane(n_blend, v))[ok], o["n_blend"][ok])
         np.testing.assert_allclose(_np(pipe.view_rgb(pipe.rgb, v))[:, ok], o["rgb"][:, ok], atol=1e-5, rtol=0)
         np.testing.assert_allclose(_np(pipe.view_plane(pipe.depth, v))[ok], o["depth"][ok], atol=1e-5 * 10, rtol=1e-5)
         np.testing.assert_allclose(_np(pipe.view_plane(pipe.T_final, v))[ok], o["T"][ok], atol=1e-5, rtol=0)
