@@ -57,8 +57,8 @@ def gaussian_step(raw, grads, state, lr, t, b1=0.9, b2=0.999, eps=1e-15, lam_iso
 
     raw: dict GROUPS -> arrays; grads: gradients w.r.t. the rasterizer inputs
     (means, scales, quats, opacities, sh); state: dict group -> (m, v); lr:
-    dict group -> learning rate (0 = frozen; the SH group takes lr["sh"] for
-    the degree-0 row and lr["sh_rest"] for the others); rows: indices of the
+    dict group -> learning rate (0 = frozen: value and moments unchanged; the SH
+    group takes lr["sh"] for the degree-0 row and lr["sh_rest"] for the others); rows: indices of the
     Gaussians being optimised (None = all); E_iso over those rows with weight
     lam_iso is added to the scale gradient.  Returns (raw', state', E_iso)."""
     idx = np.arange(raw["means"].shape[0]) if rows is None else np.asarray(rows, np.int64)
@@ -71,11 +71,14 @@ def gaussian_step(raw, grads, state, lr, t, b1=0.9, b2=0.999, eps=1e-15, lam_iso
         if k == "sh":
             lrs = np.full(out["sh"].shape[1:], lr["sh_rest"])
             lrs[0] = lr["sh"]
-            lrs = lrs[None]
+            lrs = np.broadcast_to(lrs[None], out["sh"][idx].shape)
         else:
-            lrs = lr[k]
+            lrs = np.broadcast_to(np.float64(lr[k]), out[k][idx].shape)
         p2, m2, v2 = adam(out[k][idx], chained[k], m[idx], v[idx], lrs, b1, b2, eps, t)
-        out[k][idx], m[idx], v[idx] = p2, m2, v2
+        live = lrs != 0.0            # a zero learning rate freezes the value and its moments
+        out[k][idx] = np.where(live, p2, out[k][idx])
+        m[idx] = np.where(live, m2, m[idx])
+        v[idx] = np.where(live, v2, v[idx])
     return out, st, E
 
 

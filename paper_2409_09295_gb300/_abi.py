@@ -65,6 +65,18 @@ class ActiveState(ctypes.Structure):
     _fields_ = [("last", ctypes.c_void_p), ("T", ctypes.c_void_p), ("rest", ctypes.c_void_p)]
 
 
+class MapParams(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("logit_opacities", ctypes.c_void_p),
+                ("colours", ctypes.c_void_p)]
+
+
+class MapAdam(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in (
+        "lr_means", "lr_log_scales", "lr_quats", "lr_logit_opacities", "lr_colour_dc",
+        "lr_colour_rest", "beta1", "beta2", "eps", "lambda_iso")]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("threads_per_tile", ctypes.c_int32), ("persistent", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32)]
@@ -100,6 +112,11 @@ PRIOR = {
     "gevo_to_bf16": "Ippp",
 }
 EXPORTS = EXPORTS + list(PRIOR)
+
+# Every symbol include/gevo_map.h declares.
+MAP = ["gevo_map_activate", "gevo_map_step", "gevo_pose_step", "gevo_prune_keep",
+       "gevo_gather_rows"]
+EXPORTS = EXPORTS + MAP
 
 _lib = None
 
@@ -153,6 +170,14 @@ def load(build_if_missing: bool = True):
     L.gevo_project_bwd_active.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d), vp, vp,
                                           P(GaussianGrads), vp, vp, vp]
     L.gevo_last_error.argtypes = [vp, vp]
+    L.gevo_map_activate.argtypes = [i32, vp, vp, vp, vp, vp]
+    L.gevo_map_step.argtypes = [i32, i32, P(MapParams), P(GaussianGrads), P(MapParams),
+                                P(MapParams), P(MapAdam), i32, vp, vp, vp, vp, vp, vp]
+    L.gevo_pose_step.argtypes = [i32, vp, vp, vp, vp, f32, f32, f32, f32, f32, i32, vp, vp]
+    L.gevo_prune_keep.argtypes = [i32, vp, vp, f32, vp, vp, vp, vp]
+    L.gevo_gather_rows.argtypes = [i32, vp, vp, i32, vp, vp, vp]
+    for name in MAP:
+        getattr(L, name).restype = ctypes.c_int
     L.gevo_status_str.argtypes = [ctypes.c_int]
     L.gevo_status_str.restype = ctypes.c_char_p
     L.gevo_version.restype = i32
@@ -430,3 +455,51 @@ def prior_call(name, *args, stream=None):
         else:
             conv.append(a)
     _check(name, getattr(load(), name)(*conv, _stream(stream)))
+
+
+# ---- map and pose optimisation (include/gevo_map.h) ---------------------------------
+def map_params_struct(d: dict) -> MapParams:
+    return MapParams(_p(d["means"]), _p(d["log_scales"]), _p(d["quats"]),
+                     _p(d["logit_opacities"]), _p(d["colours"]))
+
+
+def map_adam_struct(cfg: dict) -> MapAdam:
+    return MapAdam(*[float(cfg[k]) for k, _ in MapAdam._fields_])
+
+
+def gevo_map_activate(n, log_scales, logit_opacities, scales, opacities, stream=None):
+    _check("gevo_map_activate", load().gevo_map_activate(
+        int(n), _p(log_scales), _p(logit_opacities), _p(scales), _p(opacities), _stream(stream)))
+
+
+def gevo_map_step(n, K, params: dict, grads: dict, m: dict, v: dict, cfg: dict, step, rows,
+                  counts, scales, opacities, iso_loss=None, stream=None):
+    G = GaussianGrads()
+    G.means, G.scales, G.quats, G.opacities = (_p(grads["means"]), _p(grads["scales"]),
+                                               _p(grads["quats"]), _p(grads["opacities"]))
+    G.sh = _p(grads.get("sh"))
+    G.rgb = _p(grads.get("rgb"))
+    Pp, Mm, Vv = map_params_struct(params), map_params_struct(m), map_params_struct(v)
+    C = map_adam_struct(cfg)
+    _check("gevo_map_step", load().gevo_map_step(
+        int(n), int(K), ctypes.byref(Pp), ctypes.byref(G), ctypes.byref(Mm), ctypes.byref(Vv),
+        ctypes.byref(C), int(step), _p(rows), _p(counts), _p(scales), _p(opacities),
+        _p(iso_loss), _stream(stream)))
+
+
+def gevo_pose_step(n_views, cams, dxi, m, v, lr_rho, lr_phi, beta1, beta2, eps, step, fixed=None,
+                   stream=None):
+    _check("gevo_pose_step", load().gevo_pose_step(
+        int(n_views), _p(cams), _p(dxi), _p(m), _p(v), float(lr_rho), float(lr_phi), float(beta1),
+        float(beta2), float(eps), int(step), _p(fixed), _stream(stream)))
+
+
+def gevo_prune_keep(n, opacities, candidates, threshold, keep, keep_list, counts, stream=None):
+    _check("gevo_prune_keep", load().gevo_prune_keep(
+        int(n), _p(opacities), _p(candidates), float(threshold), _p(keep), _p(keep_list),
+        _p(counts), _stream(stream)))
+
+
+def gevo_gather_rows(n_max, lst, counts, width, src, dst, stream=None):
+    _check("gevo_gather_rows", load().gevo_gather_rows(
+        int(n_max), _p(lst), _p(counts), int(width), _p(src), _p(dst), _stream(stream)))

@@ -9,6 +9,7 @@
 //   2. k_active_scan: one block turns the block counts into exclusive offsets
 //      and the total;
 //   3. k_active_list: each block writes its active indices at its offset.
+#include "../../include/gevo_map.h"
 #include "gevo_internal.cuh"
 
 namespace gevo {
@@ -96,6 +97,34 @@ k_active_list(int n, const uint32_t* __restrict__ bits, const uint32_t* __restri
     if ((word >> lane) & 1u) list[off + __popc(word & ((1u << lane) - 1u))] = (uint32_t)g;
 }
 
+// Pruning after the global stage: keep unless a candidate with opacity below
+// the threshold.
+__global__ void __launch_bounds__(kActBlock)
+k_keep_bits(int n, const float* __restrict__ opac, const uint32_t* __restrict__ cand, float thresh,
+            uint32_t* __restrict__ bits, uint32_t* __restrict__ block_count)
+{
+    __shared__ uint32_t s_cnt[kActBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = blockIdx.x * kActBlock + threadIdx.x;
+    const int w = g >> 5;
+    bool keep = false;
+    if (g < n) {
+        const bool c = !cand || ((__ldg(cand + w) >> lane) & 1u);
+        keep = !(c && opac[g] < thresh);
+    }
+    const uint32_t word = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) {
+        if (w < (n + 31) / 32) bits[w] = word;
+        s_cnt[warp] = __popc(word);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int i = 0; i < kActBlock / 32; i++) t += s_cnt[i];
+        block_count[blockIdx.x] = t;
+    }
+}
+
 }  // namespace gevo
 
 using namespace gevo;
@@ -115,6 +144,24 @@ extern "C" gevo_status gevo_active_set(int32_t n_views, int32_t n, const float* 
     k_active_scan<<<1, 1024, 0, st>>>(nb, counts);
     GEVO_CHECK_LAUNCH();
     k_active_list<<<nb, kActBlock, 0, st>>>(n, active, counts, active_list);
+    GEVO_CHECK_LAUNCH();
+    return GEVO_OK;
+}
+
+extern "C" gevo_status gevo_prune_keep(int32_t n, const float* opacities, const uint32_t* candidates,
+                                       float threshold, uint32_t* keep, uint32_t* keep_list,
+                                       uint32_t* counts, void* stream)
+{
+    if (n < 0 || n > INT32_MAX - kActBlock || !opacities || !keep || !keep_list || !counts)
+        return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) return cudaMemsetAsync(counts, 0, 4, st) == cudaSuccess ? GEVO_OK : GEVO_ERR_CUDA;
+    const int nb = (n + kActBlock - 1) / kActBlock;
+    k_keep_bits<<<nb, kActBlock, 0, st>>>(n, opacities, candidates, threshold, keep, counts + 1);
+    GEVO_CHECK_LAUNCH();
+    k_active_scan<<<1, 1024, 0, st>>>(nb, counts);
+    GEVO_CHECK_LAUNCH();
+    k_active_list<<<nb, kActBlock, 0, st>>>(n, keep, counts, keep_list);
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }
