@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mapping", action="store_true")
     return ap.parse_args()
 
 
@@ -292,6 +293,7 @@ def main():
                   "ms_per_step": pms}
 
     active_line = active_set_section(rep, target_rgb, target_depth, flush, stage_ms)
+    mapping_line = mapping_section() if not args.no_mapping else None
 
     # ---- rooflines (algorithmic work per launch / live event time) ---------------------
     pk = peaks()
@@ -347,6 +349,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": None, "roofline": roof, "clocks": clk, "active_set": active_line,
+            "mapping": mapping_line,
             "wall_s_timed": wall1 - wall0}
     line["gpu_launches"] = launches_per_step(rep) * args.steps
 
@@ -433,6 +436,23 @@ def active_set_section(rep, target_rgb, target_depth, flush, stage_ms, reps=10):
             "backward_speedup_whole_lists": full / (ms["render_bwd_masked"] + ms["project_bwd_masked"]),
             "note": "E_k from the step's own render vs the stop-gradient targets; eps = 85th "
                     "percentile of max_k E_k(g) over the Gaussians some view blends (seen)"}
+
+
+def mapping_section():
+    """One mapping update (local + global stage) on the same room, at 640x480:
+    8 window keyframes, 4 past poses for E_pc, the 52k-Gaussian box as the
+    local map; median device time per iteration and the loss trajectory."""
+    import numpy as np
+
+    from paper_2409_09295_gb300.mapping import room_update
+    r = room_update(local_iters=10, global_iters=10)
+    med = lambda x: float(np.median(x[1:]))
+    return {"local_iter_ms": med(r["local_iter_ms"]), "global_iter_ms": med(r["global_iter_ms"]),
+            "local_loss": [r["local_losses"][0], r["local_losses"][-1]],
+            "global_loss": [r["global_losses"][0], r["global_losses"][-1]],
+            "active": r["active"], "error_active": r["error_active"], "pruned": r["pruned"],
+            "map_size": r["map_size"], "window": r["window"], "past": r["past"], "image": r["image"],
+            "note": "10 + 10 iterations; the full-backward global stage (exact pose gradient)"}
 
 
 def launches_per_step(rep) -> int:

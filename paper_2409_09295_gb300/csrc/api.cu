@@ -9,7 +9,6 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap)
 {
-    (void)n;
     WsLayout w;
     size_t T = (size_t)L.total_tiles;
     size_t o = 0;
@@ -21,6 +20,9 @@ WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap)
     w.dup_tmp = o;      o = align256(o + 8 * (size_t)cap);
     w.dup_tmp2 = o;     o = align256(o + 8 * (size_t)cap);
     w.dxi_acc = o;      o = align256(o + 4 * 6 * (size_t)GEVO_MAX_VIEWS);
+    w.core = o;
+    const size_t nbx = ((size_t)(n > 0 ? n : 0) + kBinChunk - 1) / kBinChunk;
+    w.blk_off = o;      o = align256(o + 4 * nbx * T);
     w.total = o;
     return w;
 }

@@ -42,56 +42,69 @@ k_count(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restri
     }
 }
 
-// One block of 1024 threads.
+// One block of 1024 threads.  Warp w owns a contiguous chunk of the tiles and
+// walks it 32 tiles at a time (coalesced loads, warp scans with a carry); the
+// warps' chunk totals are scanned once in shared memory.  The heaviest-first
+// order buckets tiles by floor(log2(count)); bucket counts and positions are
+// taken with one shared-memory atomic per distinct bucket per warp step.
 __global__ void __launch_bounds__(1024)
 k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* __restrict__ tile_start,
        uint32_t* __restrict__ tile_cursor, uint32_t* __restrict__ tile_order,
        uint32_t* __restrict__ ranges, uint64_t* __restrict__ d_n_dup, uint32_t* err)
 {
-    __shared__ unsigned long long s_warp[32];
+    constexpr int NW = 32;
+    __shared__ unsigned long long s_warp[NW];
     __shared__ uint32_t s_bucket[34];
     __shared__ uint32_t s_bucket_base[34];
     __shared__ unsigned long long s_total;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (T + blockDim.x - 1) / blockDim.x;
-    const int lo = min(T, tid * per), hi = min(T, lo + per);
+    const int chunk = ((T + NW - 1) / NW + 31) & ~31;
+    const int w0 = min(T, warp * chunk), w1 = min(T, w0 + chunk);
+    const uint32_t lt = (1u << lane) - 1u;
     if (tid < 34) s_bucket[tid] = 0;
-    unsigned long long mine = 0;
-    for (int t = lo; t < hi; t++) mine += tile_count[t];
-    // block exclusive scan of `mine`
-    unsigned long long incl = mine;
+    unsigned long long sum = 0;
+    for (int t = w0 + lane; t < w1; t += 32) sum += tile_count[t];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) s_warp[warp] = incl;
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) s_warp[warp] = sum;
     __syncthreads();
     if (warp == 0) {
-        unsigned long long w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0ull;
-        unsigned long long wi = w;
+        const unsigned long long x = s_warp[lane];
+        unsigned long long incl = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long u = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= o) wi += u;
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
         }
-        s_warp[lane] = wi - w;
-        if (lane == 31) s_total = wi;
+        s_warp[lane] = incl - x;
+        if (lane == 31) s_total = incl;
     }
     __syncthreads();
     const unsigned long long D = s_total;
     const bool overflow = D > cap;
-    unsigned long long run = s_warp[warp] + incl - mine;
-    for (int t = lo; t < hi; t++) {
-        const uint32_t c = tile_count[t];
-        tile_start[t] = (uint32_t)run;
-        tile_cursor[t] = 0u;
-        const bool empty = overflow || c == 0;
-        ranges[2 * t] = empty ? 0u : (uint32_t)run;
-        ranges[2 * t + 1] = empty ? 0u : (uint32_t)(run + c);
-        run += c;
-        const int b = c == 0 ? 0 : 32 - __clz(c);
-        atomicAdd(&s_bucket[b], 1u);
+    unsigned long long carry = s_warp[warp];
+    for (int b0 = w0; b0 < w1; b0 += 32) {
+        const int t = b0 + lane;
+        const bool valid = t < w1;
+        const uint32_t c = valid ? tile_count[t] : 0u;
+        unsigned long long incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const unsigned long long run = carry + incl - c;
+        if (valid) {
+            tile_start[t] = (uint32_t)run;
+            tile_cursor[t] = 0u;
+            const bool empty = overflow || c == 0;
+            ranges[2 * t] = empty ? 0u : (uint32_t)run;
+            ranges[2 * t + 1] = empty ? 0u : (uint32_t)(run + c);
+        }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+        const int b = valid ? (c == 0 ? 0 : 32 - __clz(c)) : 34;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_bucket[b], __popc(peers));
     }
     if (tid == 0) {
         *d_n_dup = D;
@@ -103,11 +116,17 @@ k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* _
         for (int b = 33; b >= 0; b--) { s_bucket_base[b] = acc; acc += s_bucket[b]; }
     }
     __syncthreads();
-    for (int t = lo; t < hi; t++) {
-        const uint32_t c = tile_count[t];
-        const int b = c == 0 ? 0 : 32 - __clz(c);
-        const uint32_t pos = atomicAdd(&s_bucket_base[b], 1u);
-        tile_order[pos] = (uint32_t)t;
+    for (int b0 = w0; b0 < w1; b0 += 32) {
+        const int t = b0 + lane;
+        const bool valid = t < w1;
+        const uint32_t c = valid ? tile_count[t] : 0u;
+        const int b = valid ? (c == 0 ? 0 : 32 - __clz(c)) : 34;
+        const uint32_t peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (valid && lane == leader) base = atomicAdd(&s_bucket_base[b], __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) tile_order[base + __popc(peers & lt)] = (uint32_t)t;
     }
 }
 
@@ -149,7 +168,6 @@ k_scatter(gevo_layout L, int n, const float2* __restrict__ xy, const int* __rest
 // tiles k, k+32, ...), so one large splat does not serialise its warp.
 // ---------------------------------------------------------------------------
 constexpr int kBinThreads = 256;
-constexpr int kBinChunk = 2048;
 constexpr int kBinMaxSmemTiles = 16384;   // views with more tiles use k_count / k_scatter
 
 template <typename F>
@@ -247,6 +265,54 @@ k_scatter_smem(gevo_layout L, int n, const float2* __restrict__ xy, const int* _
         if (c) s_hist[t] = tile_start[base + t] + atomicAdd(tile_cursor + base + t, c);
     }
     __syncthreads();
+    const size_t vb = (size_t)v * n;
+    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int g, int t) {
+        const uint32_t slot = atomicAdd(s_hist + t, 1u);
+        const uint32_t dbits = __float_as_uint(rgbz[vb + g].w);
+        bucket[slot] = ((unsigned long long)dbits << 32) | (uint32_t)g;
+    });
+}
+
+// The same two passes with one histogram: the counting pass keeps, per
+// (block, tile), the old tile count its atomicAdd returned -- the offset of this
+// block's run inside the tile's bucket -- so the scatter pass only adds the
+// tile start and needs neither a second histogram nor global atomics.
+__global__ void __launch_bounds__(kBinThreads)
+k_count_off(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restrict__ radius,
+            uint32_t* __restrict__ tile_count, uint32_t* __restrict__ blk_off)
+{
+    extern __shared__ uint32_t s_hist[];
+    const int v = blockIdx.y;
+    const int nt = L.tiles_x[v] * L.tiles_y[v];
+    for (int t = threadIdx.x; t < nt; t += kBinThreads) s_hist[t] = 0u;
+    __syncthreads();
+    const int g0 = blockIdx.x * kBinChunk, g1 = min(n, g0 + kBinChunk);
+    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int, int t) { atomicAdd(s_hist + t, 1u); });
+    __syncthreads();
+    uint32_t* dst = tile_count + L.tile_base[v];
+    uint32_t* off = blk_off + (size_t)gridDim.x * L.tile_base[v] + (size_t)blockIdx.x * nt;
+    for (int t = threadIdx.x; t < nt; t += kBinThreads) {
+        const uint32_t c = s_hist[t];
+        if (c) off[t] = atomicAdd(dst + t, c);
+    }
+}
+
+__global__ void __launch_bounds__(kBinThreads)
+k_scatter_off(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restrict__ radius,
+              const float4* __restrict__ rgbz, const uint32_t* __restrict__ tile_start,
+              const uint32_t* __restrict__ blk_off, const uint64_t* __restrict__ d_n_dup,
+              uint64_t cap, unsigned long long* __restrict__ bucket)
+{
+    extern __shared__ uint32_t s_hist[];
+    if (*d_n_dup > cap) return;
+    const int v = blockIdx.y;
+    const int nt = L.tiles_x[v] * L.tiles_y[v];
+    const int base = L.tile_base[v];
+    const uint32_t* off = blk_off + (size_t)gridDim.x * base + (size_t)blockIdx.x * nt;
+    // entries of tiles this block does not touch hold stale values and are never used
+    for (int t = threadIdx.x; t < nt; t += kBinThreads) s_hist[t] = tile_start[base + t] + off[t];
+    __syncthreads();
+    const int g0 = blockIdx.x * kBinChunk, g1 = min(n, g0 + kBinChunk);
     const size_t vb = (size_t)v * n;
     for_each_dup(L, v, n, g0, g1, xy, radius, [&](int g, int t) {
         const uint32_t slot = atomicAdd(s_hist + t, 1u);
@@ -402,6 +468,8 @@ static void bin_attributes(size_t bin_smem)
     if (bin_smem > 48 * 1024 && bin_smem > done) {
         cudaFuncSetAttribute(k_count_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
         cudaFuncSetAttribute(k_scatter_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
+        cudaFuncSetAttribute(k_count_off, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
+        cudaFuncSetAttribute(k_scatter_off, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
         done = bin_smem;
     }
 }
@@ -429,6 +497,7 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
     uint32_t* tile_start = reinterpret_cast<uint32_t*>(ws + w.tile_start);
     auto* bucket = reinterpret_cast<unsigned long long*>(ws + w.dup_tmp);
     auto* bucket2 = reinterpret_cast<unsigned long long*>(ws + w.dup_tmp2);
+    uint32_t* blk_off = reinterpret_cast<uint32_t*>(ws + w.blk_off);
     const int T = layout->total_tiles;
 
     if (cudaMemsetAsync(tile_count, 0, sizeof(uint32_t) * T, st) != cudaSuccess) return GEVO_ERR_CUDA;
@@ -444,8 +513,9 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
     if (smem_bins) bin_attributes(bin_smem);
     if (total > 0) {
         if (smem_bins)
-            k_count_smem<<<bin_grid, kBinThreads, bin_smem, st>>>(
-                *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius, tile_count);
+            k_count_off<<<bin_grid, kBinThreads, bin_smem, st>>>(
+                *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius, tile_count,
+                blk_off);
         else
             k_count<<<std::max(grid, 1), 256, 0, st>>>(*layout, n,
                                                        reinterpret_cast<const float2*>(proj->xy),
@@ -457,10 +527,10 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
     GEVO_CHECK_LAUNCH();
     if (total > 0 && dup_capacity > 0) {
         if (smem_bins)
-            k_scatter_smem<<<bin_grid, kBinThreads, bin_smem, st>>>(
+            k_scatter_off<<<bin_grid, kBinThreads, bin_smem, st>>>(
                 *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
-                reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor,
-                d_n_dup, dup_capacity, bucket);
+                reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, blk_off, d_n_dup,
+                dup_capacity, bucket);
         else
             k_scatter<<<std::max(grid, 1), 256, 0, st>>>(
                 *layout, n, reinterpret_cast<const float2*>(proj->xy), proj->radius,
@@ -523,7 +593,7 @@ extern "C" gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t 
     if (dup_capacity > GEVO_NOALLOC_MAX_DUPS || layout->total_tiles > GEVO_NOALLOC_MAX_TILES)
         return GEVO_ERR_SCRATCH_LIMIT;
     const WsLayout w = ws_layout(*layout, n, dup_capacity);
-    if (w.total > GEVO_NOALLOC_SCRATCH_BYTES) return GEVO_ERR_SCRATCH_LIMIT;
+    if (w.core > GEVO_NOALLOC_SCRATCH_BYTES) return GEVO_ERR_SCRATCH_LIMIT;
     char* ws = reinterpret_cast<char*>(noalloc_scratch_address());
     if (!ws) return GEVO_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

@@ -37,9 +37,14 @@ struct WsLayout {
     size_t dup_tmp;      // uint64 [cap]  (depth bits << 32 | id), bucketed by tile
     size_t dup_tmp2;     // uint64 [cap]  ping-pong for long tiles
     size_t dxi_acc;      // float [V][6]
+    size_t core;         // bytes up to here (the no-allocation sort uses only these)
+    size_t blk_off;      // uint32 [ceil(n / 2048)][T]: each binning block's run offset per tile
     size_t total;
 };
 WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap);
+
+// Gaussians per binning block of one view (the binning kernels' chunk).
+constexpr int kBinChunk = 2048;
 
 // Queue-head slots inside the error block.
 constexpr int kQueueFwd = 1;

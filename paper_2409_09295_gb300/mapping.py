@@ -165,6 +165,8 @@ class MapOptimizer:
             cfg["lambda_iso"] = lambda_iso
         losses = []
         K = self.map.K
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
+        ev[0].record()
         for it in range(iters):
             pipe.project(g, camt)
             pipe.bin_sort()
@@ -194,8 +196,11 @@ class MapOptimizer:
             _abi.gevo_pose_step(V, camt, pipe.dxi, pm, pv, self.lr_pose[0], self.lr_pose[1],
                                 cfg["beta1"], cfg["beta2"], cfg["eps"], self.pose_step_no, fixed_t)
             losses.append(pipe.loss.sum() + iso[0])
+            ev[it + 1].record()
         torch.cuda.synchronize()
         assert pipe.last_error() == 0
+        # device time per iteration (host launch gaps included)
+        self.iter_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(iters)]
         return [float(x) for x in torch.stack(losses).cpu()] if losses else []
 
 
@@ -243,6 +248,7 @@ def mapping_update(global_map: GaussianMap, local: GaussianMap, window_cams, win
     opt = MapOptimizer(both, adam)
     rep["local_losses"] = opt.iterate(window_cams, cam_w, window_images, local_iters,
                                       active=(local_bits, local_rows, counts))
+    rep["local_iter_ms"] = opt.iter_ms
     local_opt = both.rows(first, n_all)
     del both
 
@@ -283,6 +289,7 @@ def mapping_update(global_map: GaussianMap, local: GaussianMap, window_cams, win
     rep["global_losses"] = opt.iterate(cams_all, camt_all, targets, global_iters,
                                        fixed=[False] * len(window_cams) + [True] * len(past_cams),
                                        active=(abits, lst, cnt), masked=masked_backward)
+    rep["global_iter_ms"] = opt.iter_ms
     # ---- pruning among the active set
     keep = torch.zeros_like(bits)
     klist = torch.zeros(max(n_all, 1), dtype=torch.int32, device=dev)
@@ -303,3 +310,55 @@ def _bits_of(n, lo, hi, dev):
     idx = np.arange(lo, hi)
     np.add.at(w, idx // 32, np.uint64(1) << (idx % 32).astype(np.uint64))
     return torch.from_numpy(w.astype(np.uint32).view(np.int32)).to(dev)
+
+
+def room_update(n=500_000, W=640, H=480, f=525.0, window=8, past=4, local_iters=30,
+                global_iters=100, masked_backward=False, seed=5, eps=0.05):
+    """One mapping update on the synthetic room: the map is the room without a
+    box of it, the window (640x480 keyframes 0.15 m apart, 2.3 m from the box)
+    observes the whole room, the local map is the box's Gaussians displaced by
+    N(0, 3 cm) and recoloured (a noisy initialisation), the E_pc targets are
+    four random past poses."""
+    from . import prior_judge, scenes
+    from .raster import gaussians_to_device
+    w = scenes.workload(2, n=n)
+    box = prior_judge.heldout_box()
+    kept, n_out = prior_judge.split_scene(w["scene"], box)
+    wins0, _, _ = prior_judge.window_poses(window, box, seed)
+    wins = [scenes.camera(c["R"], c["t"], f, f, W / 2, H / 2, W, H) for c in wins0]
+    pasts = [scenes.camera(c["R"], c["t"], f, f, W / 2, H / 2, W, H)
+             for c in prior_judge.random_poses(past, seed + 1)]
+    world = gaussians_to_device(w["scene"])
+    pipe = Pipeline(n, [(W, H)] * window, 1 << 20, colour="sh", sh_degree=w["scene"]["sh_degree"])
+    camt = camera_tensor(wins)
+    D = pipe.ensure_capacity(world, camt)
+    pipe.alloc_capacity(int(D * 1.3) + 1024)
+    pipe.forward(world, camt)
+    images = pipe.rgb.clone()
+    del pipe, world
+    inside = np.all((w["scene"]["means"] >= box[:, 0]) & (w["scene"]["means"] <= box[:, 1]), axis=1)
+    rs = np.random.default_rng(seed)
+    new = {k: (v[inside].copy() if isinstance(v, np.ndarray) else v) for k, v in w["scene"].items()}
+    new["means"] = new["means"] + rs.normal(0, 0.03, size=new["means"].shape).astype(np.float32)
+    new["sh"] = new["sh"] + rs.normal(0, 0.3, size=new["sh"].shape).astype(np.float32)
+    new["opacities"] = np.full_like(new["opacities"], 0.9)
+    gmap = GaussianMap(kept)
+    local = GaussianMap(new)
+    rep = mapping_update(gmap, local, wins, images, pasts, local_iters, global_iters, eps=eps,
+                         masked_backward=masked_backward)
+    rep.update(map_before=int(kept["means"].shape[0]), local=int(local.n), window=window, past=past,
+               image=f"{W}x{H}")
+    return rep
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    masked = "--masked" in sys.argv
+    r = room_update(masked_backward=masked)
+    r.pop("window_poses")
+    med = lambda x: float(np.median(x)) if x else None
+    r["local_iter_ms_median"] = med(r["local_iter_ms"][1:])
+    r["global_iter_ms_median"] = med(r["global_iter_ms"][1:])
+    r["masked_backward"] = masked
+    print(json.dumps(r))
