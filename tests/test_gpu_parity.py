@@ -44,8 +44,8 @@ def _np(t):
 # --------------------------------------------------------------------------
 # a2-a4: keys / sort / ranges, bit-exact
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("case", ["one_view", "uneven_views", "crowded_tile", "equal_depths",
-                                  "empty"])
+@pytest.mark.parametrize("case", ["one_view", "uneven_views", "crowded_tile", "long_tiles",
+                                  "equal_depths", "empty"])
 def test_bin_sort_bit_exact(case):
     if case == "one_view":
         sizes, n, rec = [(64, 48)], 3000, None
@@ -57,6 +57,14 @@ def test_bin_sort_bit_exact(case):
         rec["xy"][0, :, 0] = np.random.default_rng(1).uniform(20, 27, n).astype(np.float32)
         rec["xy"][0, :, 1] = np.random.default_rng(2).uniform(20, 27, n).astype(np.float32)
         rec["radius"][0] = np.minimum(rec["radius"][0], 3)
+    elif case == "long_tiles":
+        # two tiles of about 3000 entries each: past the shared-memory sort, the
+        # L2 ping-pong path with several blocks' worth of items
+        sizes, n = [(64, 48)], 7000
+        rec = scenes.random_records(sizes, n, seed=33, sigma_px=(0.5, 1.5))
+        rec["xy"][0, :, 0] = np.random.default_rng(3).uniform(2, 30, n).astype(np.float32)
+        rec["xy"][0, :, 1] = np.random.default_rng(4).uniform(2, 14, n).astype(np.float32)
+        rec["radius"][0] = np.minimum(rec["radius"][0], 1)
     elif case == "equal_depths":
         sizes, n = [(96, 64)], 3000
         rec = scenes.random_records(sizes, n, seed=32)
@@ -84,8 +92,11 @@ def test_bin_sort_bit_exact(case):
     np.testing.assert_array_equal(_np(pipe.ranges).view(np.uint32), ref["ranges"])
     np.testing.assert_array_equal(_np(pipe.keys)[:D].view(np.uint64), ref["keys"])
     np.testing.assert_array_equal(_np(pipe.vals)[:D].view(np.uint32), ref["vals"])
+    lens = np.diff(ref["ranges"].astype(np.int64), axis=1)
     if case == "crowded_tile":
-        assert np.diff(ref["ranges"].astype(np.int64), axis=1).max() > 2048  # global-memory path
+        assert lens.max() > 4096  # global-memory path
+    if case == "long_tiles":
+        assert ((lens > 2048) & (lens <= 4096)).sum() >= 2
 
 
 def test_bin_sort_overflow_sets_error_and_reports_true_count():
