@@ -73,3 +73,67 @@ def wta_up4(V, d0=0.25, d1=25.0):
     k = np.argmin(V, axis=-1)
     d = d0 + (d1 - d0) * k / (nd - 1)
     return d.repeat(4, axis=0).repeat(4, axis=1)
+
+
+# ---------------------------------------------------------------------------
+# Belief propagation (Section III-A2, with the min-sum algorithm of Felzenszwalb
+# and Huttenlocher, 2006, that the paper cites): the labels are the depth
+# hypotheses, the data cost of label f at pixel p is V(p, d_f), the
+# discontinuity cost between neighbours is the truncated linear
+# min(s |f_p - f_q|, tau), the grid is 4-connected.  Messages start at zero and
+# are all updated together (synchronous iterations):
+#   m_{p->q}(f_q) = min_{f_p} [ D_p(f_p) + sum_{r in N(p), r != q} m_{r->p}(f_p)
+#                               + min(s |f_p - f_q|, tau) ]
+# then shifted so that their minimum over f_q is 0.  After the last iteration
+# the label of p minimises D_p + sum of all incoming messages (lowest label on
+# ties).  The minimum over f_p is taken by brute force here.
+# ---------------------------------------------------------------------------
+# directions: message sent to the left, right, upper, lower neighbour
+_DIRS = ((0, -1), (0, 1), (-1, 0), (1, 0))
+_OPP = (1, 0, 3, 2)
+
+
+def bp_message(h, s, tau):
+    """min over f_p of h(f_p) + min(s |f_p - f_q|, tau), for every f_q (last axis)."""
+    k = h.shape[-1]
+    f = np.arange(k)
+    cost = np.minimum(s * np.abs(f[:, None] - f[None, :]), tau)     # [f_p, f_q]
+    m = (h[..., :, None] + cost).min(axis=-2)
+    return m - m.min(axis=-1, keepdims=True)
+
+
+def _incoming(msgs, d):
+    """Messages arriving at each pixel from its neighbour in direction d: the
+    neighbour sent them in the opposite direction (0 outside the image)."""
+    dy, dx = _DIRS[d]
+    src = msgs[_OPP[d]]
+    out = np.zeros_like(src)
+    h, w = src.shape[:2]
+    ys = slice(max(dy, 0), h + min(dy, 0))
+    yd = slice(max(-dy, 0), h + min(-dy, 0))
+    xs = slice(max(dx, 0), w + min(dx, 0))
+    xd = slice(max(-dx, 0), w + min(-dx, 0))
+    out[yd, xd] = src[ys, xs]
+    return out
+
+
+def bp(V, s, tau, iters):
+    """V [h, w, nd] data costs.  Returns (labels [h, w], beliefs [h, w, nd],
+    messages [4, h, w, nd])."""
+    D = np.asarray(V, np.float64)
+    msgs = np.zeros((4,) + D.shape)
+    for _ in range(iters):
+        inc = [_incoming(msgs, d) for d in range(4)]
+        tot = D + sum(inc)
+        # to the neighbour in direction d: leave out what came from it
+        msgs = np.stack([bp_message(tot - inc[d], s, tau) for d in range(4)])
+    inc = [_incoming(msgs, d) for d in range(4)]
+    B = D + sum(inc)
+    return np.argmin(B, axis=-1), B, msgs
+
+
+def bp_depth_up4(V, s, tau, iters, d0=0.25, d1=25.0):
+    nd = V.shape[-1]
+    lab, _, _ = bp(V, s, tau, iters)
+    d = d0 + (d1 - d0) * lab / (nd - 1)
+    return d.repeat(4, axis=0).repeat(4, axis=1)

@@ -2,6 +2,7 @@
 recovery on analytically rendered images of a textured plane (no renderer
 involved)."""
 import numpy as np
+import pytest
 
 from oracle import costvol
 
@@ -73,3 +74,51 @@ def test_cost_volume_single_pixel_by_hand():
             fy_ * ((1 - fx_) * g[s, y0 + 1, x0] + fx_ * g[s, y0 + 1, x0 + 1])
         vals.append(abs(g[1, y, x] - val))
     assert np.isclose(V[y, x, k], np.mean(vals), rtol=1e-12)
+
+
+def test_bp_message_truncated_linear_by_hand():
+    h = np.array([3.0, 0.0, 5.0, 5.0, 5.0])
+    m = costvol.bp_message(h, 1.0, 2.5)
+    # min over f_p of h(f_p) + min(|f_p - f_q|, 2.5): from label 1 (cost 0)
+    np.testing.assert_allclose(m, [1.0, 0.0, 1.0, 2.0, 2.5])
+
+
+def test_bp_without_smoothness_is_winner_take_all():
+    rs = np.random.default_rng(0)
+    V = rs.uniform(size=(6, 7, 9))
+    lab, B, _ = costvol.bp(V, 0.0, 0.0, 5)
+    np.testing.assert_array_equal(lab, np.argmin(V, axis=-1))
+
+
+def test_bp_on_a_chain_reaches_the_exact_minimum():
+    # min-sum BP is exact on a tree: on a 1 x n chain after n iterations its
+    # labels minimise sum_p D_p(f_p) + sum_(p,p+1) min(s |f_p - f_p+1|, tau),
+    # checked against exhaustive search.
+    import itertools
+    rs = np.random.default_rng(1)
+    n, k, s, tau = 6, 4, 0.3, 0.7
+    V = rs.uniform(size=(1, n, k))
+    lab, _, _ = costvol.bp(V, s, tau, n + 1)
+
+    def energy(f):
+        e = sum(V[0, p, f[p]] for p in range(n))
+        return e + sum(min(s * abs(f[p] - f[p + 1]), tau) for p in range(n - 1))
+    best = min(itertools.product(range(k), repeat=n), key=energy)
+    assert energy(tuple(lab[0])) == pytest.approx(energy(best), abs=1e-12)
+    # and the same on a column
+    labc, _, _ = costvol.bp(V.transpose(1, 0, 2), s, tau, n + 1)
+    assert energy(tuple(labc[:, 0])) == pytest.approx(energy(best), abs=1e-12)
+
+
+def test_bp_smooths_a_noisy_plane():
+    # a constant-depth scene with 10% of the pixels' costs scrambled: BP
+    # restores the true label where winner-take-all follows the noise
+    rs = np.random.default_rng(2)
+    h, w, k, true = 20, 24, 16, 5
+    V = np.abs(np.arange(k) - true)[None, None, :] * 0.05 + rs.uniform(0, 0.02, size=(h, w, k))
+    bad = rs.uniform(size=(h, w)) < 0.1
+    V[bad] = rs.uniform(size=(bad.sum(), k))
+    wta = np.argmin(V, axis=-1)
+    lab, _, _ = costvol.bp(V, 0.2, 1.0, 20)
+    assert (wta != true).sum() > 30
+    assert (lab != true).sum() <= 5
