@@ -119,6 +119,19 @@ gevo_status gevo_cost_volume(int32_t nk, int32_t ref, int32_t H, int32_t W, cons
  * scale_px * depth / fx, identity rotation, the given opacity -- written at
  * slot atomicAdd(counter, 1) if that slot is below cap (order unspecified).
  * rgb planar [3][H][W]. */
+/* Belief propagation over a cost volume (Section III-A2, the min-sum algorithm
+ * of Felzenszwalb and Huttenlocher the paper cites): labels are the nd <= 64
+ * depth hypotheses of volume [h][w][nd] (gevo_cost_volume's layout, the data
+ * cost), neighbours on the 4-connected grid pay min(s |f_p - f_q|, tau),
+ * messages start at zero and all are updated together for `iters`
+ * iterations (each shifted to minimum 0).  Writes depth [4h][4w] (the label
+ * minimising data cost + incoming messages, lowest on ties, as
+ * d0 + (d1 - d0) f / (nd - 1), nearest x4), and if non-NULL labels [h][w] and
+ * beliefs [h][w][nd].  msgs: scratch of 2 * 4 * h * w * nd floats. */
+gevo_status gevo_depth_bp(int32_t h, int32_t w, int32_t nd, const float* volume, float s,
+                          float tau, int32_t iters, float d0, float d1, float* msgs, float* depth,
+                          int32_t* labels, float* beliefs, void* stream);
+
 gevo_status gevo_unproject(int32_t H, int32_t W, const float* rgb, const float* depth,
                            const float* mask, const float* cam, uint32_t keep, uint32_t seed,
                            float scale_px, float opacity, int32_t sh_degree, uint32_t* counter,

@@ -109,6 +109,7 @@ PRIOR = {
     "gevo_adam": "Ipppppffffip",
     "gevo_cost_volume": "iiiippiffpppp",
     "gevo_unproject": "iippppuuffipipppppp",
+    "gevo_depth_bp": "iiipffiffppppp",
     "gevo_to_bf16": "Ippp",
 }
 EXPORTS = EXPORTS + list(PRIOR)

@@ -148,6 +148,145 @@ __global__ void k_unproject(int H, int W, const float* __restrict__ rgb, const f
     }
 }
 
+// ---------------------------------------------------------------------------
+// Belief propagation over the cost volume (Section III-A2; the min-sum
+// algorithm of Felzenszwalb and Huttenlocher, 2006): 4-connected grid, data
+// cost V(p, d_f), discontinuity cost min(s |f_p - f_q|, tau), synchronous
+// iterations from zero messages, each message shifted to minimum 0.
+// One warp per pixel; lane l holds labels l and l + 32.  The minimisation over
+// f_p of h(f_p) + min(s |f_p - f|, tau) splits into
+//   min( s f + min_{f_p <= f} (h(f_p) - s f_p),  -s f + min_{f_p >= f} (h(f_p) + s f_p),
+//        min h + tau ),
+// two warp scans (prefix and suffix minimum) in place of the linear-time
+// forward / backward passes.
+// msgs: [4][h * w][nd], direction d = message sent to the left, right, upper,
+// lower neighbour.
+// ---------------------------------------------------------------------------
+__device__ __constant__ int c_bp_dy[4] = {0, 0, -1, 1};
+__device__ __constant__ int c_bp_dx[4] = {-1, 1, 0, 0};
+__device__ __constant__ int c_bp_opp[4] = {1, 0, 3, 2};
+
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// inclusive prefix (up = true) or suffix minimum over the lanes
+__device__ __forceinline__ float warp_scan_min(float v, bool up)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float u = up ? __shfl_up_sync(0xffffffffu, v, o) : __shfl_down_sync(0xffffffffu, v, o);
+        if (up ? lane >= o : lane + o < 32) v = fminf(v, u);
+    }
+    return v;
+}
+
+// Loads the data cost and the four incoming messages of pixel (x, y) for
+// labels f0 = lane, f1 = lane + 32 (INF past nd for the data cost, 0 for
+// messages).
+__device__ __forceinline__ void bp_load(int h, int w, int nd, const float* __restrict__ V,
+                                        const float* __restrict__ msg, int x, int y, float D[2],
+                                        float inc[4][2])
+{
+    const int lane = threadIdx.x & 31;
+    const size_t hw = (size_t)h * w;
+    const size_t p = (size_t)y * w + x;
+    for (int j = 0; j < 2; j++) {
+        const int f = lane + 32 * j;
+        D[j] = f < nd ? V[p * nd + f] : INFINITY;
+    }
+    for (int d = 0; d < 4; d++) {
+        const int ny = y + c_bp_dy[d], nx = x + c_bp_dx[d];
+        const bool in = ny >= 0 && ny < h && nx >= 0 && nx < w;
+        const float* src = msg + (size_t)c_bp_opp[d] * hw * nd + ((size_t)ny * w + nx) * nd;
+        for (int j = 0; j < 2; j++) {
+            const int f = lane + 32 * j;
+            inc[d][j] = (in && f < nd) ? src[f] : 0.f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_bp_iter(int h, int w, int nd, const float* __restrict__ V, const float* __restrict__ msg_in,
+          float* __restrict__ msg_out, float s, float tau)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t hw = (size_t)h * w;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (size_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < hw; p += warps) {
+        const int x = (int)(p % w), y = (int)(p / w);
+        float D[2], inc[4][2];
+        bp_load(h, w, nd, V, msg_in, x, y, D, inc);
+        float tot[2];
+        for (int j = 0; j < 2; j++) tot[j] = D[j] + inc[0][j] + inc[1][j] + inc[2][j] + inc[3][j];
+        for (int d = 0; d < 4; d++) {
+            float hv[2], a[2], b[2];
+            for (int j = 0; j < 2; j++) hv[j] = tot[j] - inc[d][j];   // INF past nd
+            const float f0 = (float)lane, f1 = (float)(lane + 32);
+            // prefix over f = 0..63: first half, then second half with the first's total
+            a[0] = warp_scan_min(hv[0] - s * f0, true);
+            const float a0_all = __shfl_sync(0xffffffffu, a[0], 31);
+            a[1] = fminf(a0_all, warp_scan_min(hv[1] - s * f1, true));
+            // suffix: second half, then first half with the second's total
+            b[1] = warp_scan_min(hv[1] + s * f1, false);
+            const float b1_all = __shfl_sync(0xffffffffu, b[1], 0);
+            b[0] = fminf(b1_all, warp_scan_min(hv[0] + s * f0, false));
+            const float hmin = warp_min(fminf(hv[0], hv[1]));
+            float m[2];
+            m[0] = fminf(fminf(a[0] + s * f0, b[0] - s * f0), hmin + tau);
+            m[1] = fminf(fminf(a[1] + s * f1, b[1] - s * f1), hmin + tau);
+            if (lane + 32 >= nd) m[1] = INFINITY;
+            if (lane >= nd) m[0] = INFINITY;
+            const float mmin = warp_min(fminf(m[0], m[1]));
+            float* dst = msg_out + (size_t)d * hw * nd + p * nd;
+            if (lane < nd) dst[lane] = m[0] - mmin;
+            if (lane + 32 < nd) dst[lane + 32] = m[1] - mmin;
+        }
+    }
+}
+
+// Beliefs D + all incoming messages; label = argmin (lowest on ties); depth
+// of the label written to the 4 x 4 full-resolution pixels it covers.
+__global__ void __launch_bounds__(256)
+k_bp_labels(int h, int w, int nd, const float* __restrict__ V, const float* __restrict__ msg,
+            float d0, float d1, float* __restrict__ depth, int* __restrict__ labels,
+            float* __restrict__ beliefs)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t hw = (size_t)h * w;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (size_t p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < hw; p += warps) {
+        const int x = (int)(p % w), y = (int)(p / w);
+        float D[2], inc[4][2];
+        bp_load(h, w, nd, V, msg, x, y, D, inc);
+        float bv = INFINITY;
+        int bi = 0x7fffffff;
+        for (int j = 0; j < 2; j++) {
+            const int f = lane + 32 * j;
+            if (f >= nd) continue;
+            const float b = D[j] + inc[0][j] + inc[1][j] + inc[2][j] + inc[3][j];
+            if (beliefs) beliefs[p * nd + f] = b;
+            if (b < bv) { bv = b; bi = f; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov < bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (labels && lane == 0) labels[p] = bi;
+        if (lane < 16) {
+            const int W = 4 * w;
+            depth[(size_t)(4 * y + (lane >> 2)) * W + 4 * x + (lane & 3)] =
+                d0 + (d1 - d0) * (float)bi / (float)(nd - 1);
+        }
+    }
+}
+
 static int gridn(size_t n) { return (int)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, (size_t)sm_count() * 16)); }
 
 }  // namespace gevo
@@ -187,6 +326,29 @@ gevo_status gevo_unproject(int32_t H, int32_t W, const float* rgb, const float* 
     k_unproject<<<gridn((size_t)H * W), 256, 0, (cudaStream_t)stream>>>(
         H, W, rgb, depth, mask, cam, keep, seed, scale_px, opacity, K, counter, cap, means, scales,
         quats, opacities, sh);
+    GEVO_CHECK_LAUNCH();
+    return GEVO_OK;
+}
+
+gevo_status gevo_depth_bp(int32_t h, int32_t w, int32_t nd, const float* volume, float s,
+                          float tau, int32_t iters, float d0, float d1, float* msgs, float* depth,
+                          int32_t* labels, float* beliefs, void* stream)
+{
+    if (h < 1 || w < 1 || nd < 2 || nd > 64 || !volume || !(s >= 0.f) || !(tau >= 0.f) ||
+        iters < 0 || !(d1 > d0) || !msgs || !depth)
+        return GEVO_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t per = (size_t)4 * h * w * nd;
+    float* a = msgs;
+    float* b = msgs + per;
+    if (cudaMemsetAsync(a, 0, sizeof(float) * per, st) != cudaSuccess) return GEVO_ERR_CUDA;
+    const int grid = gridn((size_t)h * w * 32);
+    for (int it = 0; it < iters; it++) {
+        k_bp_iter<<<grid, 256, 0, st>>>(h, w, nd, volume, a, b, s, tau);
+        GEVO_CHECK_LAUNCH();
+        float* t = a; a = b; b = t;
+    }
+    k_bp_labels<<<grid, 256, 0, st>>>(h, w, nd, volume, a, d0, d1, depth, labels, beliefs);
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }

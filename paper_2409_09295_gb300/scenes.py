@@ -223,3 +223,28 @@ def random_records(sizes, n: int, seed: int, frac_culled: float = 0.1,
         rgb[v] = r.uniform(0.0, 1.0, (n, 3))
     opac = r.uniform(opacity[0], opacity[1], n).astype(np.float32)
     return dict(xy=xy, conic=conic, depth=depth, radius=radius, rgb=rgb, opacity=opac)
+
+
+def plane_images(d_star: float, cams, H: int, W: int, seed: int = 0):
+    """Seeded keyframe images for the cost-volume tests: each camera (rows of
+    cams [nk, 16]: R, t, fx, fy, cx, cy) sees the world plane z = d_star painted
+    with a smooth random texture, ray-cast in double precision (pixel i is
+    sampled at i + 0.5 - c).  Returns binary32 [nk, 3, H, W] in [0, 1]."""
+    r = rng(seed)
+    a = r.uniform(1.5, 4.0, size=3)
+    b = r.uniform(1.5, 4.0, size=3)
+    ph = r.uniform(0, 2 * np.pi, size=3)
+    imgs = []
+    for c in np.asarray(cams, np.float64):
+        R, t = c[:9].reshape(3, 3), c[9:12]
+        fx, fy, cx, cy = c[12:16]
+        ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+        ray_c = np.stack([(xs + 0.5 - cx) / fx, (ys + 0.5 - cy) / fy, np.ones_like(xs)], -1)
+        ray_w = ray_c @ R
+        o = -R.T @ t
+        s = (d_star - o[2]) / ray_w[..., 2]
+        pw = o + s[..., None] * ray_w
+        chans = [0.5 + 0.2 * np.sin(a[k] * pw[..., 0] + ph[k]) * np.cos(b[k] * pw[..., 1])
+                 + 0.15 * np.sin(2.7 * a[k] * pw[..., 0] + 1.3 * b[k] * pw[..., 1]) for k in range(3)]
+        imgs.append(np.stack(chans))
+    return np.clip(np.stack(imgs), 0.0, 1.0).astype(np.float32)
