@@ -14,8 +14,8 @@ III-A, III-B).  The protocol here, on the 500k-Gaussian room scene:
      the map does not explain (depth or colour differ from the map's render)
      are the new region;
   4. new Gaussians (the same pixels for both methods) are placed at the depth
-     from (a) the prior on each keyframe image, (b) the cost volume + winner-
-     take-all over the 8 keyframes;
+     from (a) the prior on each keyframe image, (b) the cost volume over the
+     8 keyframes with belief propagation (Section III-A2);
   5. each initialisation is optimised for the same number of iterations (L1
      photometric loss over the keyframes, Adam on the new Gaussians' means and
      colours, the map frozen);
@@ -37,6 +37,10 @@ from .raster import Pipeline, camera_tensor, gaussians_to_device
 
 W_IMG, H_IMG, F_IMG = 320, 240, 262.5
 INSERT_OPACITY = 0.2   # new Gaussians enter the map at opacity 0.2 (Section III-B2)
+# belief propagation over the cost volume (the paper gives no parameters): the
+# discontinuity cost per hypothesis step (0.39 m) and its truncation, in units
+# of the mean absolute grey difference, and the iterations
+BP_S, BP_TAU, BP_ITERS = 0.01, 0.1, 10
 
 
 def heldout_box():
@@ -290,15 +294,21 @@ def run(n=500_000, n_train=2000, epochs=30, iters=100, total_new=50_000, log=Non
     key_rgb = world_key[0]
     # (a) learned prior
     d_prior = predict_depth(net, key_rgb)
-    # (b) plain: cost volume over the 8 keyframes, each keyframe the reference once
+    # (b) plain: cost volume over the 8 keyframes, each keyframe the reference
+    # once, depth by belief propagation over it (Section III-A2)
     rgb_all = key_rgb.contiguous()
     cams_t = camera_tensor(key_cams)
-    grey = torch.zeros(8, H_IMG // 4, W_IMG // 4, device="cuda")
-    vol = torch.zeros(H_IMG // 4 * W_IMG // 4 * 64, device="cuda")
+    h4, w4 = H_IMG // 4, W_IMG // 4
+    grey = torch.zeros(8, h4, w4, device="cuda")
+    vol = torch.zeros(h4 * w4 * 64, device="cuda")
+    d_wta = torch.zeros(H_IMG, W_IMG, device="cuda")
+    msgs = torch.zeros(2 * 4 * h4 * w4 * 64, device="cuda")
     d_plain = torch.zeros(8, H_IMG, W_IMG, device="cuda")
     for r in range(8):
         _abi.prior_call("gevo_cost_volume", 8, r, H_IMG, W_IMG, rgb_all, cams_t, 64, 0.25, 25.0,
-                        grey, vol, d_plain[r])
+                        grey, vol, d_wta)
+        _abi.prior_call("gevo_depth_bp", h4, w4, 64, vol, BP_S, BP_TAU, BP_ITERS, 0.25, 25.0, msgs,
+                        d_plain[r], None, None)
     world_depth = world_key[1] / torch.clamp(1 - world_key[2], min=1e-6)
     m = key_mask > 0.5
     res = {"held_out_gaussians": n_held, "train": tinfo,
