@@ -159,6 +159,20 @@ def run_reference(args, rank):
 FLOP_EXAMINE, FLOP_BLEND_FWD, FLOP_BLEND_BWD = 12, 11, 49
 
 
+def whole_job(ms_local: float, units_local: float, world: int, device=None):
+    """Each rank times an independent replica; the job's time is the slowest
+    rank's and its work the sum of the ranks': returns (max ms, total units)."""
+    if world == 1:
+        return ms_local, units_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=device)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -229,13 +243,8 @@ def main():
     step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
     stage_ms = {name: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps
                 for i, (name, _) in enumerate(rep.graphs)}
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     V = len(cams)
-    evals = (E_fwd + E_bwd) * args.steps * world
+    total_ms, evals = whole_job(sum(step_ms), (E_fwd + E_bwd) * args.steps, world, dev)
     value = evals / (total_ms / 1e3)
     views_per_s = V * args.steps * world / (total_ms / 1e3)
 
@@ -273,7 +282,8 @@ def main():
         e.record()
         e.synchronize()
         e2e_ms += s.elapsed_time(e)
-    e2e_value = (E_fwd + E_bwd) * args.steps * world / (e2e_ms / 1e3)
+    e2e_ms, e2e_evals = whole_job(e2e_ms, (E_fwd + E_bwd) * args.steps, world, dev)
+    e2e_value = e2e_evals / (e2e_ms / 1e3)
 
     # ---- the plain (unbatched) path on the same GPU --------------------------------------
     plain = PlainReplay(g, cams, target_rgb, target_depth, lambda_depth=1.0)
