@@ -381,14 +381,60 @@ __device__ void radix_pass(const unsigned long long* a, unsigned long long* b, i
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSortThreads)
+// The same pass on (32-bit depth key, 16-bit position in the bucket) pairs
+// kept in shared memory: 6 bytes an item instead of 8, so more blocks fit on
+// an SM.
+__device__ void radix_pass_kv(const uint32_t* ka, const uint16_t* ia, uint32_t* kb, uint16_t* ib,
+                              int L, int shift, uint32_t (*s_off)[256], uint32_t* s_tmp)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int chunk = (L + kSortWarps - 1) / kSortWarps;
+    const int lo = min(L, warp * chunk), hi = min(L, lo + chunk);
+    for (int d = lane; d < 256; d += 32) s_off[warp][d] = 0u;
+    __syncwarp();
+    for (int i = lo + lane; i < hi; i += 32) atomicAdd(&s_off[warp][(ka[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) tot += s_off[w][tid];
+    uint32_t run = block_exscan256(tot, s_tmp);
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) {
+        const uint32_t c = s_off[w][tid];
+        s_off[w][tid] = run;
+        run += c;
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int r = lo; r < hi; r += 32) {
+        const int i = r + lane;
+        const bool valid = i < hi;
+        const uint32_t key = valid ? ka[i] : 0u;
+        const uint16_t idx = valid ? ia[i] : (uint16_t)0;
+        const uint32_t dg = valid ? ((key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        if (valid) {
+            const uint32_t pos = s_off[warp][dg] + __popc(peers & lt);
+            kb[pos] = key;
+            ib[pos] = idx;
+        }
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) s_off[warp][dg] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+// 40 registers: six blocks of 256 threads fit on an SM (the sort is latency-bound)
+__global__ void __launch_bounds__(kSortThreads, 6)
 k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ tile_start,
           const uint32_t* __restrict__ tile_count, const uint64_t* __restrict__ d_n_dup,
           uint64_t cap, unsigned long long* __restrict__ bucket,
           unsigned long long* __restrict__ bucket2, unsigned long long* __restrict__ keys_out,
           uint32_t* __restrict__ vals_out)
 {
-    extern __shared__ unsigned long long s_items[];   // 2 * kSortSmemItems
+    // shared-memory path: keys [2][kSortSmemItems] uint32, then positions [2][..] uint16
+    extern __shared__ uint32_t s_kv[];
     __shared__ uint32_t s_off[kSortWarps][256];
     __shared__ uint32_t s_tmp[kSortWarps];
     __shared__ uint32_t s_or[kSortWarps], s_and[kSortWarps];
@@ -398,20 +444,21 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
     if (L == 0) return;
     const uint32_t s0 = tile_start[tile];
     const int tid = threadIdx.x;
-    unsigned long long* a;
-    unsigned long long* b;
-    if (L <= kSortSmemItems) {
-        a = s_items;
-        b = s_items + kSortSmemItems;
-        for (int i = tid; i < L; i += kSortThreads) a[i] = bucket[s0 + i];
-    } else {
-        a = bucket + s0;
-        b = bucket2 + s0;
-    }
+    const bool small = L <= kSortSmemItems;
+    unsigned long long* a = bucket + s0;
+    unsigned long long* b = bucket2 + s0;
+    uint32_t* ka = s_kv;
+    uint32_t* kb = s_kv + kSortSmemItems;
+    uint16_t* ia = reinterpret_cast<uint16_t*>(s_kv + 2 * kSortSmemItems);
+    uint16_t* ib = ia + kSortSmemItems;
     // which depth bytes vary inside this tile
     uint32_t o = 0u, an = 0xffffffffu;
     for (int i = tid; i < L; i += kSortThreads) {
         const uint32_t hi = (uint32_t)(a[i] >> 32);
+        if (small) {
+            ka[i] = hi;
+            ia[i] = (uint16_t)i;
+        }
         o |= hi;
         an &= hi;
     }
@@ -428,6 +475,39 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
 #pragma unroll
         for (int w = 0; w < kSortWarps; w++) { oo |= s_or[w]; aa &= s_and[w]; }
         vary = oo ^ aa;
+    }
+    if (small) {
+        if (L > 1) {
+            for (int d = 0; d < 4; d++) {
+                if (((vary >> (8 * d)) & 255u) == 0u) continue;
+                radix_pass_kv(ka, ia, kb, ib, L, 8 * d, s_off, s_tmp);
+                uint32_t* t = ka; ka = kb; kb = t;
+                uint16_t* u = ia; ia = ib; ib = u;
+            }
+            // equal depth bits: order by id (runs are rare and short)
+            for (int i = tid; i < L; i += kSortThreads) {
+                const uint32_t hi = ka[i];
+                const bool start = (i == 0 || ka[i - 1] != hi);
+                if (start && i + 1 < L && ka[i + 1] == hi) {
+                    int e = i + 1;
+                    while (e < L && ka[e] == hi) e++;
+                    for (int j = i + 1; j < e; j++) {
+                        const uint16_t x = ia[j];
+                        const uint32_t id = (uint32_t)a[x];
+                        int m = j - 1;
+                        while (m >= i && (uint32_t)a[ia[m]] > id) { ia[m + 1] = ia[m]; m--; }
+                        ia[m + 1] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        const unsigned long long th = (unsigned long long)tile << 32;
+        for (int i = tid; i < L; i += kSortThreads) {
+            keys_out[s0 + i] = th | ka[i];
+            vals_out[s0 + i] = (uint32_t)a[ia[i]];
+        }
+        return;
     }
     if (L > 1) {
         for (int d = 0; d < 4; d++) {
@@ -537,7 +617,7 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
                 reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor, d_n_dup,
                 dup_capacity, bucket);
         GEVO_CHECK_LAUNCH();
-        const size_t smem = sizeof(unsigned long long) * 2 * kSortSmemItems;
+        const size_t smem = (sizeof(uint32_t) + sizeof(uint16_t)) * 2 * kSortSmemItems;
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -643,7 +723,7 @@ extern "C" gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t 
                 reinterpret_cast<const float4*>(proj->rgb_depth), tile_start, tile_cursor, d_n_dup,
                 dup_capacity, bucket);
         GEVO_CHECK_LAUNCH();
-        const size_t smem = sizeof(unsigned long long) * 2 * kSortSmemItems;
+        const size_t smem = (sizeof(uint32_t) + sizeof(uint16_t)) * 2 * kSortSmemItems;
         static bool attr = false;
         if (!attr) {
             cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
