@@ -57,10 +57,52 @@ __device__ __forceinline__ float4 alpha_box(float2 m, float4 co)
     return make_float4(m.x - hx, m.x + hx, m.y - hy, m.y + hy);
 }
 
-__device__ __forceinline__ bool box_misses(float4 box, float wx0, float wx1, float wy0, float wy1)
+// Which warps of the block may blend this entry at some pixel: warp w covers
+// tile columns 0..15 and rows w*rows .. w*rows + rows - 1.  For each such
+// strip the minimum of q(d) = a dx^2 + 2 b dx dy + c dy^2, d = mean - pixel, over
+// the continuous rectangle spanned by its pixel centres (a lower bound of the
+// minimum over the pixels) is compared with 2 ln(255 o), the level below which
+// alpha < 1/255: zero if the mean lies inside, else the least of the four
+// edge minima (a 1-D quadratic per edge, its vertex clamped to the edge).  The
+// threshold is widened by 0.2% + 2e-4 against rounding.  A strip the bounding
+// box of the ellipse overlaps but the ellipse itself misses -- a thin or
+// tilted splat crossing a corner -- is culled, which the box alone cannot.
+__device__ __forceinline__ uint32_t strip_mask(float2 m, float4 co, float x0, float y0, int nw,
+                                               int rows)
 {
-    return box.y < wx0 || box.x > wx1 || box.w < wy0 || box.z > wy1;
+    const float4 box = alpha_box(m, co);
+    if (!(box.x <= box.y)) return 0u;               // o < 1/255: blends nowhere
+    const float a = co.x, b = co.y, c = co.z;
+    const float lg = __logf(255.f * co.w);
+    const float k2 = (2.f * fmaxf(lg, 0.f) + 2e-4f) * 1.002f;
+    const bool exact = a > 0.f && c > 0.f && box.x > -1e29f;   // else box only
+    const float dxl = m.x - (x0 + (float)(kTile - 1)), dxh = m.x - x0;
+    const bool in_x = dxl <= 0.f && dxh >= 0.f;
+    uint32_t mask = 0u;
+    for (int w = 0; w < nw; w++) {
+        const float ys0 = y0 + (float)(w * rows), ys1 = ys0 + (float)(rows - 1);
+        if (box.w < ys0 || box.z > ys1 || box.y < x0 || box.x > x0 + (float)(kTile - 1)) continue;
+        if (!exact) { mask |= 1u << w; continue; }
+        const float dyl = m.y - ys1, dyh = m.y - ys0;
+        float q = 0.f;
+        if (!(in_x && dyl <= 0.f && dyh >= 0.f)) {
+            q = 3.0e38f;
+            const float ex[2] = {dxl, dxh}, ey[2] = {dyl, dyh};
+#pragma unroll
+            for (int e = 0; e < 2; e++) {
+                const float dx = ex[e];
+                const float dy = fminf(fmaxf(-b * dx / c, dyl), dyh);
+                q = fminf(q, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
+                const float dy2 = ey[e];
+                const float dx2 = fminf(fmaxf(-b * dy2 / a, dxl), dxh);
+                q = fminf(q, a * dx2 * dx2 + 2.f * b * dx2 * dy2 + c * dy2 * dy2);
+            }
+        }
+        if (q <= k2) mask |= 1u << w;
+    }
+    return mask;
 }
+
 
 // log2 of the Gaussian falloff at offset (dx, dy); identical in both passes.
 __device__ __forceinline__ float power2_at(const float4& co, float dx, float dy)
@@ -104,11 +146,10 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     __shared__ float2 s_xy[kBatch];
     __shared__ float4 s_co[kBatch];
     __shared__ float4 s_rz[kBatch];
-    __shared__ float4 s_box[kBatch];
+    __shared__ uint32_t s_mask[kBatch];
     __shared__ uint32_t s_act[ACT ? kBatch : 1];
     __shared__ uint32_t s_item;
     const int tid = threadIdx.x;
-    const int wrow0 = ((tid & ~31) >> 4) * PPT;   // first tile row of this warp
     constexpr int WROWS = 2 * PPT;
 
     for (int it = 0;; it++) {
@@ -160,18 +201,17 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 s_xy[j] = m;
                 s_co[j] = prescale(c);
                 s_rz[j] = rz[id];
-                s_box[j] = alpha_box(m, c);
+                s_mask[j] = strip_mask(m, c, (float)x0, (float)y0, NT / 32, WROWS);
                 if (ACT) s_act[j] = (__ldg(active + (gid >> 5)) >> (gid & 31)) & 1u;
             }
             __syncthreads();
-            const float wx0 = (float)x0, wx1 = (float)(x0 + kTile - 1);
-            const float wy0 = (float)(y0 + wrow0), wy1 = (float)(y0 + wrow0 + WROWS - 1);
+            const uint32_t my_bit = 1u << (tid >> 5);
             for (int j = 0; j < nb; j++) {
                 bool all = true;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) all = all && done[k];
                 if (all) break;
-                if (box_misses(s_box[j], wx0, wx1, wy0, wy1)) {
+                if (!(s_mask[j] & my_bit)) {
                     if (COUNT) {
 #pragma unroll
                         for (int k = 0; k < PPT; k++) cnt[k] += done[k] ? 0u : 1u;
@@ -380,14 +420,13 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     __shared__ float2 s_xy[kBatch];
     __shared__ float4 s_co[kBatch];
     __shared__ float4 s_rz[kBatch];
-    __shared__ float4 s_box[kBatch];
+    __shared__ uint32_t s_mask[kBatch];
     __shared__ uint32_t s_id[kBatch];
     constexpr int NG = EXT ? 11 : 10;   // per-entry sums: 10 gradients (+ the error weight)
     __shared__ float s_g[kBatch][NG];
     __shared__ uint32_t s_item;
     __shared__ uint32_t s_max[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wrow0 = ((tid & ~31) >> 4) * PPT;
     constexpr int WROWS = 2 * PPT;
     (void)lane;
 
@@ -475,15 +514,14 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 s_xy[j] = m;
                 s_co[j] = prescale(c);
                 s_rz[j] = rz[gid];
-                s_box[j] = alpha_box(m, c);
+                s_mask[j] = strip_mask(m, c, (float)x0, (float)y0, NT / 32, WROWS);
 #pragma unroll
                 for (int q = 0; q < NG; q++) s_g[j][q] = 0.f;
             }
             __syncthreads();
-            const float wx0 = (float)x0, wx1 = (float)(x0 + kTile - 1);
-            const float wy0 = (float)(y0 + wrow0), wy1 = (float)(y0 + wrow0 + WROWS - 1);
+            const uint32_t my_bit = 1u << (tid >> 5);
             for (int j = nb - 1; j >= 0; j--) {
-                if (box_misses(s_box[j], wx0, wx1, wy0, wy1)) continue;
+                if (!(s_mask[j] & my_bit)) continue;
                 const uint32_t pos = bstart + j - rg.x;   // list position
                 const float2 m = s_xy[j];
                 const float4 c = s_co[j];
