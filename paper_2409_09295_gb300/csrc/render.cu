@@ -520,9 +520,12 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
             }
             __syncthreads();
             const uint32_t my_bit = 1u << (tid >> 5);
-            for (int j = nb - 1; j >= 0; j--) {
+            // entries at or past this warp's last blended position concern no lane
+            const uint32_t boff = bstart - rg.x;
+            const int jend = mymax > boff ? (int)min((uint32_t)nb, mymax - boff) : 0;
+            for (int j = jend - 1; j >= 0; j--) {
                 if (!(s_mask[j] & my_bit)) continue;
-                const uint32_t pos = bstart + j - rg.x;   // list position
+                const uint32_t pos = boff + j;   // list position
                 const float2 m = s_xy[j];
                 const float4 c = s_co[j];
                 const float dx = __fsub_rn(m.x, fpx);
