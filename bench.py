@@ -340,7 +340,11 @@ def main():
                        "unit": unit, "frac": ach / peak, "ms": stage_ms[name]}
     dom = "render_bwd"   # the largest share of the step (profiles/ launch list)
     roof = dict(roofs[dom])
-    roof.update({"traffic": None,
+    # DRAM bytes of one reverse-walk launch: ncu (dram__bytes_read.sum + write) on the
+    # 4-view case of profiles/render_kernels_4view_500k.md, 51.5 MB for 245.15M walked
+    # entries, scaled by entries to this launch (same scene, same resolution)
+    roof.update({"traffic": 51.5e6 * E_bwd / 245.15e6,
+                 "traffic_source": "ncu dram bytes of the 4-view case, scaled by walked entries",
                  "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {clk_peak:.0f} MHz"})
 
     line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
