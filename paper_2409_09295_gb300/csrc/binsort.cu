@@ -170,10 +170,14 @@ k_scatter(gevo_layout L, int n, const float2* __restrict__ xy, const int* __rest
 constexpr int kBinThreads = 256;
 constexpr int kBinMaxSmemTiles = 16384;   // views with more tiles use k_count / k_scatter
 
+// f(g, tile, depth bits of g): the depth bits are loaded with the Gaussian's
+// other record fields when rgbz != NULL (0 otherwise) and handed to the lane
+// that emits each duplicate by shuffle.
 template <typename F>
 __device__ __forceinline__ void for_each_dup(const gevo_layout& L, int v, int n, int g0, int g1,
                                              const float2* __restrict__ xy,
-                                             const int* __restrict__ radius, F&& f)
+                                             const int* __restrict__ radius,
+                                             const float4* __restrict__ rgbz, F&& f)
 {
     // The duplicates of the warp's 32 Gaussians are laid end to end (warp
     // prefix sum of the rectangle areas) and dealt out round-robin to the
@@ -184,11 +188,13 @@ __device__ __forceinline__ void for_each_dup(const gevo_layout& L, int v, int n,
     for (int gs = g0 + (int)(threadIdx.x & ~31); gs < g1; gs += kBinThreads) {
         const int g = gs + lane;
         int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+        uint32_t dbits = 0u;
         if (g < g1) {
             const int r = radius[vb + g];
             if (r > 0) {
                 const float2 m = xy[vb + g];
                 tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
+                if (rgbz) dbits = __float_as_uint(__ldg(reinterpret_cast<const float*>(rgbz + vb + g) + 3));
             }
         }
         const int w = x1 - x0;
@@ -215,10 +221,15 @@ __device__ __forceinline__ void for_each_dup(const gevo_layout& L, int v, int n,
             const int sw = __shfl_sync(0xffffffffu, w, src);
             const int se = __shfl_sync(0xffffffffu, excl, src);
             const int sg = __shfl_sync(0xffffffffu, g, src);
+            const uint32_t sd = __shfl_sync(0xffffffffu, dbits, src);
             if (k < total) {
                 const int local = k - se;
-                const int yy = sy0 + local / sw, xx = sx0 + local % sw;
-                f(sg, yy * tx + xx);
+                // local / sw by a binary32 reciprocal, off by at most one, then fixed
+                int qy = (int)((float)local * __frcp_rn((float)sw));
+                if (qy * sw > local) qy--;
+                else if ((qy + 1) * sw <= local) qy++;
+                const int yy = sy0 + qy, xx = sx0 + (local - qy * sw);
+                f(sg, yy * tx + xx, sd);
             }
         }
     }
@@ -234,7 +245,7 @@ k_count_smem(gevo_layout L, int n, const float2* __restrict__ xy, const int* __r
     for (int t = threadIdx.x; t < nt; t += kBinThreads) s_hist[t] = 0u;
     __syncthreads();
     const int g0 = blockIdx.x * kBinChunk, g1 = min(n, g0 + kBinChunk);
-    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int, int t) { atomicAdd(s_hist + t, 1u); });
+    for_each_dup(L, v, n, g0, g1, xy, radius, nullptr, [&](int, int t, uint32_t) { atomicAdd(s_hist + t, 1u); });
     __syncthreads();
     uint32_t* dst = tile_count + L.tile_base[v];
     for (int t = threadIdx.x; t < nt; t += kBinThreads) {
@@ -257,7 +268,7 @@ k_scatter_smem(gevo_layout L, int n, const float2* __restrict__ xy, const int* _
     for (int t = threadIdx.x; t < nt; t += kBinThreads) s_hist[t] = 0u;
     __syncthreads();
     const int g0 = blockIdx.x * kBinChunk, g1 = min(n, g0 + kBinChunk);
-    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int, int t) { atomicAdd(s_hist + t, 1u); });
+    for_each_dup(L, v, n, g0, g1, xy, radius, nullptr, [&](int, int t, uint32_t) { atomicAdd(s_hist + t, 1u); });
     __syncthreads();
     // reserve a contiguous run of each touched tile's bucket for this block
     for (int t = threadIdx.x; t < nt; t += kBinThreads) {
@@ -265,10 +276,8 @@ k_scatter_smem(gevo_layout L, int n, const float2* __restrict__ xy, const int* _
         if (c) s_hist[t] = tile_start[base + t] + atomicAdd(tile_cursor + base + t, c);
     }
     __syncthreads();
-    const size_t vb = (size_t)v * n;
-    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int g, int t) {
+    for_each_dup(L, v, n, g0, g1, xy, radius, rgbz, [&](int g, int t, uint32_t dbits) {
         const uint32_t slot = atomicAdd(s_hist + t, 1u);
-        const uint32_t dbits = __float_as_uint(rgbz[vb + g].w);
         bucket[slot] = ((unsigned long long)dbits << 32) | (uint32_t)g;
     });
 }
@@ -287,7 +296,7 @@ k_count_off(gevo_layout L, int n, const float2* __restrict__ xy, const int* __re
     for (int t = threadIdx.x; t < nt; t += kBinThreads) s_hist[t] = 0u;
     __syncthreads();
     const int g0 = blockIdx.x * kBinChunk, g1 = min(n, g0 + kBinChunk);
-    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int, int t) { atomicAdd(s_hist + t, 1u); });
+    for_each_dup(L, v, n, g0, g1, xy, radius, nullptr, [&](int, int t, uint32_t) { atomicAdd(s_hist + t, 1u); });
     __syncthreads();
     uint32_t* dst = tile_count + L.tile_base[v];
     uint32_t* off = blk_off + (size_t)gridDim.x * L.tile_base[v] + (size_t)blockIdx.x * nt;
@@ -313,10 +322,8 @@ k_scatter_off(gevo_layout L, int n, const float2* __restrict__ xy, const int* __
     for (int t = threadIdx.x; t < nt; t += kBinThreads) s_hist[t] = tile_start[base + t] + off[t];
     __syncthreads();
     const int g0 = blockIdx.x * kBinChunk, g1 = min(n, g0 + kBinChunk);
-    const size_t vb = (size_t)v * n;
-    for_each_dup(L, v, n, g0, g1, xy, radius, [&](int g, int t) {
+    for_each_dup(L, v, n, g0, g1, xy, radius, rgbz, [&](int g, int t, uint32_t dbits) {
         const uint32_t slot = atomicAdd(s_hist + t, 1u);
-        const uint32_t dbits = __float_as_uint(rgbz[vb + g].w);
         bucket[slot] = ((unsigned long long)dbits << 32) | (uint32_t)g;
     });
 }
