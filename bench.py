@@ -304,6 +304,7 @@ def main():
 
     active_line = active_set_section(rep, target_rgb, target_depth, flush, stage_ms)
     mapping_line = mapping_section() if not args.no_mapping else None
+    micro = micro_peaks()
 
     # ---- rooflines (algorithmic work per launch / live event time) ---------------------
     pk = peaks()
@@ -363,7 +364,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": None, "roofline": roof, "clocks": clk, "active_set": active_line,
-            "mapping": mapping_line,
+            "mapping": mapping_line, "micro_peaks": micro,
             "wall_s_timed": wall1 - wall0}
     line["gpu_launches"] = launches_per_step(rep) * args.steps
 
@@ -450,6 +451,35 @@ def active_set_section(rep, target_rgb, target_depth, flush, stage_ms, reps=10):
             "backward_speedup_whole_lists": full / (ms["render_bwd_masked"] + ms["project_bwd_masked"]),
             "note": "E_k from the step's own render vs the stop-gradient targets; eps = 85th "
                     "percentile of max_k E_k(g) over the Gaussians some view blends (seen)"}
+
+
+def micro_peaks():
+    """Measured FP32 FMA and MUFU ex2 throughput (the units the blend and its
+    reverse walk use), against which the derived ALU peak can be checked."""
+    import torch
+
+    from paper_2409_09295_gb300 import _abi
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks = sms * 8
+    sink = torch.empty(blocks * 256, device="cuda")
+
+    def best_ms(fn):
+        fn()
+        t = []
+        for _ in range(3):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            e.synchronize()
+            t.append(s.elapsed_time(e))
+        return min(t)
+    it_f, it_e = 20000, 4000
+    ms_f = best_ms(lambda: _abi.gevo_bench_fma(blocks, it_f, sink))
+    ms_e = best_ms(lambda: _abi.gevo_bench_ex2(blocks, it_e, sink))
+    return {"fp32_fma_tflops": blocks * 256 * 16 * it_f / (ms_f / 1e3) / 1e12,
+            "ex2_per_s": blocks * 256 * 8 * it_e / (ms_e / 1e3),
+            "note": f"{blocks} blocks x 256 threads, 8 independent chains per thread"}
 
 
 def mapping_section():

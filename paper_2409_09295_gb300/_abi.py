@@ -119,6 +119,10 @@ MAP = ["gevo_map_activate", "gevo_map_step", "gevo_pose_step", "gevo_prune_keep"
        "gevo_gather_rows"]
 EXPORTS = EXPORTS + MAP
 
+# Every symbol include/gevo_bench.h declares.
+BENCH = ["gevo_bench_fma", "gevo_bench_ex2"]
+EXPORTS = EXPORTS + BENCH
+
 _lib = None
 
 
@@ -178,6 +182,9 @@ def load(build_if_missing: bool = True):
     L.gevo_prune_keep.argtypes = [i32, vp, vp, f32, vp, vp, vp, vp]
     L.gevo_gather_rows.argtypes = [i32, vp, vp, i32, vp, vp, vp]
     for name in MAP:
+        getattr(L, name).restype = ctypes.c_int
+    for name in BENCH:
+        getattr(L, name).argtypes = [i32, i32, vp, vp]
         getattr(L, name).restype = ctypes.c_int
     L.gevo_status_str.argtypes = [ctypes.c_int]
     L.gevo_status_str.restype = ctypes.c_char_p
@@ -504,3 +511,12 @@ def gevo_prune_keep(n, opacities, candidates, threshold, keep, keep_list, counts
 def gevo_gather_rows(n_max, lst, counts, width, src, dst, stream=None):
     _check("gevo_gather_rows", load().gevo_gather_rows(
         int(n_max), _p(lst), _p(counts), int(width), _p(src), _p(dst), _stream(stream)))
+
+
+# ---- measurement helpers (include/gevo_bench.h) -------------------------------------
+def gevo_bench_fma(blocks, iters, sink, stream=None):
+    _check("gevo_bench_fma", load().gevo_bench_fma(int(blocks), int(iters), _p(sink), _stream(stream)))
+
+
+def gevo_bench_ex2(blocks, iters, sink, stream=None):
+    _check("gevo_bench_ex2", load().gevo_bench_ex2(int(blocks), int(iters), _p(sink), _stream(stream)))

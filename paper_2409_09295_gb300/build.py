@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgevo.so")
-SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "loss.cu", "active.cu", "optim.cu", "gemm_tc.cu", "unet.cu", "init.cu"]
+SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "loss.cu", "active.cu", "optim.cu", "peaks.cu", "gemm_tc.cu", "unet.cu", "init.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
               "--expt-relaxed-constexpr"]

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     names = set()
-    for h in ("gevo.h", "gevo_prior.h", "gevo_map.h"):
+    for h in ("gevo.h", "gevo_prior.h", "gevo_map.h", "gevo_bench.h"):
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names |= set(re.findall(r"\b(gevo_[a-z0-9_]+)\s*\(", src))
