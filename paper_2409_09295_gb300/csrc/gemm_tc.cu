@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(128)
 k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, ConvA cv,
             const __nv_bfloat16* __restrict__ B, int ldb, void* __restrict__ C, int ldc,
             int out_bf16, const float* __restrict__ bias, int relu, float beta, int ksplit,
-            uint32_t* __restrict__ err)
+            uint32_t* __restrict__ err, int trans_c)
 {
     constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -254,7 +254,10 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
                     if (c < N) {
                         float x = v[i];
                         if (ksplit > 1) {   // split-K partial: FP32 atomic accumulation
-                            atomicAdd(reinterpret_cast<float*>(C) + (size_t)r * ldc + c, x);
+                            // (trans_c: C^T is stored, element (r, c) at c * ldc + r, so
+                            // the lanes' consecutive rows are consecutive addresses)
+                            atomicAdd(reinterpret_cast<float*>(C) +
+                                          (trans_c ? (size_t)c * ldc + r : (size_t)r * ldc + c), x);
                             continue;
                         }
                         if (bias) x += bias[c];
@@ -286,7 +289,7 @@ template <int BN, bool CONV>
 static gevo_status launch_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, ConvA cv,
                                const __nv_bfloat16* B, int ldb, void* C, int ldc, int out_bf16,
                                const float* bias, int relu, float beta, int ksplit, uint32_t* err,
-                               cudaStream_t st)
+                               cudaStream_t st, int trans_c)
 {
     const size_t smem = (size_t)(kGemmBM + BN) * kGemmBK * 2;
     static bool attr = false;
@@ -297,7 +300,7 @@ static gevo_status launch_gemm(int M, int N, int K, const __nv_bfloat16* A, int 
     }
     dim3 grid((M + kGemmBM - 1) / kGemmBM, (N + BN - 1) / BN, ksplit);
     k_gemm_bf16<BN, CONV><<<grid, 128, smem, st>>>(M, N, K, A, lda, cv, B, ldb, C, ldc, out_bf16,
-                                                   bias, relu, beta, ksplit, err);
+                                                   bias, relu, beta, ksplit, err, trans_c);
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }
@@ -306,23 +309,24 @@ template <bool CONV>
 static gevo_status gemm_dispatch(int M, int N, int K, const __nv_bfloat16* a, int lda, ConvA cv,
                                  const __nv_bfloat16* b, int ldb, void* C, int ldc, int out_bf16,
                                  const float* bias, int relu, float beta, int ksplit,
-                                 uint32_t* err, cudaStream_t st)
+                                 uint32_t* err, cudaStream_t st, int trans_c = 0)
 {
-    if (N <= 16) return launch_gemm<16, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
-    if (N <= 32) return launch_gemm<32, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
-    if (N <= 64) return launch_gemm<64, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
-    if (N <= 128) return launch_gemm<128, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
-    return launch_gemm<256, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st);
+    if (N <= 16) return launch_gemm<16, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    if (N <= 32) return launch_gemm<32, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    if (N <= 64) return launch_gemm<64, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    if (N <= 128) return launch_gemm<128, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    return launch_gemm<256, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
 }
 
 gevo_status gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C,
                       int ldc, int out_bf16, const float* bias, int relu, float beta, int ksplit,
-                      uint32_t* err, cudaStream_t st)
+                      uint32_t* err, cudaStream_t st, int trans_c)
 {
+    if (trans_c && ksplit <= 1) return GEVO_ERR_INVALID;   // transposed store: split-K path only
     ConvA cv{nullptr, 0, 0, 0};
     return gemm_dispatch<false>(M, N, K, reinterpret_cast<const __nv_bfloat16*>(A), lda, cv,
                                 reinterpret_cast<const __nv_bfloat16*>(B), ldb, C, ldc, out_bf16,
-                                bias, relu, beta, ksplit, err, st);
+                                bias, relu, beta, ksplit, err, st, trans_c);
 }
 
 gevo_status conv3x3_bf16(int nb, int H, int W, int Cin, const void* X, int Cout, const void* Wt,
@@ -348,5 +352,5 @@ extern "C" gevo_status gevo_gemm_bf16(int32_t M, int32_t N, int32_t K, const voi
         return GEVO_ERR_INVALID;
     if (M == 0 || N == 0) return GEVO_OK;
     return gevo::gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, out_bf16, bias, relu, beta, 1,
-                           reinterpret_cast<uint32_t*>(workspace), (cudaStream_t)stream);
+                           reinterpret_cast<uint32_t*>(workspace), (cudaStream_t)stream, 0);
 }

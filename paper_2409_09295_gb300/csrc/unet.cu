@@ -15,7 +15,7 @@
 namespace gevo {
 gevo_status gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C,
                       int ldc, int out_bf16, const float* bias, int relu, float beta, int ksplit,
-                      uint32_t* err, cudaStream_t st);
+                      uint32_t* err, cudaStream_t st, int trans_c);
 gevo_status conv3x3_bf16(int nb, int H, int W, int Cin, const void* X, int Cout, const void* Wt,
                          void* Y, int ldy, int out_bf16, const float* bias, int relu, float beta,
                          uint32_t* err, cudaStream_t st);
@@ -89,14 +89,17 @@ __global__ void __launch_bounds__(256)
 k_colT(int nb, int H, int W, int C, const bf16* __restrict__ X, size_t p0, size_t np,
        bf16* __restrict__ colT)
 {
-    __shared__ bf16 s_t[64][200];
+    // one block: 64 pixels x one tap; 16-byte (8-channel) loads of the shifted
+    // neighbour rows into shared memory, then rows of 64 pixels per channel out
+    __shared__ __align__(16) bf16 s_t[64][200];
     const int tap = blockIdx.y;
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     const size_t q0 = (size_t)blockIdx.x * 64;
-    for (int i = threadIdx.x; i < 64 * C; i += blockDim.x) {
-        const int r = i / C, c = i - r * C;
+    const int C8 = C / 8;
+    for (int i = threadIdx.x; i < 64 * C8; i += blockDim.x) {
+        const int r = i / C8, c8 = i - r * C8;
         const size_t q = q0 + r;
-        bf16 v = __float2bfloat16_rn(0.f);
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
         if (q < np) {
             const size_t p = p0 + q;
             const int x = (int)(p % W);
@@ -104,15 +107,25 @@ k_colT(int nb, int H, int W, int C, const bf16* __restrict__ X, size_t p0, size_
             const int y = (int)(t % H);
             const size_t b = t / H;
             const int yy = y + dy, xx = x + dx;
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = X[((b * H + yy) * W + xx) * C + c];
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = *reinterpret_cast<const uint4*>(X + ((b * H + yy) * W + xx) * C + 8 * c8);
         }
-        s_t[r][c] = v;
+        *reinterpret_cast<uint4*>(&s_t[r][8 * c8]) = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 64 * C; i += blockDim.x) {
-        const int c = i / 64, r = i - c * 64;
+    // two pixels per thread and store: 4-byte writes along each channel's row
+    for (int i = threadIdx.x; i < 32 * C; i += blockDim.x) {
+        const int c = i / 32, r = 2 * (i - c * 32);
         const size_t q = q0 + r;
-        if (q < np) colT[((size_t)tap * C + c) * np + q] = s_t[r][c];
+        bf16* dst = colT + ((size_t)tap * C + c) * np + q;
+        if (q + 1 < np) {
+            __nv_bfloat162 pr;
+            pr.x = s_t[r][c];
+            pr.y = s_t[r + 1][c];
+            *reinterpret_cast<__nv_bfloat162*>(dst) = pr;
+        } else if (q < np) {
+            *dst = s_t[r][c];
+        }
     }
     (void)nb;
 }
@@ -376,12 +389,18 @@ gevo_status gevo_conv3x3_wgrad(int32_t nb, int32_t H, int32_t W, int32_t Cin, co
         k_colT<<<g, 256, 0, st>>>(nb, H, W, Cin, reinterpret_cast<const bf16*>(X), p0, np,
                                   reinterpret_cast<bf16*>(colT));
         GEVO_CHECK_LAUNCH();
-        // dW[co][(tap, ci)] += dZ^T[co][p] * colT[(tap, ci)][p] over the chunk;
-        // dZ^T rows are P long, so the chunk is the column window [p0, p0 + np)
-        const int ksplit = (int)std::max<size_t>(1, std::min<size_t>(np / 8192, 128));
-        gevo_status s = gemm_bf16(Cout, K9, (int)np, reinterpret_cast<const bf16*>(dZt) + p0,
-                                  (int)P, colT, (int)np, dWt, K9, 0, nullptr, 0, 1.f, ksplit, err,
-                                  st);
+        // dW[co][(tap, ci)] += sum_p colT[(tap, ci)][p] dZ^T[co][p] over the chunk:
+        // rows of the product are the 9 Cin taps x channels (many: full 128-row
+        // MMA tiles), columns the Cout output channels, stored transposed into
+        // dW's [Cout][9 Cin] layout; dZ^T rows are P long, so the chunk is the
+        // column window [p0, p0 + np).  Enough K slices for about eight CTAs per
+        // SM, each at least 512 pixels long.
+        const size_t mtiles = ((size_t)K9 + 127) / 128;
+        const size_t want = ((size_t)sm_count() * 8 + mtiles - 1) / mtiles;
+        const int ksplit = (int)std::max<size_t>(2, std::min<size_t>(np / 512, want));
+        gevo_status s = gemm_bf16(K9, Cout, (int)np, colT, (int)np,
+                                  reinterpret_cast<const bf16*>(dZt) + p0, (int)P, dWt, K9, 0,
+                                  nullptr, 0, 1.f, ksplit, err, st, 1);
         if (s != GEVO_OK) return s;
     }
     return GEVO_OK;
