@@ -305,6 +305,7 @@ def main():
     active_line = active_set_section(rep, target_rgb, target_depth, flush, stage_ms)
     mapping_line = mapping_section() if not args.no_mapping else None
     micro = micro_peaks()
+    prior_line = prior_section() if not args.no_mapping else None
 
     # ---- rooflines (algorithmic work per launch / live event time) ---------------------
     pk = peaks()
@@ -364,7 +365,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": None, "roofline": roof, "clocks": clk, "active_set": active_line,
-            "mapping": mapping_line, "micro_peaks": micro,
+            "mapping": mapping_line, "micro_peaks": micro, "prior": prior_line,
             "wall_s_timed": wall1 - wall0}
     line["gpu_launches"] = launches_per_step(rep) * args.steps
 
@@ -480,6 +481,47 @@ def micro_peaks():
     return {"fp32_fma_tflops": blocks * 256 * 16 * it_f / (ms_f / 1e3) / 1e12,
             "ex2_per_s": blocks * 256 * 8 * it_e / (ms_e / 1e3),
             "note": f"{blocks} blocks x 256 threads, 8 independent chains per thread"}
+
+
+def prior_section(nb=32, H=240, W=320, steps=8):
+    """Training throughput of the learned depth prior (BF16 U-Net, tcgen05) at
+    batch 32 of 320x240 renders: images per second, and the convolutions'
+    algorithmic FLOPs (forward 2 P 9 Cin Cout per layer, backward twice that
+    but no data gradient for the first layer) per second against the measured
+    BF16 tensor peak."""
+    import numpy as np
+    import torch
+
+    from paper_2409_09295_gb300.prior import DepthUNet
+    net = DepthUNet(nb, H, W, seed=3)
+    rs = np.random.default_rng(0)
+    rgb = torch.from_numpy(rs.uniform(size=(nb, 3, H, W)).astype(np.float32)).cuda()
+    tar = torch.from_numpy(rs.normal(1.0, 0.3, size=nb * H * W).astype(np.float32)).cuda()
+    wgt = torch.ones_like(tar)
+    for _ in range(2):
+        net.train_step(rgb, tar, wgt)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        net.train_step(rgb, tar, wgt)
+    e.record()
+    e.synchronize()
+    ms = s.elapsed_time(e) / steps
+    flop = 0.0
+    for name, lay in net.layers.items():
+        lvl = int(name[3])
+        P = nb * net.hw[lvl][0] * net.hw[lvl][1]
+        cin = 3 if name == "enc0a" else lay["cin"]   # RGB input, padded to 8 channels
+        f = 2.0 * P * 9 * cin * lay["cout"]
+        flop += f * (2.0 if name == "enc0a" else 3.0)
+    pk = peaks()
+    peak = float(pk.get("bf16_tflops", 1900.0))
+    ach = flop / (ms / 1e3) / 1e12
+    return {"images_per_s": nb / (ms / 1e3), "ms_per_step": ms, "batch": nb, "image": f"{W}x{H}",
+            "conv_tflops": ach, "bf16_peak_tflops": peak, "frac": ach / peak,
+            "note": "train step (forward, L1, backward, Adam) with host launches included; "
+                    "channels 16-128 keep the MMAs small, so the step is far from the tensor peak"}
 
 
 def mapping_section():
