@@ -59,6 +59,9 @@ def test_layout_and_workspace_host_calls():
         _abi.gevo_layout_init([], [])
     with pytest.raises(_abi.GevoError):
         _abi.gevo_layout_init([0], [10])
+    assert _abi.gevo_layout_init([16] * 64, [16] * 64).n_views == 64     # the maximum
+    with pytest.raises(_abi.GevoError):
+        _abi.gevo_layout_init([16] * 65, [16] * 65)
     assert _abi.gevo_status_str(2) == "duplicate capacity exceeded"
     assert _abi.gevo_version() == 1
 

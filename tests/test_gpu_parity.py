@@ -518,3 +518,38 @@ def test_autograd_function_matches_pipeline():
         for p, k in zip(params, ("means", "scales", "quats", "opacities", "sh")):
             grad_close(_np(p.grad), acc[k], k)
         grad_close(_np(twist.grad), dxi, "dxi")
+
+
+def test_maximum_view_count_batched_equals_single():
+    """A layout with the maximum of 64 views (GEVO_MAX_VIEWS), of mixed small
+    sizes: each view's image is bitwise the single-view one, and each view's
+    pose gradient matches."""
+    rs = np.random.default_rng(64)
+    n = 3000
+    scene = scenes.room_scene(n, 1064, sh_degree=1)
+    cams = []
+    for v in range(64):
+        eye = rs.uniform(-3.0, 3.0, 3) * [1.0, 0.3, 1.0]
+        W, H = (48, 32) if v % 3 else (37, 21)
+        cams.append(scenes.camera(*scenes.look_at(eye, [0.0, 0.0, 0.0]), 40, 40, W / 2, H / 2, W, H))
+    sizes = [(c["W"], c["H"]) for c in cams]
+    g = raster.gaussians_to_device(scene)
+    camt = raster.camera_tensor(cams)
+    big = raster.Pipeline(n, sizes, 2_000_000, colour="sh", sh_degree=1,
+                          tuning=dict(threads_per_tile=64, persistent=1, blocks_per_sm=0))
+    big.forward(g, camt)
+    gC = torch.from_numpy(rs.normal(size=3 * big.P).astype(np.float32)).to(big.device)
+    big.render_bwd(gC)
+    big.project_bwd(g, camt)
+    torch.cuda.synchronize()
+    assert big.last_error() == 0
+    for v in (0, 1, 31, 62, 63):
+        one = raster.Pipeline(n, [sizes[v]], 2_000_000, colour="sh", sh_degree=1)
+        c1 = camt[v:v + 1].contiguous()
+        one.forward(g, c1)
+        assert torch.equal(big.view_rgb(big.rgb, v), one.view_rgb(one.rgb, 0))
+        assert torch.equal(big.view_plane(big.n_contrib, v), one.view_plane(one.n_contrib, 0))
+        p0, p1 = big.pix_base[v], big.pix_base[v + 1]
+        one.render_bwd(gC[3 * p0:3 * p1].contiguous())
+        one.project_bwd(g, c1)
+        grad_close(_np(one.dxi[0]), _np(big.dxi[v]), f"dxi view {v}")
