@@ -185,18 +185,27 @@ __device__ __forceinline__ void for_each_dup(const gevo_layout& L, int v, int n,
     const int lane = threadIdx.x & 31;
     const int tx = L.tiles_x[v], ty = L.tiles_y[v];
     const size_t vb = (size_t)v * n;
+    // the next group's record fields are loaded while this group is expanded
+    int rn = 0;
+    float2 mn = make_float2(0.f, 0.f);
+    uint32_t dn = 0u;
+    auto fetch = [&](int gg) {
+        rn = 0;
+        if (gg < g1) {
+            rn = radius[vb + gg];
+            mn = xy[vb + gg];
+            if (rgbz) dn = __float_as_uint(__ldg(reinterpret_cast<const float*>(rgbz + vb + gg) + 3));
+        }
+    };
+    fetch(g0 + (int)(threadIdx.x & ~31) + lane);
     for (int gs = g0 + (int)(threadIdx.x & ~31); gs < g1; gs += kBinThreads) {
         const int g = gs + lane;
+        const int r = rn;
+        const float2 m = mn;
+        const uint32_t dbits = r > 0 ? dn : 0u;
+        fetch(g + kBinThreads);
         int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
-        uint32_t dbits = 0u;
-        if (g < g1) {
-            const int r = radius[vb + g];
-            if (r > 0) {
-                const float2 m = xy[vb + g];
-                tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
-                if (rgbz) dbits = __float_as_uint(__ldg(reinterpret_cast<const float*>(rgbz + vb + g) + 3));
-            }
-        }
+        if (r > 0) tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
         const int w = x1 - x0;
         const int area = w * (y1 - y0);
         int incl = area;
