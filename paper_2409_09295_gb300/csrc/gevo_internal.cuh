@@ -82,6 +82,16 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// 1/x to within 1 ulp (PTX rcp.approx): the reverse walk's transmittance
+// recovery, where a per-step ulp is far below the gradients' tolerance and no
+// integer decision depends on the result.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 int sm_count();
 int device_max_smem_optin();
 

@@ -557,7 +557,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                         if (!use[k]) continue;
                         const float alpha = al[k];
                         const float om = 1.f - alpha;
-                        const float Ti = T[k] * __frcp_rn(om);
+                        const float Ti = T[k] * rcp_approx(om);
                         T[k] = Ti;
                         a_e += alpha * Ti * pe[k];
                         S0[k] = alpha * r.x + om * S0[k];
@@ -585,7 +585,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     const float alpha = al[k];
                     const float dy = dyk[k];
                     const float om = 1.f - alpha;
-                    const float inv = __frcp_rn(om);
+                    const float inv = rcp_approx(om);
                     const float Ti = T[k] * inv;
                     T[k] = Ti;
                     const float w = alpha * Ti;
