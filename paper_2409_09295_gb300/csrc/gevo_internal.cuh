@@ -92,6 +92,14 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// sqrt(x) to within a few ulp (PTX sqrt.approx).
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 int sm_count();
 int device_max_smem_optin();
 

@@ -38,7 +38,8 @@ __device__ __forceinline__ float4 prescale(float4 co)
 // the ellipse d^T Q d <= 2 ln(255 o) has half-extents sqrt(k2 Sigma_xx) and
 // sqrt(k2 Sigma_yy), Sigma = Q^-1.  det(Q) uses Kahan's fused 2x2 determinant
 // so elongated splats keep full precision; the box is widened by 0.1% + 1 px,
-// far more than the binary32 error of the per-pixel test near its threshold.
+// far more than the binary32 error of the per-pixel test near its threshold
+// and the few-ulp error of the approximate reciprocal and square root.
 // Returns (xmin, xmax, ymin, ymax); an empty box if o < 1/255.
 __device__ __forceinline__ float4 alpha_box(float2 m, float4 co)
 {
@@ -49,9 +50,10 @@ __device__ __forceinline__ float4 alpha_box(float2 m, float4 co)
     const float w = co.y * co.y;
     const float e = __fmaf_rn(-co.y, co.y, w);
     const float det = __fmaf_rn(co.x, co.z, -w) + e;
-    const float sxx = co.z / det, syy = co.x / det;
-    const float hx = sqrtf(k2 * sxx) * 1.001f + 1.f;
-    const float hy = sqrtf(k2 * syy) * 1.001f + 1.f;
+    const float rdet = rcp_approx(det);
+    const float sxx = co.z * rdet, syy = co.x * rdet;
+    const float hx = sqrt_approx(k2 * sxx) * 1.001f + 1.f;
+    const float hy = sqrt_approx(k2 * syy) * 1.001f + 1.f;
     if (!(det > 0.f) || !(hx < 1e30f) || !(hy < 1e30f))
         return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);   // degenerate: never cull
     return make_float4(m.x - hx, m.x + hx, m.y - hy, m.y + hy);
@@ -64,7 +66,10 @@ __device__ __forceinline__ float4 alpha_box(float2 m, float4 co)
 // minimum over the pixels) is compared with 2 ln(255 o), the level below which
 // alpha < 1/255: zero if the mean lies inside, else the least of the four
 // edge minima (a 1-D quadratic per edge, its vertex clamped to the edge).  The
-// threshold is widened by 0.2% + 2e-4 against rounding.  A strip the bounding
+// threshold is widened by 0.2% + 2e-4 against rounding.  The edge vertex is
+// placed with approximate reciprocals: a vertex off by a few ulp raises q by
+// c * delta^2 only (second order), far inside that margin; conics with an
+// entry at or below 1e-30 take the box test alone.  A strip the bounding
 // box of the ellipse overlaps but the ellipse itself misses -- a thin or
 // tilted splat crossing a corner -- is culled, which the box alone cannot.
 __device__ __forceinline__ uint32_t strip_mask(float2 m, float4 co, float x0, float y0, int nw,
@@ -75,7 +80,8 @@ __device__ __forceinline__ uint32_t strip_mask(float2 m, float4 co, float x0, fl
     const float a = co.x, b = co.y, c = co.z;
     const float lg = __logf(255.f * co.w);
     const float k2 = (2.f * fmaxf(lg, 0.f) + 2e-4f) * 1.002f;
-    const bool exact = a > 0.f && c > 0.f && box.x > -1e29f;   // else box only
+    const bool exact = a > 1e-30f && c > 1e-30f && box.x > -1e29f;   // else box only
+    const float ra = rcp_approx(a), rc = rcp_approx(c);
     const float dxl = m.x - (x0 + (float)(kTile - 1)), dxh = m.x - x0;
     const bool in_x = dxl <= 0.f && dxh >= 0.f;
     uint32_t mask = 0u;
@@ -91,10 +97,10 @@ __device__ __forceinline__ uint32_t strip_mask(float2 m, float4 co, float x0, fl
 #pragma unroll
             for (int e = 0; e < 2; e++) {
                 const float dx = ex[e];
-                const float dy = fminf(fmaxf(-b * dx / c, dyl), dyh);
+                const float dy = fminf(fmaxf(-b * dx * rc, dyl), dyh);
                 q = fminf(q, a * dx * dx + 2.f * b * dx * dy + c * dy * dy);
                 const float dy2 = ey[e];
-                const float dx2 = fminf(fmaxf(-b * dy2 / a, dxl), dxh);
+                const float dx2 = fminf(fmaxf(-b * dy2 * ra, dxl), dxh);
                 q = fminf(q, a * dx2 * dx2 + 2.f * b * dx2 * dy2 + c * dy2 * dy2);
             }
         }
