@@ -355,10 +355,25 @@ __device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t* s_tmp)
     return off + incl - v;
 }
 
+// The lanes whose 9-bit value equals this lane's (bit 8 marks an empty slot),
+// from one ballot per bit; measured faster here than the match instruction
+// on rounds of low depth bytes, which hold up to 32 distinct values.
+__device__ __forceinline__ uint32_t match_digit(uint32_t dg)
+{
+    uint32_t peers = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; b++) {
+        const bool bit = (dg >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? m : ~m;
+    }
+    return peers;
+}
+
 // One stable LSD pass over the byte of `a` at bit `shift`, a -> b.  Warp w owns
 // the contiguous chunk [w L/8, (w+1) L/8): it counts its digits, one block scan
 // turns the per-warp counts into per-warp digit offsets, then each warp scatters
-// its chunk in rounds of 32 with warp-synchronous ranking (match_any).  Order is
+// its chunk in rounds of 32 with warp-synchronous ranking (match_digit).  Order is
 // kept at every level (chunk, round, lane), so the pass is stable; the block
 // synchronises five times per pass whatever the tile's length.
 __device__ void radix_pass(const unsigned long long* a, unsigned long long* b, int L, int shift,
@@ -388,7 +403,7 @@ __device__ void radix_pass(const unsigned long long* a, unsigned long long* b, i
         const bool valid = i < hi;
         const unsigned long long key = valid ? a[i] : 0ull;
         const uint32_t dg = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t peers = match_digit(dg);
         if (valid) b[s_off[warp][dg] + __popc(peers & lt)] = key;
         __syncwarp();
         if (valid && (__ffs(peers) - 1) == lane) s_off[warp][dg] += __popc(peers);
@@ -428,7 +443,7 @@ __device__ void radix_pass_kv(const uint32_t* ka, const uint16_t* ia, uint32_t* 
         const uint32_t key = valid ? ka[i] : 0u;
         const uint16_t idx = valid ? ia[i] : (uint16_t)0;
         const uint32_t dg = valid ? ((key >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const uint32_t peers = match_digit(dg);
         if (valid) {
             const uint32_t pos = s_off[warp][dg] + __popc(peers & lt);
             kb[pos] = key;
