@@ -110,13 +110,18 @@ __device__ __forceinline__ uint32_t strip_mask(float2 m, float4 co, float x0, fl
 }
 
 
-// log2 of the Gaussian falloff at offset (dx, dy); identical in both passes.
-__device__ __forceinline__ float power2_at(const float4& co, float dx, float dy)
+// log2 of the Gaussian falloff at offset (dx, dy) with the pre-scaled conic,
+// a' dx^2 + (b' dx + c' dy) dy: a thread's pixels share their column, so
+// a' dx^2 and b' dx (power2_col) are formed once per entry and each pixel costs
+// two FMAs.  Both passes evaluate exactly this expression.
+__device__ __forceinline__ float2 power2_col(const float4& co, float dx)
 {
-    const float ax = __fmul_rn(co.x, dx);
-    const float cy = __fmul_rn(co.z, dy);
-    const float bxy = __fmul_rn(__fmul_rn(co.y, dx), dy);
-    return __fmaf_rn(ax, dx, __fmaf_rn(cy, dy, bxy));
+    return make_float2(__fmul_rn(__fmul_rn(co.x, dx), dx), __fmul_rn(co.y, dx));
+}
+
+__device__ __forceinline__ float power2_at(const float4& co, float2 col, float dy)
+{
+    return __fmaf_rn(__fmaf_rn(co.z, dy, col.y), dy, col.x);
 }
 
 __device__ __forceinline__ void tile_of(const gevo_layout& L, int tile, int& v, int& x0, int& y0)
@@ -232,10 +237,11 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 // the PPT pixels are independent: evaluate them branch-free so
                 // their dependency chains interleave
                 float p2[PPT], G[PPT];
+                const float2 col = power2_col(c, dx);
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     const float dy = __fsub_rn(m.y, (float)(py0 + k));
-                    p2[k] = power2_at(c, dx, dy);
+                    p2[k] = power2_at(c, col, dy);
                 }
 #pragma unroll
                 for (int k = 0; k < PPT; k++) G[k] = ex2_approx(p2[k]);
@@ -536,10 +542,11 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 const float4 c = s_co[j];
                 const float dx = __fsub_rn(m.x, fpx);
                 float p2[PPT], G[PPT], dyk[PPT];
+                const float2 col = power2_col(c, dx);
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     dyk[k] = __fsub_rn(m.y, (float)(py0 + k));
-                    p2[k] = power2_at(c, dx, dyk[k]);
+                    p2[k] = power2_at(c, col, dyk[k]);
                 }
 #pragma unroll
                 for (int k = 0; k < PPT; k++) G[k] = ex2_approx(p2[k]);
