@@ -291,6 +291,11 @@ __device__ __forceinline__ unsigned long long visible_views(const gevo_layout& L
     return m;
 }
 
+// Per-view pose-gradient sums are kept in shared memory in kDxiCopies copies,
+// lane l adding into copy l % kDxiCopies: lanes of a warp that reach the same
+// view at once would otherwise serialise on one address.
+constexpr int kDxiCopies = 8;
+
 // Geometry part of the projection derivative: mean (through the camera-frame
 // mean, the image mean, the depth and the EWA Jacobian), scale and rotation
 // (through Sigma3), opacity, RGB colours if given, and the pose twist except
@@ -309,11 +314,11 @@ k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
                   const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count)
 {
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
-    __shared__ float s_dxi[GEVO_MAX_VIEWS][6];
+    __shared__ float s_dxi[GEVO_MAX_VIEWS][kDxiCopies][6];
     const int total = list ? (int)*list_count : n;
     if ((int)(blockIdx.x * blockDim.x) >= total) return;   // whole block: before any barrier
     load_cams(L, cams, s_cam);
-    for (int i = threadIdx.x; i < L.n_views * 6; i += blockDim.x) (&s_dxi[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < L.n_views * kDxiCopies * 6; i += blockDim.x) (&s_dxi[0][0][0])[i] = 0.f;
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = t < total ? (list ? (int)list[t] : t) : n;
@@ -410,7 +415,7 @@ k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
                     for (int j = 0; j < 3; j++)
                         B[3 * i + j] = dW[3 * i] * cam.R[3 * j] + dW[3 * i + 1] * cam.R[3 * j + 1] +
                                        dW[3 * i + 2] * cam.R[3 * j + 2];
-                float* o = s_dxi[v];
+                float* o = s_dxi[v][threadIdx.x % kDxiCopies];
                 atomicAdd(o + 0, dp[0]);
                 atomicAdd(o + 1, dp[1]);
                 atomicAdd(o + 2, dp[2]);
@@ -447,7 +452,9 @@ k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
     if (dxi) {
         __syncthreads();
         for (int i = threadIdx.x; i < L.n_views * 6; i += blockDim.x) {
-            const float r = (&s_dxi[0][0])[i];
+            float r = 0.f;
+#pragma unroll
+            for (int c = 0; c < kDxiCopies; c++) r += s_dxi[i / 6][c][i % 6];
             if (r != 0.f) atomicAdd(dxi + i, r);
         }
     }
@@ -467,11 +474,11 @@ k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
-    __shared__ float s_dxi[GEVO_MAX_VIEWS][3];
+    __shared__ float s_dxi[GEVO_MAX_VIEWS][kDxiCopies][3];
     const int total = list ? (int)*list_count : n;
     if ((int)(blockIdx.x * blockDim.x) >= total) return;   // whole block: before any barrier
     load_cams(L, cams, s_cam);
-    for (int i = threadIdx.x; i < L.n_views * 3; i += blockDim.x) (&s_dxi[0][0])[i] = 0.f;
+    for (int i = threadIdx.x; i < L.n_views * kDxiCopies * 3; i += blockDim.x) (&s_dxi[0][0][0])[i] = 0.f;
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = t < total ? (list ? (int)list[t] : t) : n;
@@ -519,7 +526,7 @@ k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
                     // camera centre c = -R^T (t + rho): dL/drho = -R dL/dc = R (dL/d(mu - c))
 #pragma unroll
                     for (int i = 0; i < 3; i++)
-                        atomicAdd(&s_dxi[v][i], cam.R[3 * i] * ex + cam.R[3 * i + 1] * ey +
+                        atomicAdd(&s_dxi[v][threadIdx.x % kDxiCopies][i], cam.R[3 * i] * ex + cam.R[3 * i + 1] * ey +
                                                     cam.R[3 * i + 2] * ez);
                 }
             }
@@ -544,7 +551,9 @@ k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
         __syncthreads();
         for (int v = threadIdx.x; v < L.n_views; v += blockDim.x)
             for (int i = 0; i < 3; i++) {
-                const float r = s_dxi[v][i];
+                float r = 0.f;
+#pragma unroll
+                for (int c = 0; c < kDxiCopies; c++) r += s_dxi[v][c][i];
                 if (r != 0.f) atomicAdd(dxi + 6 * v + i, r);
             }
     }
