@@ -294,7 +294,7 @@ __device__ __forceinline__ unsigned long long visible_views(const gevo_layout& L
 // Per-view pose-gradient sums are kept in shared memory in kDxiCopies copies,
 // lane l adding into copy l % kDxiCopies: lanes of a warp that reach the same
 // view at once would otherwise serialise on one address.
-constexpr int kDxiCopies = 8;
+constexpr int kDxiCopies = 16;
 
 // Geometry part of the projection derivative: mean (through the camera-frame
 // mean, the image mean, the depth and the EWA Jacobian), scale and rotation

@@ -607,10 +607,9 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     // and the suffix update S <- S + alpha (c - S)
                     const float d0 = r.x - S0[k], d1 = r.y - S1[k], d2 = r.z - S2[k];
                     const float dD = DD ? r.w - SD[k] : 0.f;
-                    float dLda = gC0[k] * d0 + gC1[k] * d1 + gC2[k] * d2;
-                    if (DD) dLda += gD[k] * dD;
-                    dLda = dLda * Ti;
-                    if (DT) dLda -= gTT[k] * inv;
+                    // dL/dalpha = T_i (c - S) . dL/dC (- dL/dT_final T_final / (1 - alpha))
+                    float gd = gC0[k] * d0 + gC1[k] * d1 + gC2[k] * d2;
+                    if (DD) gd += gD[k] * dD;
                     S0[k] += alpha * d0;
                     S1[k] += alpha * d1;
                     S2[k] += alpha * d2;
@@ -618,14 +617,24 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     a_r += gC0[k] * w; a_g += gC1[k] * w; a_b += gC2[k] * w;
                     if (DD) a_z += gD[k] * w;
                     if (__fmul_rn(c.w, G[k]) <= kAlphaMax) {
-                        a_o += dLda * G[k];
-                        const float dp = dLda * alpha;
+                        // dp = dL/dalpha * alpha
+                        float dp;
+                        if (DT) {
+                            const float dLda = gd * Ti - gTT[k] * inv;
+                            a_o += dLda * G[k];
+                            dp = dLda * alpha;
+                        } else {
+                            dp = gd * w;
+                        }
                         const float t = dp * dy;
                         m0 += dp;
                         m1 += t;
                         m2 += t * dy;
                     }
                 }
+                // without dL/dT_final, dL/do = sum dL/dalpha G = m0 / o (alpha = o G
+                // on every unclamped pixel), one product per entry
+                if (!DT) a_o = m0 * rcp_approx(c.w);
                 // d alpha / d(a, b, c) = alpha (-dx^2 / 2, -dx dy, -dy^2 / 2);
                 // d alpha / d(mean) = alpha ln2 (2 a' dx + b' dy, 2 c' dy + b' dx)
                 // with the pre-scaled conic (a', b', c')
