@@ -465,14 +465,19 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
         const size_t vbase = (size_t)v * n;
         const float fpx = (float)px;
 
-        float T[PPT], S0[PPT], S1[PPT], S2[PPT], SD[PPT];
+        // Only the projection of the suffix colour and depth S onto the
+        // pixel's upstream gradient, Pg = dL/dC . S (+ dL/dD S_D), enters
+        // dL/dalpha = T_i (dL/dC . c + dL/dD z - Pg), and it follows
+        // S <- S + alpha (c - S) as Pg <- Pg + alpha (q - Pg), q = dL/dC . c +
+        // dL/dD z: one scalar per pixel instead of four.
+        float T[PPT], Pg[PPT];
         float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gTT[PPT], pe[PPT];
         uint32_t last[PPT];
         uint32_t mymax = 0;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
             const int py = py0 + k;
-            S0[k] = bg0; S1[k] = bg1; S2[k] = bg2; SD[k] = 0.f;
+            Pg[k] = 0.f;
             if (px < W && py < H) {
                 const size_t pix = (size_t)py * W + px;
                 const size_t gp = (size_t)L.pix_base[v] + pix;
@@ -483,6 +488,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 gD[k] = DD ? dL_dd[gp] : 0.f;
                 gTT[k] = DT ? dL_dT[gp] * T[k] : 0.f;
                 pe[k] = (EXT && pix_err) ? pix_err[gp] : 0.f;
+                Pg[k] = gC0[k] * bg0 + gC1[k] * bg1 + gC2[k] * bg2;
                 if (EXT && act_last) {
                     // start at the last active entry: what lies behind it is
                     // summarised by the transmittance after it and the colour
@@ -492,8 +498,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                         const float Ta = act_T[gp];
                         const float4 q = act_rest[gp];
                         T[k] = Ta;
-                        S0[k] = __fdiv_rn(q.x, Ta); S1[k] = __fdiv_rn(q.y, Ta);
-                        S2[k] = __fdiv_rn(q.z, Ta); SD[k] = __fdiv_rn(q.w, Ta);
+                        Pg[k] = __fdiv_rn(gC0[k] * q.x + gC1[k] * q.y + gC2[k] * q.z + gD[k] * q.w, Ta);
                     }
                 }
             } else {
@@ -573,10 +578,9 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                         const float Ti = T[k] * rcp_approx(om);
                         T[k] = Ti;
                         a_e += alpha * Ti * pe[k];
-                        S0[k] = alpha * r.x + om * S0[k];
-                        S1[k] = alpha * r.y + om * S1[k];
-                        S2[k] = alpha * r.z + om * S2[k];
-                        if (DD) SD[k] = alpha * r.w + om * SD[k];
+                        float qc = gC0[k] * r.x + gC1[k] * r.y + gC2[k] * r.z;
+                        if (DD) qc += gD[k] * r.w;
+                        Pg[k] += alpha * (qc - Pg[k]);
                     }
                     if (pix_err) {
 #pragma unroll
@@ -603,17 +607,12 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     T[k] = Ti;
                     const float w = alpha * Ti;
                     if (EXT) a_e += w * pe[k];
-                    // colour behind minus this entry's colour, shared by dL/dalpha
-                    // and the suffix update S <- S + alpha (c - S)
-                    const float d0 = r.x - S0[k], d1 = r.y - S1[k], d2 = r.z - S2[k];
-                    const float dD = DD ? r.w - SD[k] : 0.f;
-                    // dL/dalpha = T_i (c - S) . dL/dC (- dL/dT_final T_final / (1 - alpha))
-                    float gd = gC0[k] * d0 + gC1[k] * d1 + gC2[k] * d2;
-                    if (DD) gd += gD[k] * dD;
-                    S0[k] += alpha * d0;
-                    S1[k] += alpha * d1;
-                    S2[k] += alpha * d2;
-                    if (DD) SD[k] += alpha * dD;
+                    // (c - S) . dL/dC, shared by dL/dalpha = T_i gd
+                    // (- dL/dT_final T_final / (1 - alpha)) and the suffix update
+                    float qc = gC0[k] * r.x + gC1[k] * r.y + gC2[k] * r.z;
+                    if (DD) qc += gD[k] * r.w;
+                    const float gd = qc - Pg[k];
+                    Pg[k] += alpha * gd;
                     a_r += gC0[k] * w; a_g += gC1[k] * w; a_b += gC2[k] * w;
                     if (DD) a_z += gD[k] * w;
                     if (__fmul_rn(c.w, G[k]) <= kAlphaMax) {
