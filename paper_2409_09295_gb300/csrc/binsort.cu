@@ -8,10 +8,12 @@
 //                  total D and a heaviest-first tile order for later kernels;
 //   3. k_scatter : each duplicate (depth bits << 32 | id) goes into its tile's
 //                  bucket (8 bytes written per duplicate);
-//   4. k_segsort : one block per tile sorts its bucket in shared memory (stable
-//                  LSD radix over the varying depth bytes, each warp scattering
-//                  its own chunk, then equal depths by id) and writes the final
-//                  64-bit keys and 32-bit values.
+//   4. k_segsort : one block per tile sorts its bucket (stable LSD radix, each
+//                  warp scattering its own chunk, then equal depths by id): in
+//                  shared memory over 9-bit digits of the depth bits minus the
+//                  tile's least, up to 2048 entries; through L2 over the
+//                  varying depth bytes beyond that.  It writes the final 64-bit
+//                  keys and 32-bit values.
 // The tile is handled by counting, so the sort only moves the depth half; the
 // result is the unique (tile, depth bits, id) order, identical to a full sort.
 #include "gevo_internal.cuh"
@@ -355,14 +357,15 @@ __device__ __forceinline__ uint32_t block_exscan256(uint32_t v, uint32_t* s_tmp)
     return off + incl - v;
 }
 
-// The lanes whose 9-bit value equals this lane's (bit 8 marks an empty slot),
-// from one ballot per bit; measured faster here than the match instruction
-// on rounds of low depth bytes, which hold up to 32 distinct values.
-__device__ __forceinline__ uint32_t match_digit(uint32_t dg)
+// The lanes whose BITS-bit value equals this lane's (the top bit marks an
+// empty slot), from one ballot per bit; measured faster here than the match
+// instruction on rounds of low depth bits, which hold up to 32 distinct values.
+template <int BITS>
+__device__ __forceinline__ uint32_t match_bits(uint32_t dg)
 {
     uint32_t peers = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b < 9; b++) {
+    for (int b = 0; b < BITS; b++) {
         const bool bit = (dg >> b) & 1u;
         const uint32_t m = __ballot_sync(0xffffffffu, bit);
         peers &= bit ? m : ~m;
@@ -373,7 +376,7 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t dg)
 // One stable LSD pass over the byte of `a` at bit `shift`, a -> b.  Warp w owns
 // the contiguous chunk [w L/8, (w+1) L/8): it counts its digits, one block scan
 // turns the per-warp counts into per-warp digit offsets, then each warp scatters
-// its chunk in rounds of 32 with warp-synchronous ranking (match_digit).  Order is
+// its chunk in rounds of 32 with warp-synchronous ranking (match_bits).  Order is
 // kept at every level (chunk, round, lane), so the pass is stable; the block
 // synchronises five times per pass whatever the tile's length.
 __device__ void radix_pass(const unsigned long long* a, unsigned long long* b, int L, int shift,
@@ -403,7 +406,7 @@ __device__ void radix_pass(const unsigned long long* a, unsigned long long* b, i
         const bool valid = i < hi;
         const unsigned long long key = valid ? a[i] : 0ull;
         const uint32_t dg = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
-        const uint32_t peers = match_digit(dg);
+        const uint32_t peers = match_bits<9>(dg);
         if (valid) b[s_off[warp][dg] + __popc(peers & lt)] = key;
         __syncwarp();
         if (valid && (__ffs(peers) - 1) == lane) s_off[warp][dg] += __popc(peers);
@@ -412,45 +415,62 @@ __device__ void radix_pass(const unsigned long long* a, unsigned long long* b, i
     __syncthreads();
 }
 
-// The same pass on (32-bit depth key, 16-bit position in the bucket) pairs
-// kept in shared memory: 6 bytes an item instead of 8, so more blocks fit on
-// an SM.
-__device__ void radix_pass_kv(const uint32_t* ka, const uint16_t* ia, uint32_t* kb, uint16_t* ib,
-                              int L, int shift, uint32_t (*s_off)[256], uint32_t* s_tmp)
+// The shared-memory pass, on (32-bit depth key, 16-bit position in the bucket)
+// pairs (6 bytes an item instead of 8, so more blocks fit on an SM) and 9-bit
+// digits of (key - kmin) at bit `shift`: the
+// depths of one tile span a range of about 2^26 in their bit patterns, which
+// three 9-bit passes cover where four byte passes were needed.  Per-warp digit
+// counts and offsets are 16-bit (a tile here holds at most 2048 items), packed
+// two to a word, so the 512 counters of each warp take the bytes the 256
+// 32-bit ones of the byte pass take.
+__device__ void radix_pass_kv9(const uint32_t* ka, const uint16_t* ia, uint32_t* kb, uint16_t* ib,
+                               int L, int shift, uint32_t kmin, uint32_t (*s_off)[256],
+                               uint32_t* s_tmp)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int chunk = (L + kSortWarps - 1) / kSortWarps;
     const int lo = min(L, warp * chunk), hi = min(L, lo + chunk);
     for (int d = lane; d < 256; d += 32) s_off[warp][d] = 0u;
     __syncwarp();
-    for (int i = lo + lane; i < hi; i += 32) atomicAdd(&s_off[warp][(ka[i] >> shift) & 255u], 1u);
-    __syncthreads();
-    uint32_t tot = 0;
-#pragma unroll
-    for (int w = 0; w < kSortWarps; w++) tot += s_off[w][tid];
-    uint32_t run = block_exscan256(tot, s_tmp);
-#pragma unroll
-    for (int w = 0; w < kSortWarps; w++) {
-        const uint32_t c = s_off[w][tid];
-        s_off[w][tid] = run;
-        run += c;
+    for (int i = lo + lane; i < hi; i += 32) {
+        const uint32_t dg = ((ka[i] - kmin) >> shift) & 511u;
+        atomicAdd(&s_off[warp][dg >> 1], 1u << ((dg & 1u) * 16));
     }
     __syncthreads();
+    // thread t owns digits 2t (low halves) and 2t + 1 (high halves)
+    uint32_t t0 = 0, t1 = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) {
+        const uint32_t pr = s_off[w][tid];
+        t0 += pr & 0xffffu;
+        t1 += pr >> 16;
+    }
+    uint32_t r0 = block_exscan256(t0 + t1, s_tmp);
+    uint32_t r1 = r0 + t0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; w++) {
+        const uint32_t pr = s_off[w][tid];
+        s_off[w][tid] = r0 | (r1 << 16);
+        r0 += pr & 0xffffu;
+        r1 += pr >> 16;
+    }
+    __syncthreads();
+    uint16_t* off = reinterpret_cast<uint16_t*>(s_off[warp]);
     const uint32_t lt = (1u << lane) - 1u;
     for (int r = lo; r < hi; r += 32) {
         const int i = r + lane;
         const bool valid = i < hi;
         const uint32_t key = valid ? ka[i] : 0u;
         const uint16_t idx = valid ? ia[i] : (uint16_t)0;
-        const uint32_t dg = valid ? ((key >> shift) & 255u) : 256u;
-        const uint32_t peers = match_digit(dg);
+        const uint32_t dg = valid ? (((key - kmin) >> shift) & 511u) : 512u;
+        const uint32_t peers = match_bits<10>(dg);
         if (valid) {
-            const uint32_t pos = s_off[warp][dg] + __popc(peers & lt);
+            const uint32_t pos = off[dg] + __popc(peers & lt);
             kb[pos] = key;
             ib[pos] = idx;
         }
         __syncwarp();
-        if (valid && (__ffs(peers) - 1) == lane) s_off[warp][dg] += __popc(peers);
+        if (valid && (__ffs(peers) - 1) == lane) off[dg] = (uint16_t)(off[dg] + __popc(peers));
         __syncwarp();
     }
     __syncthreads();
@@ -468,7 +488,7 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
     extern __shared__ uint32_t s_kv[];
     __shared__ uint32_t s_off[kSortWarps][256];
     __shared__ uint32_t s_tmp[kSortWarps];
-    __shared__ uint32_t s_or[kSortWarps], s_and[kSortWarps];
+    __shared__ uint32_t s_or[kSortWarps], s_and[kSortWarps], s_min[kSortWarps], s_max[kSortWarps];
     if (*d_n_dup > cap) return;
     const uint32_t tile = tile_order[blockIdx.x];
     const int L = (int)tile_count[tile];
@@ -482,8 +502,9 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
     uint32_t* kb = s_kv + kSortSmemItems;
     uint16_t* ia = reinterpret_cast<uint16_t*>(s_kv + 2 * kSortSmemItems);
     uint16_t* ib = ia + kSortSmemItems;
-    // which depth bytes vary inside this tile
-    uint32_t o = 0u, an = 0xffffffffu;
+    // which depth bytes vary inside this tile (long tiles), and the range of
+    // the depth bit patterns (short tiles)
+    uint32_t o = 0u, an = 0xffffffffu, mn = 0xffffffffu, mx = 0u;
     for (int i = tid; i < L; i += kSortThreads) {
         const uint32_t hi = (uint32_t)(a[i] >> 32);
         if (small) {
@@ -492,26 +513,36 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
         }
         o |= hi;
         an &= hi;
+        mn = min(mn, hi);
+        mx = max(mx, hi);
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         o |= __shfl_xor_sync(0xffffffffu, o, d);
         an &= __shfl_xor_sync(0xffffffffu, an, d);
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, d));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
     }
-    if ((tid & 31) == 0) { s_or[tid >> 5] = o; s_and[tid >> 5] = an; }
+    if ((tid & 31) == 0) {
+        s_or[tid >> 5] = o; s_and[tid >> 5] = an;
+        s_min[tid >> 5] = mn; s_max[tid >> 5] = mx;
+    }
     __syncthreads();
-    uint32_t vary = 0u;
+    uint32_t vary = 0u, kmin = 0xffffffffu, kmax = 0u;
     {
         uint32_t oo = 0u, aa = 0xffffffffu;
 #pragma unroll
-        for (int w = 0; w < kSortWarps; w++) { oo |= s_or[w]; aa &= s_and[w]; }
+        for (int w = 0; w < kSortWarps; w++) {
+            oo |= s_or[w]; aa &= s_and[w];
+            kmin = min(kmin, s_min[w]); kmax = max(kmax, s_max[w]);
+        }
         vary = oo ^ aa;
     }
     if (small) {
         if (L > 1) {
-            for (int d = 0; d < 4; d++) {
-                if (((vary >> (8 * d)) & 255u) == 0u) continue;
-                radix_pass_kv(ka, ia, kb, ib, L, 8 * d, s_off, s_tmp);
+            const int bits = 32 - __clz(kmax - kmin);   // 0 when all depths are equal
+            for (int shift = 0; shift < bits; shift += 9) {
+                radix_pass_kv9(ka, ia, kb, ib, L, shift, kmin, s_off, s_tmp);
                 uint32_t* t = ka; ka = kb; kb = t;
                 uint16_t* u = ia; ia = ib; ib = u;
             }

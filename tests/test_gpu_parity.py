@@ -45,7 +45,7 @@ def _np(t):
 # a2-a4: keys / sort / ranges, bit-exact
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("case", ["one_view", "uneven_views", "crowded_tile", "long_tiles",
-                                  "equal_depths", "empty"])
+                                  "equal_depths", "one_depth", "wide_depths", "empty"])
 def test_bin_sort_bit_exact(case):
     if case == "one_view":
         sizes, n, rec = [(64, 48)], 3000, None
@@ -69,6 +69,17 @@ def test_bin_sort_bit_exact(case):
         sizes, n = [(96, 64)], 3000
         rec = scenes.random_records(sizes, n, seed=32)
         rec["depth"][0] = np.round(rec["depth"][0] * 2.0).astype(np.float32) / 2.0
+    elif case == "one_depth":
+        # every entry ties on depth: no radix pass, the id order decides alone
+        sizes, n = [(64, 48)], 1500
+        rec = scenes.random_records(sizes, n, seed=34)
+        rec["depth"][0] = np.float32(3.0)
+    elif case == "wide_depths":
+        # depths log-uniform over 0.2 .. 1e6: the bit patterns of one tile span
+        # more than 2^27, so the shared-memory sort takes all four 9-bit passes
+        sizes, n = [(64, 48)], 3000
+        rec = scenes.random_records(sizes, n, seed=35)
+        rec["depth"][0] = np.exp(np.random.default_rng(5).uniform(np.log(0.2), np.log(1e6), n)).astype(np.float32)
     else:
         sizes, n, rec = [(64, 48)], 0, None
     if rec is None:
@@ -97,6 +108,10 @@ def test_bin_sort_bit_exact(case):
         assert lens.max() > 4096  # global-memory path
     if case == "long_tiles":
         assert ((lens > 2048) & (lens <= 4096)).sum() >= 2
+    if case == "wide_depths":
+        k = ref["keys"] & 0xffffffff
+        spans = [int(k[a:b].max()) - int(k[a:b].min()) for a, b in ref["ranges"] if 1 < b - a <= 2048]
+        assert max(spans) >= 1 << 27
 
 
 def test_bin_sort_overflow_sets_error_and_reports_true_count():
