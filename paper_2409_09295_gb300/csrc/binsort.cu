@@ -184,7 +184,14 @@ __device__ __forceinline__ void for_each_dup(const gevo_layout& L, int v, int n,
     // The duplicates of the warp's 32 Gaussians are laid end to end (warp
     // prefix sum of the rectangle areas) and dealt out round-robin to the
     // lanes, so every lane does the same amount of work whatever the sizes.
-    const int lane = threadIdx.x & 31;
+    // The Gaussians with a non-empty rectangle are packed into shared memory
+    // in lane order; the owner of duplicate k0 + p of a round of 32 is then
+    // (packed rectangles starting before k0) + (starts at k0 .. k0 + p) - 1,
+    // from one ballot, one OR-reduction and a population count.
+    __shared__ int4 s_rect[kBinThreads / 32][32];      // x0, y0, width, first duplicate
+    __shared__ uint2 s_gd[kBinThreads / 32][32];       // Gaussian, depth bits
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     const int tx = L.tiles_x[v], ty = L.tiles_y[v];
     const size_t vb = (size_t)v * n;
     // the next group's record fields are loaded while this group is expanded
@@ -210,6 +217,8 @@ __device__ __forceinline__ void for_each_dup(const gevo_layout& L, int v, int n,
         if (r > 0) tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
         const int w = x1 - x0;
         const int area = w * (y1 - y0);
+        const uint32_t nz = __ballot_sync(0xffffffffu, area > 0);
+        if (nz == 0u) continue;
         int incl = area;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -218,29 +227,29 @@ __device__ __forceinline__ void for_each_dup(const gevo_layout& L, int v, int n,
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         const int excl = incl - area;
+        __syncwarp();   // the previous group's readers are done
+        if (area > 0) {
+            const int c = __popc(nz & lt);
+            s_rect[warp][c] = make_int4(x0, y0, w, excl);
+            s_gd[warp][c] = make_uint2((uint32_t)g, dbits);
+        }
+        __syncwarp();
         for (int k0 = 0; k0 < total; k0 += 32) {
             const int k = k0 + lane;
-            // owner lane: the last lane whose exclusive prefix is <= k
-            int src = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int e = __shfl_sync(0xffffffffu, excl, src + step);
-                if (k >= e) src += step;
-            }
-            const int sx0 = __shfl_sync(0xffffffffu, x0, src);
-            const int sy0 = __shfl_sync(0xffffffffu, y0, src);
-            const int sw = __shfl_sync(0xffffffffu, w, src);
-            const int se = __shfl_sync(0xffffffffu, excl, src);
-            const int sg = __shfl_sync(0xffffffffu, g, src);
-            const uint32_t sd = __shfl_sync(0xffffffffu, dbits, src);
+            const bool starts = area > 0 && excl >= k0 && excl < k0 + 32;
+            const uint32_t M = __reduce_or_sync(0xffffffffu, starts ? 1u << (excl - k0) : 0u);
+            const int before = __popc(__ballot_sync(0xffffffffu, area > 0 && excl < k0));
             if (k < total) {
-                const int local = k - se;
-                // local / sw by a binary32 reciprocal, off by at most one, then fixed
-                int qy = (int)((float)local * __frcp_rn((float)sw));
-                if (qy * sw > local) qy--;
-                else if ((qy + 1) * sw <= local) qy++;
-                const int yy = sy0 + qy, xx = sx0 + (local - qy * sw);
-                f(sg, yy * tx + xx, sd);
+                const int own = before + __popc(M & (0xffffffffu >> (31 - lane))) - 1;
+                const int4 rc = s_rect[warp][own];
+                const uint2 gd = s_gd[warp][own];
+                const int local = k - rc.w;
+                // local / width by an approximate reciprocal, off by at most one, then fixed
+                int qy = (int)((float)local * rcp_approx((float)rc.z));
+                if (qy * rc.z > local) qy--;
+                else if ((qy + 1) * rc.z <= local) qy++;
+                const int yy = rc.y + qy, xx = rc.x + (local - qy * rc.z);
+                f((int)gd.x, yy * tx + xx, gd.y);
             }
         }
     }
