@@ -328,9 +328,9 @@ def main():
         "render_bwd": ("alu", FLOP_EXAMINE * E_bwd + FLOP_BLEND_BWD * B, "TFLOP/s"),
         "project_bwd": ("hbm", 2 * param_b * N + 4 * VN + 40 * vis, "GB/s"),
     }
-    kernels = {"project": "k_project_fwd", "bin_sort": "k_count_smem+k_scan+k_scatter_smem+k_segsort",
+    kernels = {"project": "k_project_fwd", "bin_sort": "k_count_off+k_scan+k_scatter_off+k_segsort",
                "render_fwd": "k_render_fwd", "loss": "k_loss_l1+k_zero_grad2d",
-               "render_bwd": "k_render_bwd", "project_bwd": "k_project_bwd"}
+               "render_bwd": "k_render_bwd", "project_bwd": "k_project_bwd_geo+k_project_bwd_col"}
     roofs = {}
     for name, (bound, amount, unit) in work.items():
         sec = stage_ms[name] / 1e3
@@ -342,9 +342,10 @@ def main():
                        "unit": unit, "frac": ach / peak, "ms": stage_ms[name]}
     dom = "render_bwd"   # the largest share of the step (profiles/ launch list)
     roof = dict(roofs[dom])
-    # DRAM bytes of one reverse-walk launch: ncu (dram__bytes_read.sum + write) on the
-    # 4-view case of profiles/render_kernels_4view_500k.md, 51.5 MB for 245.15M walked
-    # entries, scaled by entries to this launch (same scene, same resolution)
+    # DRAM bytes of one reverse-walk launch: ncu (dram__bytes_read.sum + write) of the
+    # current kernel on the 4-view case of profiles/render_kernels_4view_500k.md, 51.5 MB
+    # for 245.15M walked entries, scaled by entries to this launch (same scene, same
+    # resolution)
     roof.update({"traffic": 51.5e6 * E_bwd / 245.15e6,
                  "traffic_source": "ncu dram bytes of the 4-view case, scaled by walked entries",
                  "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {clk_peak:.0f} MHz"})
