@@ -555,16 +555,15 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 }
 #pragma unroll
                 for (int k = 0; k < PPT; k++) G[k] = ex2_approx(p2[k]);
+                // no warp-wide skip when no pixel uses the entry: the vote
+                // separates the test from the update, and measured slower
                 float al[PPT];
                 bool use[PPT];
-                bool any = false;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
                     al[k] = fminf(kAlphaMax, __fmul_rn(c.w, G[k]));
                     use[k] = pos < last[k] && !(p2[k] > 0.f) && !(al[k] < kAlphaMin);
-                    any = any || use[k];
                 }
-                if (!__any_sync(0xffffffffu, any)) continue;
                 const float4 r = s_rz[j];
                 const bool act = !EXT || !(s_id[j] >> 31);
                 if (EXT && !act) {
