@@ -260,13 +260,26 @@ def main():
         host_tr.numel() * 4 + host_td.numel() * 4
     d2h = out_loss.numel() * 4 + out_dxi.numel() * 4
 
+    # The parameters and cameras are uploaded first (projection reads them); the
+    # targets, first read by the loss stage, are uploaded on a second stream
+    # while projection, sort and blend run, and the loss stage waits for them.
+    main = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+
     def e2e_step():
+        side.wait_stream(main)             # the previous step is done with the targets
         for k, t in host_in.items():
             g[k].copy_(t, non_blocking=True)
         rep.camt.copy_(host_cams, non_blocking=True)
-        target_rgb.copy_(host_tr, non_blocking=True)
-        target_depth.copy_(host_td, non_blocking=True)
-        rep.replay()
+        params_in = torch.cuda.Event()
+        params_in.record(main)
+        side.wait_event(params_in)         # no contention with the parameter upload
+        with torch.cuda.stream(side):
+            target_rgb.copy_(host_tr, non_blocking=True)
+            target_depth.copy_(host_td, non_blocking=True)
+        targets_in = torch.cuda.Event()
+        targets_in.record(side)
+        rep.replay(before={"loss": lambda: main.wait_event(targets_in)})
         out_loss.copy_(rep.pipe.loss, non_blocking=True)
         out_dxi.copy_(rep.pipe.dxi, non_blocking=True)
 

@@ -158,14 +158,19 @@ class BatchedReplay:
             self.graphs.append((name, gph))
         torch.cuda.synchronize()
 
-    def replay(self, events=None):
+    def replay(self, events=None, before=None):
         """One step.  events: optional list of len(stages) + 1 timing events
-        recorded between the stage graphs on the current stream."""
+        recorded between the stage graphs on the current stream.  before:
+        optional {stage name: callable} run on the host right before that
+        stage's graph is launched, e.g. to make the current stream wait for an
+        upload the stage reads (the targets are first read by "loss")."""
         if self.graphs is None:
             self.capture()
         if events is not None:
             events[0].record()
-        for i, (_, gph) in enumerate(self.graphs):
+        for i, (name, gph) in enumerate(self.graphs):
+            if before and name in before:
+                before[name]()
             gph.replay()
             if events is not None:
                 events[i + 1].record()
