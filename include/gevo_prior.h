@@ -31,7 +31,8 @@ extern "C" {
  * [nb][H][W][Cin] BF16, Cin % 8 == 0; Wt: [Cout][9*Cin]; bias: float[Cout] or
  * NULL; Y: rows of stride ldy (BF16 if out_bf16 else FP32); act = ReLU if relu.
  * The data gradient of a convolution is this call on dZ with gevo_flip3x3
- * weights (no bias, no ReLU, FP32 out). */
+ * weights (no bias, no ReLU, FP32 out).  Sizes: H < 32768, W < 65536 and
+ * nb*H*W < 2^31, else GEVO_ERR_INVALID. */
 gevo_status gevo_conv3x3(int32_t nb, int32_t H, int32_t W, int32_t Cin, const void* X,
                          int32_t Cout, const void* Wt, const float* bias, void* Y, int32_t ldy,
                          int32_t out_bf16, int32_t relu, float beta, void* workspace,
@@ -41,7 +42,8 @@ gevo_status gevo_conv3x3(int32_t nb, int32_t H, int32_t W, int32_t Cin, const vo
  * (Wt's own layout; FP32, written).  dZt: dZ transposed,
  * [Cout][nb*H*W] BF16.  colT: caller scratch of 9*Cin*colT_pixels BF16 that
  * holds one chunk of the pixel-contiguous im2col at a time; the contraction
- * over pixels is split across CTAs and summed with FP32 atomics. */
+ * over pixels is split across CTAs and summed with FP32 atomics.  Sizes as
+ * for gevo_conv3x3. */
 gevo_status gevo_conv3x3_wgrad(int32_t nb, int32_t H, int32_t W, int32_t Cin, const void* X,
                                int32_t Cout, const void* dZt, void* colT, int64_t colT_pixels,
                                float* dWt, void* workspace, void* stream);

@@ -5,17 +5,21 @@
 //   C[M x N] = A[M x K] * B[N x K]^T  (+ bias[N]) (ReLU optional)
 //
 // A and B are row-major with K contiguous ("K-major").  One CTA of 128 threads
-// computes a 128 x BN tile (BN in {16, 32, 64, 128, 256}):
-//   1. every thread copies 16-byte pieces of the next 128 x 64 slice of A and
-//      BN x 64 slice of B into shared memory, arranged as the canonical
-//      no-swizzle K-major layout of 8-row x 16-byte core matrices (core
-//      matrices 128 B apart along K, 1 KB apart along M / N);
-//   2. one elected thread issues four tcgen05.mma (K = 16 each) that
-//      accumulate into a 128-lane x BN-column FP32 tile in tensor memory, then
-//      tcgen05.commit arrives on an mbarrier when they have completed;
-//   3. the CTA waits on the mbarrier (bounded: after ~1 s it records
-//      GEVO_ERR_TIMEOUT in the error word and stops issuing) before reusing
-//      the shared-memory slices;
+// computes a 128 x BN tile (BN in {16, 32, 64, 128, 256}) over K in slices of
+// 64, through a ring of kGemmStages shared-memory stages:
+//   1. every thread copies 16-byte pieces of a slice's 128 x 64 block of A and
+//      BN x 64 block of B into a stage with asynchronous copies (cp.async,
+//      zero-filled outside the matrix), arranged as the canonical no-swizzle
+//      K-major layout of 8-row x 16-byte core matrices (core matrices 128 B
+//      apart along K, 1 KB apart along M / N); the copies run kGemmStages - 1
+//      slices ahead of the tensor core;
+//   2. once a slice has landed, one elected thread issues four tcgen05.mma
+//      (K = 16 each) that accumulate into a 128-lane x BN-column FP32 tile in
+//      tensor memory, and tcgen05.commit arrives on the stage's mbarrier when
+//      they have completed;
+//   3. a stage is refilled only after its mbarrier shows that the MMAs reading
+//      it are done (bounded waits: after ~1 s a CTA records GEVO_ERR_TIMEOUT
+//      in the error word and stops issuing);
 //   4. the epilogue reads the accumulator with tcgen05.ld (warp w owns lanes
 //      32w..32w+31 = rows) and writes FP32 or BF16 with bias and ReLU.
 #include <cuda_bf16.h>
@@ -26,6 +30,7 @@ namespace gevo {
 
 constexpr int kGemmBM = 128;
 constexpr int kGemmBK = 64;
+constexpr int kGemmStages = 3;
 constexpr long long kWaitLimit = 1ll << 22;    // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -110,22 +115,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// 16-byte asynchronous global -> shared copy; a piece outside the matrix is
+// zero-filled (source size 0: nothing is read, the address given is the
+// matrix base).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Copies rows [row0, row0 + ROWS) x columns [k0, k0 + 64) of a K-major bf16
-// matrix into the core-matrix layout at `dst`, zero-filling outside the matrix.
+// matrix into the core-matrix layout at shared address `dst`, zero-filling
+// outside the matrix.
 template <int ROWS>
 __device__ __forceinline__ void stage_tile(const __nv_bfloat16* __restrict__ src, int ld, int nrows,
-                                           int K, int row0, int k0, unsigned char* dst)
+                                           int K, int row0, int k0, uint32_t dst)
 {
     constexpr int CHUNKS = ROWS * (kGemmBK / 8);      // 16-byte pieces
     for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x) {
         const int r = c / (kGemmBK / 8);
         const int kg = c % (kGemmBK / 8);
         const int gr = row0 + r, gk = k0 + kg * 8;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < nrows && gk < K)   // K is a multiple of 8, so a piece is all in or all out
-            v = *reinterpret_cast<const uint4*>(src + (size_t)gr * ld + gk);
+        // K is a multiple of 8, so a piece is all in or all out
+        const bool in = gr < nrows && gk < K;
         const int off = (r >> 3) * 1024 + kg * 128 + (r & 7) * 16;
-        *reinterpret_cast<uint4*>(dst + off) = v;
+        cp_async16(dst + off, in ? src + (size_t)gr * ld + gk : src, in);
     }
 }
 
@@ -138,27 +164,44 @@ struct ConvA {
     int H, W, C;
 };
 
-__device__ __forceinline__ void stage_conv_tile(const ConvA& cv, int M, int K, int row0, int k0,
-                                                unsigned char* dst)
+// Thread t stages the 16-byte pieces (row t / 8 + 16 j, column group t % 8),
+// j < 8, of every slice: the rows' (y, x) are decomposed once per CTA (yx[j] =
+// y << 16 | x, or -1 past the last row), and the slice's tap and channel once
+// per slice, so no integer division runs per piece.
+constexpr int kConvRowsPerThread = kGemmBM * (kGemmBK / 8) / 128;   // 8
+
+__device__ __forceinline__ void conv_rows(const ConvA& cv, int M, int row0, int yx[kConvRowsPerThread])
 {
-    constexpr int CHUNKS = kGemmBM * (kGemmBK / 8);
-    for (int c = threadIdx.x; c < CHUNKS; c += blockDim.x) {
-        const int r = c / (kGemmBK / 8);
-        const int kg = c % (kGemmBK / 8);
-        const int gr = row0 + r, gk = k0 + kg * 8;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < M && gk < K) {
-            const int tap = gk / cv.C, ch = gk - tap * cv.C;
-            const int x = gr % cv.W;
-            const int t = gr / cv.W;
-            const int y = t % cv.H, b = t / cv.H;
-            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-            if (yy >= 0 && yy < cv.H && xx >= 0 && xx < cv.W)
-                v = *reinterpret_cast<const uint4*>(
-                    cv.X + ((size_t)(b * cv.H + yy) * cv.W + xx) * cv.C + ch);
+#pragma unroll
+    for (int j = 0; j < kConvRowsPerThread; j++) {
+        const int gr = row0 + (int)(threadIdx.x >> 3) + 16 * j;
+        yx[j] = -1;
+        if (gr < M) {
+            const int x = gr % cv.W, y = (gr / cv.W) % cv.H;
+            yx[j] = (y << 16) | x;
         }
+    }
+}
+
+__device__ __forceinline__ void stage_conv_tile(const ConvA& cv, int K, int row0, int k0,
+                                                const int yx[kConvRowsPerThread], uint32_t dst)
+{
+    const int kg = threadIdx.x & 7;
+    const int gk = k0 + kg * 8;
+    const bool kin = gk < K;
+    const int tap = kin ? gk / cv.C : 0;
+    const int ch = gk - tap * cv.C;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    const ptrdiff_t shift = ((ptrdiff_t)dy * cv.W + dx) * cv.C + ch;
+#pragma unroll
+    for (int j = 0; j < kConvRowsPerThread; j++) {
+        const int r = (int)(threadIdx.x >> 3) + 16 * j;
+        const int y = yx[j] >> 16, x = yx[j] & 0xffff;
+        const bool in = kin && yx[j] >= 0 && (unsigned)(y + dy) < (unsigned)cv.H &&
+                        (unsigned)(x + dx) < (unsigned)cv.W;
+        const __nv_bfloat16* p = in ? cv.X + (ptrdiff_t)(row0 + r) * cv.C + shift : cv.X;
         const int off = (r >> 3) * 1024 + kg * 128 + (r & 7) * 16;
-        *reinterpret_cast<uint4*>(dst + off) = v;
+        cp_async16(dst + off, p, in);
     }
 }
 
@@ -170,19 +213,20 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
             uint32_t* __restrict__ err, int trans_c)
 {
     constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    constexpr int S = kGemmStages;
+    constexpr uint32_t A_BYTES = kGemmBM * kGemmBK * 2;         // 16 KB
+    constexpr uint32_t STAGE = (kGemmBM + BN) * kGemmBK * 2;    // A block, then B block
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;                                   // 128 x 64 bf16 = 16 KB
-    unsigned char* sB = smem + kGemmBM * kGemmBK * 2;           // BN x 64 bf16
-    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ __align__(8) unsigned long long s_mbar[S];
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * kGemmBM, col0 = blockIdx.y * BN;
-    const uint32_t mbar = smem_u32(&s_mbar);
     if (threadIdx.x == 0) {
         s_fail = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        for (int i = 0; i < S; i++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -197,50 +241,78 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
     constexpr uint32_t idesc = idesc_bf16(kGemmBM, BN);
-    const uint32_t aBase = smem_u32(sA), bBase = smem_u32(sB);
+    const uint32_t base = smem_u32(smem);
 
-    uint32_t phase = 0;
-    // split-K: CTA z of ksplit handles K chunks [kc0, kc1)
+    // split-K: CTA z of ksplit handles K slices [kc0, kc1)
     const int nk_all = (K + kGemmBK - 1) / kGemmBK;
     const int per = (nk_all + ksplit - 1) / ksplit;
     const int kc0 = min(nk_all, (int)blockIdx.z * per), kc1 = min(nk_all, kc0 + per);
-    for (int kc = kc0; kc < kc1; kc++) {
+    const int nk = kc1 - kc0;
+    int yx[kConvRowsPerThread];
+    if (CONV) conv_rows(cv, M, row0, yx);
+    auto load = [&](int i) {   // slice kc0 + i into stage i % S
+        const uint32_t st = base + (uint32_t)(i % S) * STAGE;
+        const int k0 = (kc0 + i) * kGemmBK;
         if (CONV)
-            stage_conv_tile(cv, M, K, row0, kc * kGemmBK, sA);
+            stage_conv_tile(cv, K, row0, k0, yx, st);
         else
-            stage_tile<kGemmBM>(A, lda, M, K, row0, kc * kGemmBK, sA);
-        stage_tile<BN>(B, ldb, N, K, col0, kc * kGemmBK, sB);
+            stage_tile<kGemmBM>(A, lda, M, K, row0, k0, st);
+        stage_tile<BN>(B, ldb, N, K, col0, k0, st + A_BYTES);
+    };
+    // the copies run S - 1 slices ahead; every iteration commits one group
+    // (possibly empty) so that group i always holds slice i
+#pragma unroll
+    for (int i = 0; i < S - 1; i++) {
+        if (i < nk) load(i);
+        cp_async_commit();
+    }
+    int issued = 0;
+    for (int i = 0; i < nk; i++) {
+        cp_async_wait<S - 2>();                       // slice i has landed
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (threadIdx.x == 0 && !s_fail) {
+        if (s_fail) break;
+        const int s = i % S;
+        if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t aBase = base + (uint32_t)s * STAGE, bBase = aBase + A_BYTES;
 #pragma unroll
             for (int k16 = 0; k16 < kGemmBK / 16; k16++) {
                 const uint64_t da = smem_desc(aBase + k16 * 256, 128, 1024);
                 const uint64_t db = smem_desc(bBase + k16 * 256, 128, 1024);
-                mma_bf16(tmem, da, db, idesc, (kc > kc0 || k16 > 0) ? 1u : 0u);
+                mma_bf16(tmem, da, db, idesc, (i > 0 || k16 > 0) ? 1u : 0u);
             }
-            mma_commit(mbar);
+            mma_commit(smem_u32(&s_mbar[s]));
         }
-        // every thread waits for the MMAs to finish reading shared memory
-        if (!s_fail) {
-            if (!mbar_wait(mbar, phase)) {
+        issued = i + 1;
+        const int j = i + S - 1;
+        if (j < nk) {
+            const int sj = j % S;
+            // stage sj was last read by the MMAs of slice j - S (its use (j - S) / S)
+            bool ok = true;
+            if (j >= S) ok = mbar_wait(smem_u32(&s_mbar[sj]), (uint32_t)((j - S) / S) & 1u);
+            if (ok) {
+                load(j);
+            } else {
                 s_fail = 1;
                 atomicOr(err, kErrTimeout);
             }
         }
-        phase ^= 1u;
-        __syncthreads();
-        if (s_fail) break;
+        cp_async_commit();
     }
-    if (s_fail) {
-        // give MMAs that may still be in flight a second bounded chance to land
-        // before the accumulator's tensor memory is released
-        mbar_wait(mbar, phase ^ 1u);
+    cp_async_wait<0>();
+    // the last commit arrives once every MMA issued before it has completed
+    if (issued > 0) {
+        const int last = issued - 1;
+        if (!mbar_wait(smem_u32(&s_mbar[last % S]), (uint32_t)(last / S) & 1u)) {
+            s_fail = 1;
+            atomicOr(err, kErrTimeout);
+        }
     }
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    if (!s_fail && kc1 > kc0) {
+    if (!s_fail && nk > 0) {
         // epilogue: warp w reads accumulator lanes (rows) 32w .. 32w + 31
         const int r = row0 + warp * 32 + lane;
 #pragma unroll 1
@@ -291,7 +363,7 @@ static gevo_status launch_gemm(int M, int N, int K, const __nv_bfloat16* A, int 
                                const float* bias, int relu, float beta, int ksplit, uint32_t* err,
                                cudaStream_t st, int trans_c)
 {
-    const size_t smem = (size_t)(kGemmBM + BN) * kGemmBK * 2;
+    const size_t smem = (size_t)kGemmStages * (kGemmBM + BN) * kGemmBK * 2;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_gemm_bf16<BN, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -92,23 +92,33 @@ k_colT(int nb, int H, int W, int C, const bf16* __restrict__ X, size_t p0, size_
     // one block: 64 pixels x one tap; 16-byte (8-channel) loads of the shifted
     // neighbour rows into shared memory, then rows of 64 pixels per channel out
     __shared__ __align__(16) bf16 s_t[64][200];
+    __shared__ int s_yx[64];   // y << 16 | x of the block's pixels (-1 past the end)
     const int tap = blockIdx.y;
     const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     const size_t q0 = (size_t)blockIdx.x * 64;
     const int C8 = C / 8;
+    // pixel indices fit in 32 bits (the entry point checks nb H W < 2^31): the
+    // pixel decomposition runs once per pixel, not once per 16-byte piece
+    if (threadIdx.x < 64) {
+        const size_t q = q0 + threadIdx.x;
+        int v = -1;
+        if (q < np) {
+            const int p = (int)(p0 + q);
+            v = (((p / W) % H) << 16) | (p % W);
+        }
+        s_yx[threadIdx.x] = v;
+    }
+    __syncthreads();
     for (int i = threadIdx.x; i < 64 * C8; i += blockDim.x) {
         const int r = i / C8, c8 = i - r * C8;
-        const size_t q = q0 + r;
+        const int yx = s_yx[r];
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (q < np) {
-            const size_t p = p0 + q;
-            const int x = (int)(p % W);
-            const size_t t = p / W;
-            const int y = (int)(t % H);
-            const size_t b = t / H;
-            const int yy = y + dy, xx = x + dx;
-            if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                v = *reinterpret_cast<const uint4*>(X + ((b * H + yy) * W + xx) * C + 8 * c8);
+        if (yx >= 0) {
+            const int y = yx >> 16, x = yx & 0xffff;
+            if ((unsigned)(y + dy) < (unsigned)H && (unsigned)(x + dx) < (unsigned)W) {
+                const int p = (int)(p0 + q0) + r + dy * W + dx;   // the neighbour pixel
+                v = *reinterpret_cast<const uint4*>(X + (size_t)p * C + 8 * c8);
+            }
         }
         *reinterpret_cast<uint4*>(&s_t[r][8 * c8]) = v;
     }
@@ -353,6 +363,13 @@ using namespace gevo;
 #define GEVO_LAUNCHED() \
     do { GEVO_CHECK_LAUNCH(); return GEVO_OK; } while (0)
 
+// The convolution kernels keep a pixel's (y, x) as y << 16 | x and pixel
+// indices in 32 bits.
+static bool conv_sizes_ok(int32_t nb, int32_t H, int32_t W)
+{
+    return H < 32768 && W < 65536 && (int64_t)nb * H * W < ((int64_t)1 << 31);
+}
+
 extern "C" {
 
 gevo_status gevo_conv3x3(int32_t nb, int32_t H, int32_t W, int32_t Cin, const void* X, int32_t Cout,
@@ -360,7 +377,8 @@ gevo_status gevo_conv3x3(int32_t nb, int32_t H, int32_t W, int32_t Cin, const vo
                          int32_t relu, float beta, void* workspace, void* stream)
 {
     if (nb <= 0 || H <= 0 || W <= 0 || Cin <= 0 || Cin % 8 || Cout <= 0 || !X || !Wt || !Y ||
-        !workspace || ldy < Cout || !gevo_aligned(X, 16) || !gevo_aligned(Wt, 16))
+        !workspace || ldy < Cout || !gevo_aligned(X, 16) || !gevo_aligned(Wt, 16) ||
+        !conv_sizes_ok(nb, H, W))
         return GEVO_ERR_INVALID;
     return conv3x3_bf16(nb, H, W, Cin, X, Cout, Wt, Y, ldy, out_bf16, bias, relu, beta,
                         reinterpret_cast<uint32_t*>(workspace), (cudaStream_t)stream);
@@ -372,7 +390,7 @@ gevo_status gevo_conv3x3_wgrad(int32_t nb, int32_t H, int32_t W, int32_t Cin, co
 {
     if (nb <= 0 || H <= 0 || W <= 0 || Cin <= 0 || Cin % 8 || Cout <= 0 || Cout % 8 || !X ||
         !dZt || !colT || !dWt || !workspace || colT_pixels < 64 || Cin > 192 ||
-        ((int64_t)nb * H * W) % 8)
+        ((int64_t)nb * H * W) % 8 || !conv_sizes_ok(nb, H, W))
         return GEVO_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t* err = reinterpret_cast<uint32_t*>(workspace);
