@@ -39,14 +39,15 @@ gevo_status gevo_conv3x3(int32_t nb, int32_t H, int32_t W, int32_t Cin, const vo
                          void* stream);
 
 /* Weight gradient dWt[co][(tap, ci)] = sum_p dZ[p][co] col(X)[p][(tap, ci)]
- * (Wt's own layout; FP32, written).  dZt: dZ transposed,
- * [Cout][nb*H*W] BF16.  colT: caller scratch of 9*Cin*colT_pixels BF16 that
- * holds one chunk of the pixel-contiguous im2col at a time; the contraction
- * over pixels is split across CTAs and summed with FP32 atomics.  Sizes as
- * for gevo_conv3x3. */
+ * (Wt's own layout; FP32, written).  dZt: dZ transposed, [Cout][nb*H*W] BF16
+ * (nb*H*W a multiple of 8).  An implicit GEMM (rows = 9*Cin taps x channels,
+ * columns = Cout, depth = pixels) whose A tiles are gathered from X's shifted
+ * pixels straight into shared memory, with no im2col in memory; the
+ * contraction over pixels is split across CTAs and summed with FP32 atomics.
+ * Cin % 8 == 0, Cout % 8 == 0; sizes as for gevo_conv3x3. */
 gevo_status gevo_conv3x3_wgrad(int32_t nb, int32_t H, int32_t W, int32_t Cin, const void* X,
-                               int32_t Cout, const void* dZt, void* colT, int64_t colT_pixels,
-                               float* dWt, void* workspace, void* stream);
+                               int32_t Cout, const void* dZt, float* dWt, void* workspace,
+                               void* stream);
 
 /* dZ = dY * [Y > 0] (BF16 [P][C]); dZt = its transpose (BF16 [C][P], may be NULL);
  * db += sum over pixels of dZ (FP32 [C]).  C <= 128. */

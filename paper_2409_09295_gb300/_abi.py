@@ -94,7 +94,7 @@ EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin
 # (i: int32, u: uint32, I: int64, f: float, p: pointer; the last p is the stream).
 PRIOR = {
     "gevo_conv3x3": "iiiipipppiiifpp",
-    "gevo_conv3x3_wgrad": "iiiipippIppp",
+    "gevo_conv3x3_wgrad": "iiiipipppp",
     "gevo_relu_bwd": "Iipipipppp",
     "gevo_maxpool2": "iiiipipp",
     "gevo_maxpool2_bwd": "iiiipippifp",

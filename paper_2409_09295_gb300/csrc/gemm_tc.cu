@@ -205,7 +205,64 @@ __device__ __forceinline__ void stage_conv_tile(const ConvA& cv, int K, int row0
     }
 }
 
-template <int BN, bool CONV>
+// Weight-gradient operand without a materialised im2col: rows m = (tap, ci)
+// (m = tap Cin + ci, tap = 3 ky + kx), depth k = pixel p, element
+// X[p + (ky - 1) W + (kx - 1)][ci] (zero outside the image).  A 16-byte piece
+// of X (8 channels of one pixel) is a column of 8 rows of one core matrix, so it
+// is scattered as 8 two-byte stores.  Thread t takes pixel column t % 64 and
+// row groups t / 64 + 2 j, j < 8; the rows' (tap, ci) are decomposed once per
+// CTA (wr[j] = tap << 16 | ci, or -1 past the last row), the pixel once per
+// slice.
+__device__ __forceinline__ void wgrad_rows(const ConvA& cv, int M, int row0, int wr[8])
+{
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int m = row0 + 8 * ((int)(threadIdx.x >> 6) + 2 * j);
+        wr[j] = -1;
+        if (m < M) {
+            const int tap = m / cv.C;
+            wr[j] = (tap << 16) | (m - tap * cv.C);
+        }
+    }
+}
+
+__device__ __forceinline__ void stage_wgrad_tile(const ConvA& cv, int P, int k0, const int wr[8],
+                                                 unsigned char* dst)
+{
+    const int kk = threadIdx.x & 63;
+    const int p = k0 + kk;
+    int y = -1, x = 0;
+    if (p < P) {
+        x = p % cv.W;
+        y = (p / cv.W) % cv.H;
+    }
+    unsigned char* col = dst + (kk >> 3) * 128 + (kk & 7) * 2;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int g = (int)(threadIdx.x >> 6) + 2 * j;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (wr[j] >= 0 && y >= 0) {
+            const int tap = wr[j] >> 16, ci = wr[j] & 0xffff;
+            const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+            if ((unsigned)(y + dy) < (unsigned)cv.H && (unsigned)(x + dx) < (unsigned)cv.W)
+                v = *reinterpret_cast<const uint4*>(cv.X + ((size_t)p + dy * cv.W + dx) * cv.C + ci);
+        }
+        unsigned char* d = col + g * 1024;
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            *reinterpret_cast<uint16_t*>(d + (2 * i) * 16) = (uint16_t)(w[i] & 0xffffu);
+            *reinterpret_cast<uint16_t*>(d + (2 * i + 1) * 16) = (uint16_t)(w[i] >> 16);
+        }
+    }
+}
+
+// Operand modes of k_gemm_bf16.
+constexpr int kModePlain = 0;   // A a K-major matrix
+constexpr int kModeConv = 1;    // A the implicit im2col of a 3x3 convolution
+constexpr int kModeWgrad = 2;   // A the implicit transposed im2col (weight gradient)
+
+template <int BN, int MODE>
 __global__ void __launch_bounds__(128)
 k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, ConvA cv,
             const __nv_bfloat16* __restrict__ B, int ldb, void* __restrict__ C, int ldc,
@@ -249,12 +306,15 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
     const int kc0 = min(nk_all, (int)blockIdx.z * per), kc1 = min(nk_all, kc0 + per);
     const int nk = kc1 - kc0;
     int yx[kConvRowsPerThread];
-    if (CONV) conv_rows(cv, M, row0, yx);
+    if (MODE == kModeConv) conv_rows(cv, M, row0, yx);
+    if (MODE == kModeWgrad) wgrad_rows(cv, M, row0, yx);
     auto load = [&](int i) {   // slice kc0 + i into stage i % S
         const uint32_t st = base + (uint32_t)(i % S) * STAGE;
         const int k0 = (kc0 + i) * kGemmBK;
-        if (CONV)
+        if (MODE == kModeConv)
             stage_conv_tile(cv, K, row0, k0, yx, st);
+        else if (MODE == kModeWgrad)
+            stage_wgrad_tile(cv, K, k0, yx, smem + (size_t)(i % S) * STAGE);
         else
             stage_tile<kGemmBM>(A, lda, M, K, row0, k0, st);
         stage_tile<BN>(B, ldb, N, K, col0, k0, st + A_BYTES);
@@ -357,7 +417,7 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
                      : "memory");
 }
 
-template <int BN, bool CONV>
+template <int BN, int MODE>
 static gevo_status launch_gemm(int M, int N, int K, const __nv_bfloat16* A, int lda, ConvA cv,
                                const __nv_bfloat16* B, int ldb, void* C, int ldc, int out_bf16,
                                const float* bias, int relu, float beta, int ksplit, uint32_t* err,
@@ -366,28 +426,28 @@ static gevo_status launch_gemm(int M, int N, int K, const __nv_bfloat16* A, int 
     const size_t smem = (size_t)kGemmStages * (kGemmBM + BN) * kGemmBK * 2;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_gemm_bf16<BN, CONV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_gemm_bf16<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         attr = true;
     }
     dim3 grid((M + kGemmBM - 1) / kGemmBM, (N + BN - 1) / BN, ksplit);
-    k_gemm_bf16<BN, CONV><<<grid, 128, smem, st>>>(M, N, K, A, lda, cv, B, ldb, C, ldc, out_bf16,
+    k_gemm_bf16<BN, MODE><<<grid, 128, smem, st>>>(M, N, K, A, lda, cv, B, ldb, C, ldc, out_bf16,
                                                    bias, relu, beta, ksplit, err, trans_c);
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }
 
-template <bool CONV>
+template <int MODE>
 static gevo_status gemm_dispatch(int M, int N, int K, const __nv_bfloat16* a, int lda, ConvA cv,
                                  const __nv_bfloat16* b, int ldb, void* C, int ldc, int out_bf16,
                                  const float* bias, int relu, float beta, int ksplit,
                                  uint32_t* err, cudaStream_t st, int trans_c = 0)
 {
-    if (N <= 16) return launch_gemm<16, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
-    if (N <= 32) return launch_gemm<32, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
-    if (N <= 64) return launch_gemm<64, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
-    if (N <= 128) return launch_gemm<128, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
-    return launch_gemm<256, CONV>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    if (N <= 16) return launch_gemm<16, MODE>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    if (N <= 32) return launch_gemm<32, MODE>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    if (N <= 64) return launch_gemm<64, MODE>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    if (N <= 128) return launch_gemm<128, MODE>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
+    return launch_gemm<256, MODE>(M, N, K, a, lda, cv, b, ldb, C, ldc, out_bf16, bias, relu, beta, ksplit, err, st, trans_c);
 }
 
 gevo_status gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, void* C,
@@ -396,7 +456,7 @@ gevo_status gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B
 {
     if (trans_c && ksplit <= 1) return GEVO_ERR_INVALID;   // transposed store: split-K path only
     ConvA cv{nullptr, 0, 0, 0};
-    return gemm_dispatch<false>(M, N, K, reinterpret_cast<const __nv_bfloat16*>(A), lda, cv,
+    return gemm_dispatch<kModePlain>(M, N, K, reinterpret_cast<const __nv_bfloat16*>(A), lda, cv,
                                 reinterpret_cast<const __nv_bfloat16*>(B), ldb, C, ldc, out_bf16,
                                 bias, relu, beta, ksplit, err, st, trans_c);
 }
@@ -406,9 +466,22 @@ gevo_status conv3x3_bf16(int nb, int H, int W, int Cin, const void* X, int Cout,
                          uint32_t* err, cudaStream_t st)
 {
     ConvA cv{reinterpret_cast<const __nv_bfloat16*>(X), H, W, Cin};
-    return gemm_dispatch<true>(nb * H * W, Cout, 9 * Cin, nullptr, 0, cv,
+    return gemm_dispatch<kModeConv>(nb * H * W, Cout, 9 * Cin, nullptr, 0, cv,
                                reinterpret_cast<const __nv_bfloat16*>(Wt), 9 * Cin, Y, ldy,
                                out_bf16, bias, relu, beta, 1, err, st);
+}
+
+// dWt[co][(tap, ci)] = sum_p dZt[co][p] X[p + shift(tap)][ci]: rows 9 Cin, columns
+// Cout, depth P pixels, split over ksplit CTAs and summed with FP32 atomics into
+// the transposed (Wt-layout) result, which the caller zeroes.
+gevo_status conv3x3_wgrad_bf16(int nb, int H, int W, int Cin, const void* X, int Cout,
+                               const void* dZt, float* dWt, int ksplit, uint32_t* err,
+                               cudaStream_t st)
+{
+    ConvA cv{reinterpret_cast<const __nv_bfloat16*>(X), H, W, Cin};
+    return gemm_dispatch<kModeWgrad>(9 * Cin, Cout, nb * H * W, nullptr, 0, cv,
+                                     reinterpret_cast<const __nv_bfloat16*>(dZt), nb * H * W, dWt,
+                                     9 * Cin, 0, nullptr, 0, 1.f, ksplit, err, st, 1);
 }
 
 }  // namespace gevo

@@ -19,6 +19,9 @@ gevo_status gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B
 gevo_status conv3x3_bf16(int nb, int H, int W, int Cin, const void* X, int Cout, const void* Wt,
                          void* Y, int ldy, int out_bf16, const float* bias, int relu, float beta,
                          uint32_t* err, cudaStream_t st);
+gevo_status conv3x3_wgrad_bf16(int nb, int H, int W, int Cin, const void* X, int Cout,
+                               const void* dZt, float* dWt, int ksplit, uint32_t* err,
+                               cudaStream_t st);
 
 using bf16 = __nv_bfloat16;
 
@@ -51,10 +54,7 @@ k_relu_bwd(size_t P, int C, const float* __restrict__ dY, int lddy, const bf16* 
            int ldy, bf16* __restrict__ dZ, bf16* __restrict__ dZt, float* __restrict__ db)
 {
     __shared__ float s_t[64][129];
-    __shared__ float s_db[128];
     const size_t p0 = (size_t)blockIdx.x * 64;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) s_db[c] = 0.f;
-    __syncthreads();
     for (int i = threadIdx.x; i < 64 * C; i += blockDim.x) {
         const int r = i / C, c = i - r * C;
         const size_t p = p0 + r;
@@ -80,64 +80,6 @@ k_relu_bwd(size_t P, int C, const float* __restrict__ dY, int lddy, const bf16* 
             if (p < P) dZt[(size_t)c * P + p] = __float2bfloat16_rn(s_t[r][c]);
         }
     }
-}
-
-// colT[(tap, c)][p - p0] = X[neighbour(p, tap)][c] (zero outside), the K-major
-// (pixel-contiguous) im2col used as the A operand of the weight gradient.
-// Block = 64 pixels x C channels of one tap.
-__global__ void __launch_bounds__(256)
-k_colT(int nb, int H, int W, int C, const bf16* __restrict__ X, size_t p0, size_t np,
-       bf16* __restrict__ colT)
-{
-    // one block: 64 pixels x one tap; 16-byte (8-channel) loads of the shifted
-    // neighbour rows into shared memory, then rows of 64 pixels per channel out
-    __shared__ __align__(16) bf16 s_t[64][200];
-    __shared__ int s_yx[64];   // y << 16 | x of the block's pixels (-1 past the end)
-    const int tap = blockIdx.y;
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    const size_t q0 = (size_t)blockIdx.x * 64;
-    const int C8 = C / 8;
-    // pixel indices fit in 32 bits (the entry point checks nb H W < 2^31): the
-    // pixel decomposition runs once per pixel, not once per 16-byte piece
-    if (threadIdx.x < 64) {
-        const size_t q = q0 + threadIdx.x;
-        int v = -1;
-        if (q < np) {
-            const int p = (int)(p0 + q);
-            v = (((p / W) % H) << 16) | (p % W);
-        }
-        s_yx[threadIdx.x] = v;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * C8; i += blockDim.x) {
-        const int r = i / C8, c8 = i - r * C8;
-        const int yx = s_yx[r];
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (yx >= 0) {
-            const int y = yx >> 16, x = yx & 0xffff;
-            if ((unsigned)(y + dy) < (unsigned)H && (unsigned)(x + dx) < (unsigned)W) {
-                const int p = (int)(p0 + q0) + r + dy * W + dx;   // the neighbour pixel
-                v = *reinterpret_cast<const uint4*>(X + (size_t)p * C + 8 * c8);
-            }
-        }
-        *reinterpret_cast<uint4*>(&s_t[r][8 * c8]) = v;
-    }
-    __syncthreads();
-    // two pixels per thread and store: 4-byte writes along each channel's row
-    for (int i = threadIdx.x; i < 32 * C; i += blockDim.x) {
-        const int c = i / 32, r = 2 * (i - c * 32);
-        const size_t q = q0 + r;
-        bf16* dst = colT + ((size_t)tap * C + c) * np + q;
-        if (q + 1 < np) {
-            __nv_bfloat162 pr;
-            pr.x = s_t[r][c];
-            pr.y = s_t[r + 1][c];
-            *reinterpret_cast<__nv_bfloat162*>(dst) = pr;
-        } else if (q < np) {
-            *dst = s_t[r][c];
-        }
-    }
-    (void)nb;
 }
 
 // 2x2 max pool, NHWC; X rows have stride ldx (a channel slice of a wider buffer)
@@ -385,43 +327,27 @@ gevo_status gevo_conv3x3(int32_t nb, int32_t H, int32_t W, int32_t Cin, const vo
 }
 
 gevo_status gevo_conv3x3_wgrad(int32_t nb, int32_t H, int32_t W, int32_t Cin, const void* X,
-                               int32_t Cout, const void* dZt, void* colT, int64_t colT_pixels,
-                               float* dWt, void* workspace, void* stream)
+                               int32_t Cout, const void* dZt, float* dWt, void* workspace,
+                               void* stream)
 {
     if (nb <= 0 || H <= 0 || W <= 0 || Cin <= 0 || Cin % 8 || Cout <= 0 || Cout % 8 || !X ||
-        !dZt || !colT || !dWt || !workspace || colT_pixels < 64 || Cin > 192 ||
-        ((int64_t)nb * H * W) % 8 || !conv_sizes_ok(nb, H, W))
+        !dZt || !dWt || !workspace || ((int64_t)nb * H * W) % 8 || !conv_sizes_ok(nb, H, W) ||
+        !gevo_aligned(X, 16) || !gevo_aligned(dZt, 16))
         return GEVO_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t* err = reinterpret_cast<uint32_t*>(workspace);
     const size_t P = (size_t)nb * H * W;
     const int K9 = 9 * Cin;
-    // chunks of at most colT_pixels pixels (a multiple of 64); dW accumulates
-    const size_t chunk = (size_t)(colT_pixels / 64) * 64;
     if (cudaMemsetAsync(dWt, 0, sizeof(float) * (size_t)K9 * Cout, st) != cudaSuccess)
         return GEVO_ERR_CUDA;
-    for (size_t p0 = 0; p0 < P; p0 += chunk) {
-        const size_t np = std::min(chunk, P - p0);
-        if (np % 8) return GEVO_ERR_INVALID;   // K-major rows must stay 16-byte aligned
-        dim3 g((unsigned)((np + 63) / 64), 9);
-        k_colT<<<g, 256, 0, st>>>(nb, H, W, Cin, reinterpret_cast<const bf16*>(X), p0, np,
-                                  reinterpret_cast<bf16*>(colT));
-        GEVO_CHECK_LAUNCH();
-        // dW[co][(tap, ci)] += sum_p colT[(tap, ci)][p] dZ^T[co][p] over the chunk:
-        // rows of the product are the 9 Cin taps x channels (many: full 128-row
-        // MMA tiles), columns the Cout output channels, stored transposed into
-        // dW's [Cout][9 Cin] layout; dZ^T rows are P long, so the chunk is the
-        // column window [p0, p0 + np).  Enough K slices for about eight CTAs per
-        // SM, each at least 512 pixels long.
-        const size_t mtiles = ((size_t)K9 + 127) / 128;
-        const size_t want = ((size_t)sm_count() * 8 + mtiles - 1) / mtiles;
-        const int ksplit = (int)std::max<size_t>(2, std::min<size_t>(np / 512, want));
-        gevo_status s = gemm_bf16(K9, Cout, (int)np, colT, (int)np,
-                                  reinterpret_cast<const bf16*>(dZt) + p0, (int)P, dWt, K9, 0,
-                                  nullptr, 0, 1.f, ksplit, err, st, 1);
-        if (s != GEVO_OK) return s;
-    }
-    return GEVO_OK;
+    // rows of the product are the 9 Cin taps x channels (many: full 128-row MMA
+    // tiles), columns the Cout output channels, stored transposed into dW's
+    // [Cout][9 Cin] layout; the pixels are split into enough K ranges for about
+    // eight CTAs per SM, each at least 512 pixels long
+    const size_t mtiles = ((size_t)K9 + 127) / 128;
+    const size_t want = ((size_t)sm_count() * 8 + mtiles - 1) / mtiles;
+    const int ksplit = (int)std::max<size_t>(2, std::min<size_t>(P / 512, want));
+    return conv3x3_wgrad_bf16(nb, H, W, Cin, X, Cout, dZt, dWt, ksplit, err, st);
 }
 
 gevo_status gevo_relu_bwd(int64_t P, int32_t C, const float* dY, int32_t lddy, const void* Y,

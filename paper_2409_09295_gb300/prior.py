@@ -31,7 +31,7 @@ def _ptr(t: torch.Tensor, offset_elems: int = 0):
 
 class DepthUNet:
     def __init__(self, nb: int, H: int, W: int, chans=(16, 32, 64, 128), device="cuda",
-                 seed: int = 0, colT_bytes: int = 512 << 20):
+                 seed: int = 0):
         L = len(chans)
         assert H % (1 << (L - 1)) == 0 and W % (1 << (L - 1)) == 0
         assert all(c % 8 == 0 for c in chans) and chans[0] <= 16
@@ -78,7 +78,6 @@ class DepthUNet:
         zmax = max(self.P[i] * chans[i] for i in range(L))
         self.dZ = torch.zeros(zmax, dtype=BF16, device=d)
         self.dZt = torch.zeros(zmax, dtype=BF16, device=d)
-        self.colT = torch.zeros(colT_bytes // 2, dtype=BF16, device=d)
         self.ws = torch.zeros(256, dtype=torch.uint8, device=d)
         self.step_count = 0
 
@@ -147,9 +146,8 @@ class DepthUNet:
         cin, cout = lay["cin"], lay["cout"]
         _abi.prior_call("gevo_relu_bwd", P, cout, _ptr(dY, dy_off), lddy, _ptr(Y, y_off), ldy,
                         self.dZ, self.dZt, lay["db"])
-        chunk = max(64, (self.colT.numel() // (9 * cin)) // 64 * 64)
-        _abi.prior_call("gevo_conv3x3_wgrad", nb, h, w, cin, Xin, cout, self.dZt, self.colT,
-                        chunk, lay["dW"], self.ws)
+        _abi.prior_call("gevo_conv3x3_wgrad", nb, h, w, cin, Xin, cout, self.dZt, lay["dW"],
+                        self.ws)
         if need_dx:
             _abi.prior_call("gevo_conv3x3", nb, h, w, cout, self.dZ, cin, lay["Wf16"], None,
                             dX, lddx, 0, 0, 0.0, self.ws)

@@ -2,8 +2,8 @@
 
   python -m paper_2409_09295_gb300.profile_cases render   # 4 views x 640x480 of
       the 500k-Gaussian room scene: two full forward + L1 + backward steps
-  python -m paper_2409_09295_gb300.profile_cases prior    # two depth-prior train
-      steps at batch 8 x 320x240
+  python -m paper_2409_09295_gb300.profile_cases prior [B] # two depth-prior train
+      steps at batch B (default 8) x 320x240; the bench line's step is B = 32
 
 Each case holds well under 1 GB on the device while its inputs exceed the
 129 MB L2, so DRAM counters stay meaningful and an ncu capture of one launch
@@ -35,12 +35,12 @@ def render_case():
     print("render case ok, duplicates", rep.n_dup, "evals fwd", e_fwd, "bwd", e_bwd)
 
 
-def prior_case():
+def prior_case(nb=8):
     from .prior import DepthUNet
-    net = DepthUNet(8, 240, 320, seed=1, colT_bytes=256 << 20)
+    net = DepthUNet(nb, 240, 320, seed=1)   # the bench line's scratch size
     rs = np.random.default_rng(0)
-    rgb = torch.from_numpy(rs.uniform(size=(8, 3, 240, 320)).astype(np.float32)).cuda()
-    tar = torch.from_numpy(rs.normal(1.0, 0.3, size=8 * 240 * 320).astype(np.float32)).cuda()
+    rgb = torch.from_numpy(rs.uniform(size=(nb, 3, 240, 320)).astype(np.float32)).cuda()
+    tar = torch.from_numpy(rs.normal(1.0, 0.3, size=nb * 240 * 320).astype(np.float32)).cuda()
     for _ in range(2):
         net.train_step(rgb, tar, torch.ones_like(tar))
     torch.cuda.synchronize()
@@ -49,4 +49,8 @@ def prior_case():
 
 if __name__ == "__main__":
     torch.cuda.set_device(0)
-    {"render": render_case, "prior": prior_case}[sys.argv[1] if len(sys.argv) > 1 else "render"]()
+    case = sys.argv[1] if len(sys.argv) > 1 else "render"
+    if case == "prior":
+        prior_case(int(sys.argv[2]) if len(sys.argv) > 2 else 8)
+    else:
+        render_case()

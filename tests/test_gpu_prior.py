@@ -24,7 +24,7 @@ def _bf(x):
 
 
 def _case(nb, H, W, chans, seed):
-    net = DepthUNet(nb, H, W, chans, seed=seed, colT_bytes=8 << 20)
+    net = DepthUNet(nb, H, W, chans, seed=seed)
     rs = np.random.default_rng(seed + 1)
     rgb = rs.uniform(size=(nb, 3, H, W)).astype(np.float32)
     target = rs.normal(1.0, 0.3, size=nb * H * W).astype(np.float32)
@@ -69,7 +69,7 @@ def test_prior_forward_and_gradients_match_oracle(nb, H, W, chans):
 
 def test_prior_training_reduces_loss():
     nb, H, W = 4, 32, 32
-    net = DepthUNet(nb, H, W, (16, 32, 64), seed=3, colT_bytes=16 << 20)
+    net = DepthUNet(nb, H, W, (16, 32, 64), seed=3)
     rs = np.random.default_rng(5)
     # a learnable synthetic mapping: log-depth = 1 + brightness of the image
     rgb = rs.uniform(size=(nb, 3, H, W)).astype(np.float32)
