@@ -375,11 +375,60 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
     if (!s_fail && nk > 0) {
         // epilogue: warp w reads accumulator lanes (rows) 32w .. 32w + 31
         const int r = row0 + warp * 32 + lane;
+        // whole 16-column groups of a row are stored as 16-byte vectors when the
+        // rows keep 16-byte alignment
+        const bool vec_ok = ((uintptr_t)C % 16 == 0) && (ldc % (out_bf16 ? 8 : 4) == 0);
 #pragma unroll 1
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
             tmem_ld16<16>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (r < M) {
+            if (r < M && ksplit <= 1 && col0 + c0 + 16 <= N && vec_ok) {
+                // 16 whole columns of this row: bias, beta, ReLU, then 16-byte
+                // stores (one row's 16 values are contiguous)
+                const int cb = col0 + c0;
+#pragma unroll
+                for (int i = 0; i < 16; i++)
+                    if (bias) v[i] += bias[cb + i];
+                if (out_bf16) {
+                    uint4* o = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(C) +
+                                                        (size_t)r * ldc + cb);
+                    uint32_t w[8];
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const uint4 old = beta != 0.f ? o[h] : make_uint4(0u, 0u, 0u, 0u);
+                        const uint32_t ow[4] = {old.x, old.y, old.z, old.w};
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            float x0 = v[8 * h + 2 * q], x1 = v[8 * h + 2 * q + 1];
+                            if (beta != 0.f) {
+                                x0 += beta * __uint_as_float(ow[q] << 16);
+                                x1 += beta * __uint_as_float(ow[q] & 0xffff0000u);
+                            }
+                            if (relu) { x0 = fmaxf(x0, 0.f); x1 = fmaxf(x1, 0.f); }
+                            const __nv_bfloat162 pr = __floats2bfloat162_rn(x0, x1);
+                            w[4 * h + q] = *reinterpret_cast<const uint32_t*>(&pr);
+                        }
+                    }
+                    o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                } else {
+                    float4* o = reinterpret_cast<float4*>(reinterpret_cast<float*>(C) + (size_t)r * ldc + cb);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        float4 x = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        if (beta != 0.f) {
+                            const float4 old = o[q];
+                            x.x += beta * old.x; x.y += beta * old.y;
+                            x.z += beta * old.z; x.w += beta * old.w;
+                        }
+                        if (relu) {
+                            x.x = fmaxf(x.x, 0.f); x.y = fmaxf(x.y, 0.f);
+                            x.z = fmaxf(x.z, 0.f); x.w = fmaxf(x.w, 0.f);
+                        }
+                        o[q] = x;
+                    }
+                }
+            } else if (r < M) {
 #pragma unroll
                 for (int i = 0; i < 16; i++) {
                     const int c = col0 + c0 + i;

@@ -49,22 +49,52 @@ __global__ void k_rgb_pack(size_t P, int HW, const float* __restrict__ rgb, bf16
 // dZ = dY * [Y > 0] for a ReLU layer: writes dZ (BF16, [P][C]) and dZ^T (BF16,
 // [C][P], the K-major operand of the weight gradient) and adds the bias
 // gradient sum_p dZ into db.  Block = 64 pixels x C channels through shared memory.
+// vec: C, ldy a multiple of 8, lddy of 4, all three arrays 16-byte aligned --
+// 8 channels of a pixel move as one 16-byte piece of Y and dZ and two of dY.
 __global__ void __launch_bounds__(256)
 k_relu_bwd(size_t P, int C, const float* __restrict__ dY, int lddy, const bf16* __restrict__ Y,
-           int ldy, bf16* __restrict__ dZ, bf16* __restrict__ dZt, float* __restrict__ db)
+           int ldy, bf16* __restrict__ dZ, bf16* __restrict__ dZt, float* __restrict__ db, int vec)
 {
     __shared__ float s_t[64][129];
     const size_t p0 = (size_t)blockIdx.x * 64;
-    for (int i = threadIdx.x; i < 64 * C; i += blockDim.x) {
-        const int r = i / C, c = i - r * C;
-        const size_t p = p0 + r;
-        float z = 0.f;
-        if (p < P) {
-            const float y = __bfloat162float(Y[p * ldy + c]);
-            z = y > 0.f ? dY[p * lddy + c] : 0.f;
-            dZ[p * C + c] = __float2bfloat16_rn(z);
+    if (vec) {
+        const int C8 = C / 8;
+        for (int i = threadIdx.x; i < 64 * C8; i += blockDim.x) {
+            const int r = i / C8, c = 8 * (i - r * C8);
+            const size_t p = p0 + r;
+            float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (p < P) {
+                const uint4 y = *reinterpret_cast<const uint4*>(Y + p * ldy + c);
+                const float4 g0 = *reinterpret_cast<const float4*>(dY + p * lddy + c);
+                const float4 g1 = *reinterpret_cast<const float4*>(dY + p * lddy + c + 4);
+                const uint32_t yw[4] = {y.x, y.y, y.z, y.w};
+                const float g[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                uint32_t o[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    // bf16 > 0 as a float: the low half shifted up, the high half masked
+                    z[2 * q] = __uint_as_float(yw[q] << 16) > 0.f ? g[2 * q] : 0.f;
+                    z[2 * q + 1] = __uint_as_float(yw[q] & 0xffff0000u) > 0.f ? g[2 * q + 1] : 0.f;
+                    const __nv_bfloat162 pr = __floats2bfloat162_rn(z[2 * q], z[2 * q + 1]);
+                    o[q] = *reinterpret_cast<const uint32_t*>(&pr);
+                }
+                *reinterpret_cast<uint4*>(dZ + p * C + c) = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) s_t[r][c + q] = z[q];
         }
-        s_t[r][c] = z;
+    } else {
+        for (int i = threadIdx.x; i < 64 * C; i += blockDim.x) {
+            const int r = i / C, c = i - r * C;
+            const size_t p = p0 + r;
+            float z = 0.f;
+            if (p < P) {
+                const float y = __bfloat162float(Y[p * ldy + c]);
+                z = y > 0.f ? dY[p * lddy + c] : 0.f;
+                dZ[p * C + c] = __float2bfloat16_rn(z);
+            }
+            s_t[r][c] = z;
+        }
     }
     __syncthreads();
     // bias gradient: one partial per channel per block
@@ -354,9 +384,11 @@ gevo_status gevo_relu_bwd(int64_t P, int32_t C, const float* dY, int32_t lddy, c
                           int32_t ldy, void* dZ, void* dZt, float* db, void* stream)
 {
     if (P <= 0 || C <= 0 || C > 128 || !dY || !Y || !dZ || !db) return GEVO_ERR_INVALID;
+    const int vec = C % 8 == 0 && ldy % 8 == 0 && lddy % 4 == 0 && gevo_aligned(Y, 16) &&
+                    gevo_aligned(dY, 16) && gevo_aligned(dZ, 16);
     k_relu_bwd<<<(unsigned)((P + 63) / 64), 256, 0, (cudaStream_t)stream>>>(
         (size_t)P, C, dY, lddy, reinterpret_cast<const bf16*>(Y), ldy, reinterpret_cast<bf16*>(dZ),
-        reinterpret_cast<bf16*>(dZt), db);
+        reinterpret_cast<bf16*>(dZt), db, vec);
     GEVO_LAUNCHED();
 }
 
