@@ -30,7 +30,9 @@ namespace gevo {
 
 constexpr int kGemmBM = 128;
 constexpr int kGemmBK = 64;
-constexpr int kGemmStages = 3;
+// two stages: the layers' K is short (3-18 slices) and more resident CTAs hide
+// the gathers' latency better than a deeper ring (measured: 2 > 3 > 4 stages)
+constexpr int kGemmStages = 2;
 constexpr long long kWaitLimit = 1ll << 22;    // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -226,29 +228,39 @@ __device__ __forceinline__ void wgrad_rows(const ConvA& cv, int M, int row0, int
     }
 }
 
-__device__ __forceinline__ void stage_wgrad_tile(const ConvA& cv, int P, int k0, const int wr[8],
-                                                 unsigned char* dst)
+// Loads the pieces of one slice into registers (issued a slice ahead, so their
+// latency overlaps the wait for the previous slice) ...
+__device__ __forceinline__ void wgrad_fetch(const ConvA& cv, int P, int k0, const int wr[8],
+                                            uint4 pa[8])
 {
-    const int kk = threadIdx.x & 63;
-    const int p = k0 + kk;
+    const int p = k0 + (int)(threadIdx.x & 63);
     int y = -1, x = 0;
     if (p < P) {
         x = p % cv.W;
         y = (p / cv.W) % cv.H;
     }
-    unsigned char* col = dst + (kk >> 3) * 128 + (kk & 7) * 2;
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-        const int g = (int)(threadIdx.x >> 6) + 2 * j;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        pa[j] = make_uint4(0u, 0u, 0u, 0u);
         if (wr[j] >= 0 && y >= 0) {
             const int tap = wr[j] >> 16, ci = wr[j] & 0xffff;
             const int dy = tap / 3 - 1, dx = tap % 3 - 1;
             if ((unsigned)(y + dy) < (unsigned)cv.H && (unsigned)(x + dx) < (unsigned)cv.W)
-                v = *reinterpret_cast<const uint4*>(cv.X + ((size_t)p + dy * cv.W + dx) * cv.C + ci);
+                pa[j] = *reinterpret_cast<const uint4*>(cv.X + ((size_t)p + dy * cv.W + dx) * cv.C + ci);
         }
-        unsigned char* d = col + g * 1024;
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    }
+}
+
+// ... and scatters them into a stage: piece j is rows 8 g .. 8 g + 7 (g = t / 64
+// + 2 j) of pixel column t % 64.
+__device__ __forceinline__ void wgrad_store(const uint4 pa[8], unsigned char* dst)
+{
+    const int kk = threadIdx.x & 63;
+    unsigned char* col = dst + (kk >> 3) * 128 + (kk & 7) * 2;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        unsigned char* d = col + ((int)(threadIdx.x >> 6) + 2 * j) * 1024;
+        const uint32_t w[4] = {pa[j].x, pa[j].y, pa[j].z, pa[j].w};
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             *reinterpret_cast<uint16_t*>(d + (2 * i) * 16) = (uint16_t)(w[i] & 0xffffu);
@@ -308,17 +320,22 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
     int yx[kConvRowsPerThread];
     if (MODE == kModeConv) conv_rows(cv, M, row0, yx);
     if (MODE == kModeWgrad) wgrad_rows(cv, M, row0, yx);
+    uint4 pa[MODE == kModeWgrad ? 8 : 1];   // the weight gradient's next A slice
     auto load = [&](int i) {   // slice kc0 + i into stage i % S
         const uint32_t st = base + (uint32_t)(i % S) * STAGE;
         const int k0 = (kc0 + i) * kGemmBK;
-        if (MODE == kModeConv)
+        if (MODE == kModeConv) {
             stage_conv_tile(cv, K, row0, k0, yx, st);
-        else if (MODE == kModeWgrad)
-            stage_wgrad_tile(cv, K, k0, yx, smem + (size_t)(i % S) * STAGE);
-        else
+        } else if (MODE == kModeWgrad) {
+            // A of this slice is in registers: store it, then fetch the next one
+            wgrad_store(pa, smem + (size_t)(i % S) * STAGE);
+            if (i + 1 < nk) wgrad_fetch(cv, K, k0 + kGemmBK, yx, pa);
+        } else {
             stage_tile<kGemmBM>(A, lda, M, K, row0, k0, st);
+        }
         stage_tile<BN>(B, ldb, N, K, col0, k0, st + A_BYTES);
     };
+    if (MODE == kModeWgrad && nk > 0) wgrad_fetch(cv, K, kc0 * kGemmBK, yx, pa);
     // the copies run S - 1 slices ahead; every iteration commits one group
     // (possibly empty) so that group i always holds slice i
 #pragma unroll
