@@ -113,19 +113,22 @@ k_relu_bwd(size_t P, int C, const float* __restrict__ dY, int lddy, const bf16* 
 }
 
 // 2x2 max pool, NHWC; X rows have stride ldx (a channel slice of a wider buffer)
+// I: the index type, 32-bit whenever the element count allows (the index
+// arithmetic's divisions dominate these element-wise kernels)
+template <typename I>
 __global__ void k_maxpool2(int nb, int H, int W, int C, const bf16* __restrict__ X, int ldx,
                            bf16* __restrict__ Y)
 {
     const int h = H / 2, w = W / 2;
-    const size_t n = (size_t)nb * h * w * C;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const I n = (I)nb * h * w * C;
+    for (I i = blockIdx.x * (I)blockDim.x + threadIdx.x; i < n; i += (I)gridDim.x * blockDim.x) {
         const int c = (int)(i % C);
-        const size_t q = i / C;
+        const I q = i / C;
         const int x = (int)(q % w);
-        const size_t t = q / w;
+        const I t = q / w;
         const int y = (int)(t % h);
-        const size_t b = t / h;
-        const size_t base = ((b * H + 2 * y) * W + 2 * x) * ldx + c;
+        const I b = t / h;
+        const size_t base = (((size_t)b * H + 2 * y) * W + 2 * x) * ldx + c;
         float m = __bfloat162float(X[base]);
         m = fmaxf(m, __bfloat162float(X[base + ldx]));
         m = fmaxf(m, __bfloat162float(X[base + (size_t)W * ldx]));
@@ -136,19 +139,20 @@ __global__ void k_maxpool2(int nb, int H, int W, int C, const bf16* __restrict__
 
 // gradient of the 2x2 max pool: the first maximum (row-major scan) of each
 // window receives dY; dX = beta dX + that (FP32, stride lddx)
+template <typename I>
 __global__ void k_maxpool2_bwd(int nb, int H, int W, int C, const bf16* __restrict__ X, int ldx,
                                const float* __restrict__ dY, float* __restrict__ dX, int lddx,
                                float beta)
 {
     const int h = H / 2, w = W / 2;
-    const size_t n = (size_t)nb * h * w * C;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const I n = (I)nb * h * w * C;
+    for (I i = blockIdx.x * (I)blockDim.x + threadIdx.x; i < n; i += (I)gridDim.x * blockDim.x) {
         const int c = (int)(i % C);
-        const size_t q = i / C;
+        const I q = i / C;
         const int x = (int)(q % w);
-        const size_t t = q / w;
+        const I t = q / w;
         const int y = (int)(t % h);
-        const size_t b = t / h;
+        const size_t b = (size_t)(t / h);
         const size_t pix[4] = {(b * H + 2 * y) * W + 2 * x, (b * H + 2 * y) * W + 2 * x + 1,
                                (b * H + 2 * y + 1) * W + 2 * x, (b * H + 2 * y + 1) * W + 2 * x + 1};
         float v[4];
@@ -169,6 +173,22 @@ __global__ void k_maxpool2_bwd(int nb, int H, int W, int C, const bf16* __restri
 }
 
 // nearest x2 upsample: Y (stride ldy, a channel slice) from X [nb][h][w][C]
+// vec: 8 channels (16 bytes) per step, 32-bit indices (C, ldy multiples of 8,
+// 16-byte aligned, fewer than 2^31 pieces)
+__global__ void k_upsample2_vec(int nb, int h, int w, int C, const bf16* __restrict__ X,
+                                bf16* __restrict__ Y, int ldy)
+{
+    const int H = 2 * h, W = 2 * w, C8 = C / 8;
+    const unsigned n = (unsigned)nb * H * W * C8;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned c8 = i % C8, q = i / C8;
+        const unsigned x = q % W, t = q / W;
+        const unsigned y = t % H, b = t / H;
+        *reinterpret_cast<uint4*>(Y + (size_t)q * ldy + 8 * c8) =
+            *reinterpret_cast<const uint4*>(X + ((size_t)(b * h + y / 2) * w + x / 2) * C + 8 * c8);
+    }
+}
+
 __global__ void k_upsample2(int nb, int h, int w, int C, const bf16* __restrict__ X,
                             bf16* __restrict__ Y, int ldy)
 {
@@ -185,7 +205,28 @@ __global__ void k_upsample2(int nb, int h, int w, int C, const bf16* __restrict_
     }
 }
 
-// gradient of the x2 upsample: dX[y][x] = sum of the four dY it was copied to
+// gradient of the x2 upsample: dX[y][x] = sum of the four dY it was copied to;
+// vec: 4 channels (16 bytes) per step, 32-bit indices
+__global__ void k_upsample2_bwd_vec(int nb, int h, int w, int C, const float* __restrict__ dY,
+                                    int lddy, float* __restrict__ dX)
+{
+    const int W = 2 * w, C4 = C / 4;
+    const unsigned n = (unsigned)nb * h * w * C4;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned c4 = i % C4, q = i / C4;
+        const unsigned x = q % w, t = q / w;
+        const unsigned y = t % h, b = t / h;
+        const size_t r0 = ((size_t)b * 2 * h + 2 * y) * W + 2 * x;
+        const float4 a = *reinterpret_cast<const float4*>(dY + r0 * lddy + 4 * c4);
+        const float4 e = *reinterpret_cast<const float4*>(dY + (r0 + 1) * lddy + 4 * c4);
+        const float4 f = *reinterpret_cast<const float4*>(dY + (r0 + W) * lddy + 4 * c4);
+        const float4 g = *reinterpret_cast<const float4*>(dY + (r0 + W + 1) * lddy + 4 * c4);
+        *reinterpret_cast<float4*>(dX + (size_t)q * C + 4 * c4) =
+            make_float4(a.x + e.x + f.x + g.x, a.y + e.y + f.y + g.y, a.z + e.z + f.z + g.z,
+                        a.w + e.w + f.w + g.w);
+    }
+}
+
 __global__ void k_upsample2_bwd(int nb, int h, int w, int C, const float* __restrict__ dY,
                                 int lddy, float* __restrict__ dX)
 {
@@ -397,7 +438,8 @@ gevo_status gevo_maxpool2(int32_t nb, int32_t H, int32_t W, int32_t C, const voi
 {
     if (nb <= 0 || H % 2 || W % 2 || C <= 0 || !X || !Y) return GEVO_ERR_INVALID;
     const size_t n = (size_t)nb * (H / 2) * (W / 2) * C;
-    k_maxpool2<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(
+    auto kern = n < ((size_t)1 << 31) ? k_maxpool2<uint32_t> : k_maxpool2<size_t>;
+    kern<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(
         nb, H, W, C, reinterpret_cast<const bf16*>(X), ldx, reinterpret_cast<bf16*>(Y));
     GEVO_LAUNCHED();
 }
@@ -408,7 +450,8 @@ gevo_status gevo_maxpool2_bwd(int32_t nb, int32_t H, int32_t W, int32_t C, const
 {
     if (nb <= 0 || H % 2 || W % 2 || C <= 0 || !X || !dY || !dX) return GEVO_ERR_INVALID;
     const size_t n = (size_t)nb * (H / 2) * (W / 2) * C;
-    k_maxpool2_bwd<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(
+    auto kern = n < ((size_t)1 << 31) ? k_maxpool2_bwd<uint32_t> : k_maxpool2_bwd<size_t>;
+    kern<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(
         nb, H, W, C, reinterpret_cast<const bf16*>(X), ldx, dY, dX, lddx, beta);
     GEVO_LAUNCHED();
 }
@@ -418,8 +461,13 @@ gevo_status gevo_upsample2(int32_t nb, int32_t h, int32_t w, int32_t C, const vo
 {
     if (nb <= 0 || h <= 0 || w <= 0 || C <= 0 || !X || !Y) return GEVO_ERR_INVALID;
     const size_t n = (size_t)nb * 4 * h * w * C;
-    k_upsample2<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(
-        nb, h, w, C, reinterpret_cast<const bf16*>(X), reinterpret_cast<bf16*>(Y), ldy);
+    if (C % 8 == 0 && ldy % 8 == 0 && gevo_aligned(X, 16) && gevo_aligned(Y, 16) &&
+        n / 8 < ((size_t)1 << 31))
+        k_upsample2_vec<<<grid_for(n / 8), 256, 0, (cudaStream_t)stream>>>(
+            nb, h, w, C, reinterpret_cast<const bf16*>(X), reinterpret_cast<bf16*>(Y), ldy);
+    else
+        k_upsample2<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(
+            nb, h, w, C, reinterpret_cast<const bf16*>(X), reinterpret_cast<bf16*>(Y), ldy);
     GEVO_LAUNCHED();
 }
 
@@ -428,7 +476,12 @@ gevo_status gevo_upsample2_bwd(int32_t nb, int32_t h, int32_t w, int32_t C, cons
 {
     if (nb <= 0 || h <= 0 || w <= 0 || C <= 0 || !dY || !dX) return GEVO_ERR_INVALID;
     const size_t n = (size_t)nb * h * w * C;
-    k_upsample2_bwd<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(nb, h, w, C, dY, lddy, dX);
+    if (C % 4 == 0 && lddy % 4 == 0 && gevo_aligned(dY, 16) && gevo_aligned(dX, 16) &&
+        n / 4 < ((size_t)1 << 31))
+        k_upsample2_bwd_vec<<<grid_for(n / 4), 256, 0, (cudaStream_t)stream>>>(nb, h, w, C, dY,
+                                                                              lddy, dX);
+    else
+        k_upsample2_bwd<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(nb, h, w, C, dY, lddy, dX);
     GEVO_LAUNCHED();
 }
 
