@@ -252,14 +252,20 @@ __device__ __forceinline__ void wgrad_fetch(const ConvA& cv, int P, int k0, cons
 }
 
 // ... and scatters them into a stage: piece j is rows 8 g .. 8 g + 7 (g = t / 64
-// + 2 j) of pixel column t % 64.
+// + 2 j) of pixel column t % 64.  This operand's core matrices sit kWgradLBO =
+// 144 bytes apart along K (8-row groups kWgradSBO = 8 x 144 apart) instead of
+// 128: the 32 lanes of a store then hit 16 distinct banks, two lanes per word,
+// where 128 put four columns on one bank.
+constexpr int kWgradLBO = 144;
+constexpr int kWgradSBO = 8 * kWgradLBO;
+
 __device__ __forceinline__ void wgrad_store(const uint4 pa[8], unsigned char* dst)
 {
     const int kk = threadIdx.x & 63;
-    unsigned char* col = dst + (kk >> 3) * 128 + (kk & 7) * 2;
+    unsigned char* col = dst + (kk >> 3) * kWgradLBO + (kk & 7) * 2;
 #pragma unroll
     for (int j = 0; j < 8; j++) {
-        unsigned char* d = col + ((int)(threadIdx.x >> 6) + 2 * j) * 1024;
+        unsigned char* d = col + ((int)(threadIdx.x >> 6) + 2 * j) * kWgradSBO;
         const uint32_t w[4] = {pa[j].x, pa[j].y, pa[j].z, pa[j].w};
 #pragma unroll
         for (int i = 0; i < 4; i++) {
@@ -283,8 +289,9 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
 {
     constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
     constexpr int S = kGemmStages;
-    constexpr uint32_t A_BYTES = kGemmBM * kGemmBK * 2;         // 16 KB
-    constexpr uint32_t STAGE = (kGemmBM + BN) * kGemmBK * 2;    // A block, then B block
+    // A block (16 KB; 18 KB padded for the weight gradient), then B block
+    constexpr uint32_t A_BYTES = MODE == kModeWgrad ? (kGemmBM / 8) * kWgradSBO : kGemmBM * kGemmBK * 2;
+    constexpr uint32_t STAGE = A_BYTES + BN * kGemmBK * 2;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long s_mbar[S];
     __shared__ uint32_t s_tmem;
@@ -355,7 +362,9 @@ k_gemm_bf16(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, C
             const uint32_t aBase = base + (uint32_t)s * STAGE, bBase = aBase + A_BYTES;
 #pragma unroll
             for (int k16 = 0; k16 < kGemmBK / 16; k16++) {
-                const uint64_t da = smem_desc(aBase + k16 * 256, 128, 1024);
+                const uint64_t da = MODE == kModeWgrad
+                                        ? smem_desc(aBase + k16 * 2 * kWgradLBO, kWgradLBO, kWgradSBO)
+                                        : smem_desc(aBase + k16 * 256, 128, 1024);
                 const uint64_t db = smem_desc(bBase + k16 * 256, 128, 1024);
                 mma_bf16(tmem, da, db, idesc, (i > 0 || k16 > 0) ? 1u : 0u);
             }
@@ -489,7 +498,8 @@ static gevo_status launch_gemm(int M, int N, int K, const __nv_bfloat16* A, int 
                                const float* bias, int relu, float beta, int ksplit, uint32_t* err,
                                cudaStream_t st, int trans_c)
 {
-    const size_t smem = (size_t)kGemmStages * (kGemmBM + BN) * kGemmBK * 2;
+    const size_t a_bytes = MODE == kModeWgrad ? (kGemmBM / 8) * kWgradSBO : kGemmBM * kGemmBK * 2;
+    const size_t smem = (size_t)kGemmStages * (a_bytes + BN * kGemmBK * 2);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_gemm_bf16<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
