@@ -64,3 +64,36 @@ def test_gemm_bf16_relu_bf16_out_and_accumulate():
     ref2 = a.astype(np.float64) @ b.astype(np.float64).T + 0.5
     assert (np.abs(C2.cpu().numpy() - ref2) <= 2e-6 * scale + 1e-6).all()
     assert _abi.gevo_last_error(ws) == 0
+
+
+@pytest.mark.parametrize("nb,H,W,Cin,Cout", [(2, 6, 10, 24, 8), (1, 12, 20, 8, 40), (3, 5, 8, 16, 16)])
+def test_conv_and_weight_gradient_ragged_sizes(nb, H, W, Cin, Cout):
+    """The implicit-GEMM convolution and weight gradient (gathered A operands) on
+    sizes that leave partial row tiles, partial column tiles and a partial last
+    K slice (P = nb H W not a multiple of 64, 9 Cin not of 128), against the
+    FP64 oracle convolution on the same BF16 values."""
+    from oracle import unet as ounet
+    rs = np.random.default_rng(nb * 1000 + H * 10 + Cin)
+    P = nb * H * W
+    x, xb = bf16_round(rs.normal(size=(nb, H, W, Cin)).astype(np.float32))
+    w, wb = bf16_round(rs.normal(size=(Cout, 9, Cin)).astype(np.float32) * 0.2)
+    dz, dzb = bf16_round(rs.normal(size=(nb, H, W, Cout)).astype(np.float32))
+    ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    X = to_dev_bf16(xb.reshape(-1))
+    Wt = to_dev_bf16(wb.reshape(-1))
+    Y = torch.zeros(P * Cout, dtype=torch.float32, device="cuda")
+    _abi.prior_call("gevo_conv3x3", nb, H, W, Cin, X, Cout, Wt, None, Y, Cout, 0, 0, 0.0, ws)
+    dZt = to_dev_bf16(np.ascontiguousarray(dzb.reshape(P, Cout).T).reshape(-1))
+    dW = torch.zeros(Cout * 9 * Cin, dtype=torch.float32, device="cuda")
+    _abi.prior_call("gevo_conv3x3_wgrad", nb, H, W, Cin, X, Cout, dZt, dW, ws)
+    torch.cuda.synchronize()
+    assert _abi.gevo_last_error(ws) == 0
+    x64, w64, dz64 = (a.astype(np.float64) for a in (x, w, dz))
+    ref = ounet.conv3x3(x64, w64, np.zeros(Cout))
+    mag = ounet.conv3x3(np.abs(x64), np.abs(w64), np.zeros(Cout))
+    got = Y.cpu().numpy().reshape(nb, H, W, Cout)
+    assert (np.abs(got - ref) <= 2e-6 * mag + 1e-30).all()
+    _, dw_ref, _ = ounet.conv3x3_bwd(x64, w64, dz64)
+    _, dw_mag, _ = ounet.conv3x3_bwd(np.abs(x64), w64, np.abs(dz64))
+    got_dw = dW.cpu().numpy().reshape(Cout, 9, Cin)
+    assert (np.abs(got_dw - dw_ref) <= 2e-6 * np.abs(dw_mag) + 1e-30).all()
