@@ -159,6 +159,7 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     __shared__ float4 s_rz[kBatch];
     __shared__ uint32_t s_mask[kBatch];
     __shared__ uint32_t s_act[ACT ? kBatch : 1];
+    __shared__ uint16_t s_list[NT / 32][kBatch];
     __shared__ uint32_t s_item;
     const int tid = threadIdx.x;
     constexpr int WROWS = 2 * PPT;
@@ -216,19 +217,27 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 if (ACT) s_act[j] = (__ldg(active + (gid >> 5)) >> (gid & 31)) & 1u;
             }
             __syncthreads();
-            const uint32_t my_bit = 1u << (tid >> 5);
-            for (int j = 0; j < nb; j++) {
+            // the batch entries whose strip mask has this warp's bit, in order: the
+            // walk below runs over them without a per-entry mask branch
+            const int warp = tid >> 5;
+            int nl = 0;
+            {
+                const uint32_t my_bit = 1u << warp, lt = (1u << (tid & 31)) - 1u;
+                for (int r = 0; r < nb; r += 32) {
+                    const int jj = r + (tid & 31);
+                    const bool in = jj < nb && (s_mask[jj] & my_bit);
+                    const uint32_t bal = __ballot_sync(0xffffffffu, in);
+                    if (in) s_list[warp][nl + __popc(bal & lt)] = (uint16_t)jj;
+                    nl += __popc(bal);
+                }
+                __syncwarp();
+            }
+            for (int q = 0; q < nl; q++) {
                 bool all = true;
 #pragma unroll
                 for (int k = 0; k < PPT; k++) all = all && done[k];
                 if (all) break;
-                if (!(s_mask[j] & my_bit)) {
-                    if (COUNT) {
-#pragma unroll
-                        for (int k = 0; k < PPT; k++) cnt[k] += done[k] ? 0u : 1u;
-                    }
-                    continue;
-                }
+                const int j = s_list[warp][q];
                 const float2 m = s_xy[j];
                 const float4 c = s_co[j];
                 const float4 r = s_rz[j];
@@ -247,13 +256,15 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 for (int k = 0; k < PPT; k++) G[k] = ex2_approx(p2[k]);
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    if (COUNT) cnt[k] += done[k] ? 0u : 1u;
                     const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, G[k]));
                     const bool ok = !done[k] && !(p2[k] > 0.f) && !(alpha < kAlphaMin);
                     const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
                     const bool stop = ok && Tn < kTStop;
                     const bool bl = ok && !stop;
                     done[k] = done[k] || stop;
+                    // entries examined = the stopping entry's position (entries
+                    // past the stop, masked or not, are not examined)
+                    if (COUNT && stop) cnt[k] = pos1;
                     const float w = bl ? __fmul_rn(alpha, T[k]) : 0.f;
                     C0[k] = __fmaf_rn(w, r.x, C0[k]);
                     C1[k] = __fmaf_rn(w, r.y, C1[k]);
@@ -309,7 +320,7 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 out_T[gp] = T[k];
                 out_nc[gp] = last[k];
                 if (COUNT) {
-                    out_ne[gp] = cnt[k];
+                    out_ne[gp] = cnt[k] ? cnt[k] : rg.y - rg.x;   // never stopped: the whole list
                     if (out_nb) out_nb[gp] = nbl[k];
                 }
             }
