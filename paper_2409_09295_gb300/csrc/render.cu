@@ -447,11 +447,11 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     __shared__ uint32_t s_id[kBatch];
     constexpr int NG = EXT ? 11 : 10;   // per-entry sums: 10 gradients (+ the error weight)
     __shared__ float s_g[kBatch][NG];
+    __shared__ uint16_t s_list[NW][kBatch];
     __shared__ uint32_t s_item;
     __shared__ uint32_t s_max[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int WROWS = 2 * PPT;
-    (void)lane;
 
     for (int it = 0;; it++) {
         int item;
@@ -547,12 +547,25 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 for (int q = 0; q < NG; q++) s_g[j][q] = 0.f;
             }
             __syncthreads();
-            const uint32_t my_bit = 1u << (tid >> 5);
             // entries at or past this warp's last blended position concern no lane
             const uint32_t boff = bstart - rg.x;
             const int jend = mymax > boff ? (int)min((uint32_t)nb, mymax - boff) : 0;
-            for (int j = jend - 1; j >= 0; j--) {
-                if (!(s_mask[j] & my_bit)) continue;
+            // the entries below jend whose strip mask has this warp's bit, in order
+            // (walked backwards below, without a per-entry mask branch)
+            int nl = 0;
+            {
+                const uint32_t my_bit = 1u << warp, lt = (1u << lane) - 1u;
+                for (int r = 0; r < jend; r += 32) {
+                    const int jj = r + lane;
+                    const bool in = jj < jend && (s_mask[jj] & my_bit);
+                    const uint32_t bal = __ballot_sync(0xffffffffu, in);
+                    if (in) s_list[warp][nl + __popc(bal & lt)] = (uint16_t)jj;
+                    nl += __popc(bal);
+                }
+                __syncwarp();
+            }
+            for (int q = nl - 1; q >= 0; q--) {
+                const int j = s_list[warp][q];
                 const uint32_t pos = boff + j;   // list position
                 const float2 m = s_xy[j];
                 const float4 c = s_co[j];
