@@ -619,14 +619,15 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 // coefficients are applied once per entry.
                 float m0 = 0.f, m1 = 0.f, m2 = 0.f, a_o = 0.f;
                 float a_r = 0.f, a_g = 0.f, a_b = 0.f, a_z = 0.f, a_e = 0.f;
+                // branch-free over the pixels: an unused pixel takes alpha = 0,
+                // which leaves T and the suffix unchanged and adds zeros
 #pragma unroll
                 for (int k = 0; k < PPT; k++) {
-                    if (!use[k]) continue;
-                    const float alpha = al[k];
+                    const float alpha = use[k] ? al[k] : 0.f;
                     const float dy = dyk[k];
                     const float om = 1.f - alpha;
                     const float inv = rcp_approx(om);
-                    const float Ti = T[k] * inv;
+                    const float Ti = use[k] ? T[k] * inv : T[k];
                     T[k] = Ti;
                     const float w = alpha * Ti;
                     if (EXT) a_e += w * pe[k];
@@ -638,21 +639,20 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     Pg[k] += alpha * gd;
                     a_r += gC0[k] * w; a_g += gC1[k] * w; a_b += gC2[k] * w;
                     if (DD) a_z += gD[k] * w;
-                    if (__fmul_rn(c.w, G[k]) <= kAlphaMax) {
-                        // dp = dL/dalpha * alpha
-                        float dp;
-                        if (DT) {
-                            const float dLda = gd * Ti - gTT[k] * inv;
-                            a_o += dLda * G[k];
-                            dp = dLda * alpha;
-                        } else {
-                            dp = gd * w;
-                        }
-                        const float t = dp * dy;
-                        m0 += dp;
-                        m1 += t;
-                        m2 += t * dy;
+                    // dp = dL/dalpha * alpha on unclamped pixels
+                    const bool unclamped = use[k] && __fmul_rn(c.w, G[k]) <= kAlphaMax;
+                    float dp;
+                    if (DT) {
+                        const float dLda = gd * Ti - gTT[k] * inv;
+                        a_o += unclamped ? dLda * G[k] : 0.f;
+                        dp = unclamped ? dLda * alpha : 0.f;
+                    } else {
+                        dp = unclamped ? gd * w : 0.f;
                     }
+                    const float t = dp * dy;
+                    m0 += dp;
+                    m1 += t;
+                    m2 += t * dy;
                 }
                 // without dL/dT_final, dL/do = sum dL/dalpha G = m0 / o (alpha = o G
                 // on every unclamped pixel), one product per entry
