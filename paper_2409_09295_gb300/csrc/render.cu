@@ -595,10 +595,9 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     float a_e = 0.f;
 #pragma unroll
                     for (int k = 0; k < PPT; k++) {
-                        if (!use[k]) continue;
-                        const float alpha = al[k];
+                        const float alpha = use[k] ? al[k] : 0.f;
                         const float om = 1.f - alpha;
-                        const float Ti = T[k] * rcp_approx(om);
+                        const float Ti = use[k] ? T[k] * rcp_approx(om) : T[k];
                         T[k] = Ti;
                         a_e += alpha * Ti * pe[k];
                         float qc = gC0[k] * r.x + gC1[k] * r.y + gC2[k] * r.z;
