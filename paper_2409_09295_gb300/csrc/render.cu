@@ -258,7 +258,7 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 for (int k = 0; k < PPT; k++) {
                     const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, G[k]));
                     const bool ok = !done[k] && !(p2[k] > 0.f) && !(alpha < kAlphaMin);
-                    const float Tn = __fmul_rn(T[k], __fsub_rn(1.f, alpha));
+                    const float Tn = __fmaf_rn(-alpha, T[k], T[k]);   // T (1 - alpha), one rounding
                     const bool stop = ok && Tn < kTStop;
                     const bool bl = ok && !stop;
                     done[k] = done[k] || stop;
