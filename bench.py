@@ -356,10 +356,10 @@ def main():
     dom = "render_bwd"   # the largest share of the step (profiles/ launch list)
     roof = dict(roofs[dom])
     # DRAM bytes of one reverse-walk launch: ncu (dram__bytes_read.sum + write) of the
-    # current kernel on the 4-view case of profiles/render_kernels_4view_500k.md, 51.43 MB
+    # current kernel on the 4-view case of profiles/render_kernels_4view_500k.md, 51.51 MB
     # for 245.15M walked entries, scaled by entries to this launch (same scene, same
     # resolution)
-    roof.update({"traffic": 51.43e6 * E_bwd / 245.15e6,
+    roof.update({"traffic": 51.51e6 * E_bwd / 245.15e6,
                  "traffic_source": "ncu dram bytes of the 4-view case, scaled by walked entries",
                  "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {clk_peak:.0f} MHz"})
 
