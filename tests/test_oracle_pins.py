@@ -360,19 +360,71 @@ def _rodrigues(phi):
     return np.eye(3) + np.sin(th) / th * K + (1 - np.cos(th)) / th ** 2 * K @ K
 
 
+GUARD = 1.3   # guard band of the EWA Jacobian: |x/z| clamped at 1.3 x the half field of view
+
+
+def _guard_flags(g, cams):
+    """Per view and Gaussian: (x/z beyond the guard band, y/z beyond it), from the
+    camera-frame means.  Used to keep finite differences away from a clamp that
+    flips inside [-h, h] and to count the Gaussians a case sends through the
+    clamped-Jacobian branch."""
+    out = []
+    for c in cams:
+        R = np.asarray(c["R"], np.float64)
+        p = np.asarray(g["means"], np.float64) @ R.T + np.asarray(c["t"], np.float64)
+        limx = GUARD * 0.5 * c["W"] / c["fx"]
+        limy = GUARD * 0.5 * c["H"] / c["fy"]
+        out.append(np.stack([np.abs(p[:, 0] / p[:, 2]) > limx,
+                             np.abs(p[:, 1] / p[:, 2]) > limy], axis=1))
+    return out
+
+
 def _lin_loss(g, cams, Wts):
     outs, projs, b = oracle.render_views(g, cams)
     L = sum((o["rgb"] * w["rgb"]).sum() + (o["depth"] * w["depth"]).sum()
             + (o["T"] * w["T"]).sum() for o, w in zip(outs, Wts))
-    sig = [o["sig"] for o in outs] + [p["radius"] for p in projs]
+    sig = ([o["sig"] for o in outs] + [p["radius"] for p in projs]
+           + [p["clamped"] for p in projs] + _guard_flags(g, cams))
     return L, outs, projs, b, sig
+
+
+def _front_alpha_clamped(cams, projs, b):
+    """Number of pixels whose first blended entry has o G above the 0.99 clamp.
+    The first blended entry of a pixel is always blended (T = 1 before it and
+    1 - 0.99 > 1e-4), so every pixel counted here sends one entry through the
+    clamped-alpha branch of the backward pass."""
+    n = 0
+    base = 0
+    for v, c in enumerate(cams):
+        W, H = int(c["W"]), int(c["H"])
+        tx = (W + 15) // 16
+        p = projs[v]
+        for py in range(H):
+            for px in range(W):
+                s, e = b["ranges"][base + (py // 16) * tx + px // 16]
+                for i in range(s, e):
+                    gi = b["vals"][i]
+                    dx, dy = p["xy"][gi, 0] - px, p["xy"][gi, 1] - py
+                    ca, cb, cc = p["conic"][gi]
+                    power = -0.5 * (ca * dx * dx + cc * dy * dy) - cb * dx * dy
+                    if power > 0:
+                        continue
+                    og = p["opacity"][gi] * np.exp(power)
+                    if min(og, 0.99) < 1.0 / 255.0:
+                        continue
+                    n += og > 0.99
+                    break
+        base += tx * ((H + 15) // 16)
+    return n
 
 
 def _same(s1, s2):
     return all(np.array_equal(a, b) for a, b in zip(s1, s2))
 
 
-def _fd_case(g, cams, n_per_tensor, seed, h=1e-6):
+def _fd_case(g, cams, n_per_tensor, seed, h=1e-6, n_for=None):
+    """Checks sampled parameters and every pose component against central
+    differences; n_for overrides the sample size per parameter tensor."""
     rs = np.random.default_rng(seed)
     g = {k: (np.asarray(v, np.float64) if isinstance(v, np.ndarray) else v) for k, v in g.items()}
     Wts = [dict(rgb=rs.normal(size=(3, c["H"], c["W"])), depth=rs.normal(size=(c["H"], c["W"])),
@@ -384,7 +436,8 @@ def _fd_case(g, cams, n_per_tensor, seed, h=1e-6):
     keys = ["means", "scales", "quats", "opacities"] + (["rgb"] if "rgb" in g else ["sh"])
     for k in keys:
         flat = g[k].reshape(-1)
-        for i in rs.choice(flat.size, size=min(flat.size, n_per_tensor), replace=False):
+        n_k = (n_for or {}).get(k, n_per_tensor)
+        for i in rs.choice(flat.size, size=min(flat.size, n_k), replace=False):
             gp, gm = dict(g), dict(g)
             gp[k], gm[k] = g[k].copy(), g[k].copy()
             gp[k].reshape(-1)[i] += h
@@ -440,6 +493,60 @@ def test_fd_tracking_subscene_sample():
     a random sample of parameters plus all six pose components."""
     g, cams = scenes.tracking_subscene(2000)
     assert _fd_case(g, cams, 4, 2) >= 15
+
+
+def test_fd_alpha_clamp_branch():
+    """Near-opaque, wide splats: pixels near their centres have o G > 0.99, so
+    alpha sits at the clamp and those pixels must add nothing to the opacity,
+    conic and mean gradients (finite differences see alpha not move)."""
+    g = scenes.camera_box_scene(6, 7, sh_degree=None, box=((-0.6, 0.6), (-0.4, 0.4), (2, 3)))
+    g["scales"] = np.tile(np.array([0.5, 0.4, 0.3]), (6, 1))
+    g["opacities"] = np.linspace(0.996, 0.9995, 6)
+    cams = [scenes.identity_camera(64, 48, 60.0)]
+    _, projs, b = oracle.render_views(g, cams)
+    assert _front_alpha_clamped(cams, projs, b) >= 5
+    assert _fd_case(g, cams, 12, 3) >= 50
+
+
+def test_fd_sh_clamp_branch():
+    """SH-3 splats whose DC coefficient drives a channel below zero: the clamped
+    channel's colour is 0 whatever its coefficients, so its SH gradients and its
+    share of the view-direction (mean and pose) gradient must vanish."""
+    g = scenes.camera_box_scene(8, 8, sh_degree=3, box=((-0.3, 0.3), (-0.3, 0.3), (2, 3)))
+    g["scales"] = g["scales"] * 4
+    sh = np.array(g["sh"], np.float64)
+    sh[::2, 0, 0] = -2.2
+    sh[1::3, 0, 2] = -2.0
+    g["sh"] = sh
+    R1, t1 = scenes.look_at([0.1, -0.2, -0.5], [0, 0, 2.5])
+    cams = [scenes.camera(R1, t1, 60, 62, 24, 16, 48, 32)]
+    _, projs, _ = oracle.render_views(g, cams)
+    vis = projs[0]["radius"] > 0
+    assert (projs[0]["clamped"][vis].sum(axis=1) > 0).sum() >= 5
+    assert _fd_case(g, cams, 10, 4, n_for=dict(sh=200)) >= 150
+
+
+def test_fd_guard_band_branch():
+    """Wide splats whose means lie beyond 1.3 x the half field of view (in x and
+    in y) but still reach the image: the EWA Jacobian uses the clamped x/z, y/z,
+    and the clamped coordinate passes gradient only through 1/z."""
+    g = scenes.camera_box_scene(8, 9, sh_degree=3, box=((-0.3, 0.3), (-0.3, 0.3), (2, 3)))
+    m = np.array(g["means"], np.float64)
+    m[:4] = [[1.5, 0.1, 2.5], [-1.6, -0.2, 2.6], [0.2, 1.1, 2.4], [-0.1, -1.2, 2.7]]
+    g["means"] = m
+    sc = np.array(g["scales"], np.float64)
+    sc[:4] = [0.3, 0.25, 0.2]
+    sc[4:] *= 4
+    g["scales"] = sc
+    R1, t1 = scenes.look_at([0.0, 0.0, 0.0], [0, 0, 2.5])
+    R2, t2 = scenes.look_at([0.2, 0.1, 0.1], [0.1, 0, 2.5])
+    cams = [scenes.camera(R1, t1, 60, 62, 24, 16, 48, 32),
+            scenes.camera(R2, t2, 58, 58, 24, 16, 48, 32)]
+    _, projs, _ = oracle.render_views(g, cams)
+    for v, flags in enumerate(_guard_flags(g, cams)):
+        seen = projs[v]["radius"] > 0
+        assert (flags[:, 0] & seen).sum() >= 2 and (flags[:, 1] & seen).sum() >= 2
+    assert _fd_case(g, cams, 12, 5) >= 60
 
 
 def test_l1_loss_closed_form():
