@@ -213,9 +213,18 @@ gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const gevo_proj*
  * every GPU loading the library holds until the process exits.  It caps
  * dup_capacity at GEVO_NOALLOC_MAX_DUPS and the layout at GEVO_NOALLOC_MAX_TILES
  * tiles; larger sizes return GEVO_ERR_SCRATCH_LIMIT without launching.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and clears the parts that must
+ * The array is reserved in device memory when the CUDA runtime loads this
+ * library's kernels on a device.  Under lazy module loading (the default of
+ * CUDA 12 and later) that can be the first call of this function on that
+ * device, so that first call may fail with GEVO_ERR_CUDA when the device has no
+ * memory left.  A caller whose allocation-free region must not reserve
+ * anything makes one call outside it first, for example with dup_capacity 0
+ * (which counts the duplicates only).
+ * The first call on a device also looks up the array's device address (once
+ * per device, with that device current) and keeps it for the process; make
+ * that first call before any stream capture.  cudaDeviceReset on that device
+ * unloads the array, after which this function must not be called again in
+ * the process.  Every call shares the one array and clears the parts that must
  * start at zero, so calls whose GPU work overlaps (other streams, other host
  * threads) race and must be serialised by the caller.  A duplicate count above
  * dup_capacity is reported only through *d_n_dup > dup_capacity (the ranges are

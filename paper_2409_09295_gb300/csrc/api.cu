@@ -27,6 +27,25 @@ WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap)
     return w;
 }
 
+bool layout_valid(const gevo_layout& L)
+{
+    if (L.n_views < 1 || L.n_views > GEVO_MAX_VIEWS) return false;
+    int64_t tiles = 0, pix = 0;
+    for (int v = 0; v < L.n_views; v++) {
+        const int32_t w = L.width[v], h = L.height[v];
+        if (w <= 0 || h <= 0 || w > 65536 || h > 65536) return false;
+        if (L.tiles_x[v] != (w + GEVO_TILE - 1) / GEVO_TILE ||
+            L.tiles_y[v] != (h + GEVO_TILE - 1) / GEVO_TILE)
+            return false;
+        if (L.tile_base[v] != tiles || L.pix_base[v] != pix) return false;
+        tiles += (int64_t)L.tiles_x[v] * L.tiles_y[v];
+        pix += (int64_t)w * h;
+        if (tiles > (1 << 30)) return false;
+    }
+    return L.tile_base[L.n_views] == tiles && L.pix_base[L.n_views] == pix &&
+           L.total_tiles == tiles && L.total_pixels == pix;
+}
+
 int sm_count()
 {
     static int cached = 0;
@@ -85,7 +104,7 @@ gevo_status gevo_layout_init(gevo_layout* layout, int32_t n_views, const int32_t
 
 size_t gevo_workspace_bytes(const gevo_layout* layout, int32_t n, uint64_t dup_capacity)
 {
-    if (!layout || layout->n_views < 1) return 0;
+    if (!layout || !gevo::layout_valid(*layout)) return 0;
     return gevo::ws_layout(*layout, n, dup_capacity).total;
 }
 

@@ -17,6 +17,7 @@
 // The tile is handled by counting, so the sort only moves the depth half; the
 // result is the unique (tile, depth bits, id) order, identical to a full sort.
 #include "gevo_internal.cuh"
+#include <mutex>
 
 namespace gevo {
 
@@ -613,15 +614,36 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
     }
 }
 
+// Dynamic shared-memory limits of the binning and sort kernels, raised once per
+// device (the attribute belongs to the device's context) and only upwards.
+// Host threads may sort concurrently, so the record sits behind a mutex.
+static std::mutex g_attr_mu;
+
 static void bin_attributes(size_t bin_smem)
 {
-    static size_t done = 0;
-    if (bin_smem > 48 * 1024 && bin_smem > done) {
+    static size_t done[256] = {0};
+    int dev = 0;
+    if (bin_smem <= 48 * 1024 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256)
+        return;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (bin_smem > done[dev]) {
         cudaFuncSetAttribute(k_count_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
         cudaFuncSetAttribute(k_scatter_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
         cudaFuncSetAttribute(k_count_off, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
         cudaFuncSetAttribute(k_scatter_off, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
-        done = bin_smem;
+        done[dev] = bin_smem;
+    }
+}
+
+static void segsort_attributes(size_t smem)
+{
+    static bool done[256] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (!done[dev]) {
+        cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        done[dev] = true;
     }
 }
 
@@ -634,7 +656,7 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
                                      uint32_t* ranges, uint64_t* d_n_dup, void* workspace,
                                      void* stream)
 {
-    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->radius ||
+    if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->radius ||
         !proj->rgb_depth || !ranges || !d_n_dup || !workspace || !gevo_aligned(workspace, 256) ||
         (dup_capacity > 0 && (!keys || !vals)) || dup_capacity > 0xffffffffull)
         return GEVO_ERR_INVALID;
@@ -689,11 +711,7 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
                 dup_capacity, bucket);
         GEVO_CHECK_LAUNCH();
         const size_t smem = (sizeof(uint32_t) + sizeof(uint16_t)) * 2 * kSortSmemItems;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
+        segsort_attributes(smem);
         k_segsort<<<T, kSortThreads, smem, st>>>(tile_order, tile_start, tile_count, d_n_dup,
                                                  dup_capacity, bucket, bucket2,
                                                  reinterpret_cast<unsigned long long*>(keys), vals);
@@ -709,8 +727,6 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
 // scratch is the static array below; the launch sequence is that of
 // gevo_bin_sort with workspace pointers into the array.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace gevo {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GEVO_NOALLOC_SCRATCH_BYTES];
 
@@ -738,7 +754,7 @@ extern "C" gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t 
                                              uint64_t* keys, uint32_t* vals, uint32_t* ranges,
                                              uint64_t* d_n_dup, void* stream)
 {
-    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->radius ||
+    if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->radius ||
         !proj->rgb_depth || !ranges || !d_n_dup || (dup_capacity > 0 && (!keys || !vals)))
         return GEVO_ERR_INVALID;
     if (dup_capacity > GEVO_NOALLOC_MAX_DUPS || layout->total_tiles > GEVO_NOALLOC_MAX_TILES)
@@ -795,11 +811,7 @@ extern "C" gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t 
                 dup_capacity, bucket);
         GEVO_CHECK_LAUNCH();
         const size_t smem = (sizeof(uint32_t) + sizeof(uint16_t)) * 2 * kSortSmemItems;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_segsort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            attr = true;
-        }
+        segsort_attributes(smem);
         k_segsort<<<T, kSortThreads, smem, st>>>(tile_order, tile_start, tile_count, d_n_dup,
                                                  dup_capacity, bucket, bucket2,
                                                  reinterpret_cast<unsigned long long*>(keys), vals);

@@ -500,12 +500,10 @@ static gevo_status launch_gemm(int M, int N, int K, const __nv_bfloat16* A, int 
 {
     const size_t a_bytes = MODE == kModeWgrad ? (kGemmBM / 8) * kWgradSBO : kGemmBM * kGemmBK * 2;
     const size_t smem = (size_t)kGemmStages * (a_bytes + BN * kGemmBK * 2);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_gemm_bf16<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        attr = true;
-    }
+    // set on every launch: a host-only call of about a microsecond, correct for
+    // whichever device is current and free of shared state between host threads
+    cudaFuncSetAttribute(k_gemm_bf16<BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     dim3 grid((M + kGemmBM - 1) / kGemmBM, (N + BN - 1) / BN, ksplit);
     k_gemm_bf16<BN, MODE><<<grid, 128, smem, st>>>(M, N, K, A, lda, cv, B, ldb, C, ldc, out_bf16,
                                                    bias, relu, beta, ksplit, err, trans_c);

@@ -100,6 +100,62 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return y;
 }
 
+// A layout is used only as gevo_layout_init fills it: 1..GEVO_MAX_VIEWS views of
+// positive size, tile and pixel counts and the per-view bases recomputed from
+// the widths and heights.  Entry points reject anything else as invalid, so a
+// hand-built layout cannot make a kernel index past the tile or pixel planes.
+bool layout_valid(const gevo_layout& L);
+
+// Packed pairs of binary32 values for the paired FP32 instructions of sm_100
+// and later (add / sub / mul / fma .rn.f32x2: two IEEE round-to-nearest
+// results per lane and instruction, each the same as the scalar instruction's).
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_make(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_splat(float a) { return f2_make(a, a); }
+__device__ __forceinline__ float f2_lo(f2 x)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+    return a;
+}
+__device__ __forceinline__ float f2_hi(f2 x)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+    return b;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b)
+{
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
 int sm_count();
 int device_max_smem_optin();
 

@@ -132,7 +132,7 @@ extern "C" gevo_status gevo_loss_l1(const gevo_layout* layout, const float* rgb,
                                     float* dL_ddepth, float* loss, void* workspace, void* stream)
 {
     (void)workspace;
-    if (!layout || layout->n_views < 1 || !rgb || !target_rgb || !dL_drgb || !loss)
+    if (!layout || !gevo::layout_valid(*layout) || !rgb || !target_rgb || !dL_drgb || !loss)
         return GEVO_ERR_INVALID;
     if (lambda_depth != 0.f && (!depth || !target_depth || !dL_ddepth)) return GEVO_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
@@ -166,7 +166,7 @@ extern "C" gevo_status gevo_loss_l1_err(const gevo_layout* layout, const float* 
                                         float* pix_err, void* workspace, void* stream)
 {
     (void)workspace;
-    if (!layout || layout->n_views < 1 || !rgb || !target_rgb || !dL_drgb || !loss || !pix_err)
+    if (!layout || !gevo::layout_valid(*layout) || !rgb || !target_rgb || !dL_drgb || !loss || !pix_err)
         return GEVO_ERR_INVALID;
     if (lambda_depth != 0.f && (!depth || !target_depth || !dL_ddepth)) return GEVO_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;

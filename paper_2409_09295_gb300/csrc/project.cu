@@ -616,7 +616,7 @@ extern "C" gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussi
                                     const gevo_camera* cams, gevo_proj* out, void* workspace,
                                     void* stream)
 {
-    if (!layout || layout->n_views < 1 || !valid_gaussians(g) || !cams || !valid_proj(out) ||
+    if (!layout || !gevo::layout_valid(*layout) || !valid_gaussians(g) || !cams || !valid_proj(out) ||
         !workspace || !gevo_aligned(workspace, 256))
         return GEVO_ERR_INVALID;
     if (g->n == 0) return GEVO_OK;
@@ -642,7 +642,7 @@ static gevo_status project_bwd(const gevo_layout* layout, const gevo_gaussians* 
                                void* workspace, void* stream, const uint32_t* list,
                                const uint32_t* list_count)
 {
-    if (!layout || layout->n_views < 1 || !valid_gaussians(g) || !cams || !proj || !proj->radius ||
+    if (!layout || !gevo::layout_valid(*layout) || !valid_gaussians(g) || !cams || !proj || !proj->radius ||
         !grad2d || !grad2d->xy || !grad2d->conic_opacity || !grad2d->rgb_depth || !out ||
         !out->means || !out->scales || !out->quats || !out->opacities || !workspace)
         return GEVO_ERR_INVALID;

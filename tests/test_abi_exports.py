@@ -11,9 +11,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
+def _declared(headers=("gevo.h", "gevo_prior.h", "gevo_map.h")):
     names = set()
-    for h in ("gevo.h", "gevo_prior.h", "gevo_map.h", "gevo_bench.h"):
+    for h in headers:
         src = open(os.path.join(ROOT, "include", h)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names |= set(re.findall(r"\b(gevo_[a-z0-9_]+)\s*\(", src))
@@ -37,6 +37,44 @@ def test_header_declares_the_stage_calls():
 def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_probe_library_exports_the_measurement_symbols_only(lib):
+    from paper_2409_09295_gb300 import _abi, build
+    probes = ctypes.CDLL(build.PROBE_LIB)
+    bench = _declared(("gevo_bench.h",))
+    assert sorted(_abi.BENCH) == bench
+    assert all(hasattr(probes, n) for n in bench)
+    assert not any(hasattr(lib, n) for n in bench)   # not part of the product library
+
+
+def test_bad_layouts_are_rejected_before_any_launch(lib):
+    """A layout that gevo_layout_init did not produce (too many views, counts or
+    bases that disagree with the sizes) is refused by the entry points with
+    GEVO_ERR_INVALID before they touch any pointer, so no GPU is needed."""
+    from paper_2409_09295_gb300 import _abi
+    L = _abi.load()
+    good = _abi.gevo_layout_init([64, 32], [48, 16])
+    bad = []
+    for field, val in (("n_views", 65), ("n_views", 0), ("total_tiles", good.total_tiles + 1),
+                       ("total_pixels", good.total_pixels - 1)):
+        b = _abi.Layout.from_buffer_copy(good)
+        setattr(b, field, val)
+        bad.append(b)
+    for arr, v, val in (("tile_base", 1, 11), ("tiles_x", 0, 5), ("pix_base", 2, 1),
+                        ("width", 1, 0)):
+        b = _abi.Layout.from_buffer_copy(good)
+        getattr(b, arr)[v] = val
+        bad.append(b)
+    dummy = ctypes.c_void_p(256)       # never dereferenced: validation comes first
+    proj = _abi.Proj(dummy, dummy, dummy, dummy, dummy)
+    for b in bad:
+        for fn in (L.gevo_bin_sort, L.gevo_bin_sort_noalloc):
+            args = [ctypes.byref(b), 10, ctypes.byref(proj), 16] + [dummy] * 4
+            if fn is L.gevo_bin_sort:
+                args += [dummy]
+            assert fn(*args, None) == 1
+        assert _abi.gevo_workspace_bytes(b, 10, 16) == 0
 
 
 def test_binding_lists_every_declared_symbol():
