@@ -10,6 +10,8 @@ L1 photometric + depth loss against stop-gradient targets, the reverse walk and
 the projection backward with se(3) pose gradients.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --case render|prior [--batch B]   # small cases to profile one
+                                                    # kernel with ncu; no JSON line
 
 N > 1 runs independent replicas, one per GPU (the path has no exchange step).
 Rank 0 prints one JSON line.
@@ -42,7 +44,58 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mapping", action="store_true")
+    ap.add_argument("--case", choices=["render", "prior"], default=None,
+                    help="run a small profiling case instead of the benchmark")
+    ap.add_argument("--batch", type=int, default=8, help="batch of the prior case")
+    ap.add_argument("--threads-fwd", type=int, default=64, help="render case: blend threads per tile")
+    ap.add_argument("--threads-bwd", type=int, default=64, help="render case: walk threads per tile")
     return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# small cases to profile one kernel at a time with ncu: each holds well under
+# 1 GB on the device while its inputs exceed the 129 MB L2, so DRAM counters
+# stay meaningful and a capture of one launch (-k regex:<kernel> -s 1 -c 1)
+# ends in seconds
+# ---------------------------------------------------------------------------
+def render_case(threads_fwd=64, threads_bwd=64):
+    """4 views x 640x480 of the 500k-Gaussian room scene: two full forward +
+    L1 + backward steps (persistent grids with the given threads per tile)."""
+    import torch
+
+    from paper_2409_09295_gb300 import raster, scenes
+    from paper_2409_09295_gb300.batch import BatchedReplay
+    w = scenes.workload(2)
+    cams = w["cams"][:4]
+    g = raster.gaussians_to_device(w["scene"])
+    P = sum(c["W"] * c["H"] for c in cams)
+    tr = torch.full((3 * P,), 0.5, device="cuda")
+    td = torch.full((P,), 3.0, device="cuda")
+    tf = dict(threads_per_tile=threads_fwd, persistent=1, blocks_per_sm=0)
+    tb = dict(threads_per_tile=threads_bwd, persistent=1, blocks_per_sm=0)
+    rep = BatchedReplay(g, cams, tr, td, 1.0, autotune=False, tuning_fwd=tf, tuning_bwd=tb)
+    for _ in range(2):
+        rep.step_eager()
+        torch.cuda.synchronize()
+    e_fwd, e_bwd = rep.eval_counts()
+    print("render case ok, duplicates", rep.n_dup, "evals fwd", e_fwd, "bwd", e_bwd)
+
+
+def prior_case(nb=8):
+    """Two depth-prior train steps at batch nb x 320x240 (the bench line's step
+    is nb = 32)."""
+    import numpy as np
+    import torch
+
+    from paper_2409_09295_gb300.prior import DepthUNet
+    net = DepthUNet(nb, 240, 320, seed=1)
+    rs = np.random.default_rng(0)
+    rgb = torch.from_numpy(rs.uniform(size=(nb, 3, 240, 320)).astype(np.float32)).cuda()
+    tar = torch.from_numpy(rs.normal(1.0, 0.3, size=nb * 240 * 320).astype(np.float32)).cuda()
+    for _ in range(2):
+        net.train_step(rgb, tar, torch.ones_like(tar))
+    torch.cuda.synchronize()
+    print("prior case ok, loss", float(net.loss.item()))
 
 
 def peaks():
@@ -175,6 +228,14 @@ def whole_job(ms_local: float, units_local: float, world: int, device=None):
 
 def main():
     args = parse()
+    if args.case is not None:
+        import torch
+        torch.cuda.set_device(0)
+        if args.case == "render":
+            render_case(args.threads_fwd, args.threads_bwd)
+        else:
+            prior_case(args.batch)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -191,7 +252,7 @@ def main():
         dist.init_process_group("nccl")
 
     from paper_2409_09295_gb300 import _abi, raster, scenes
-    from paper_2409_09295_gb300.batch import BatchedReplay, PlainReplay
+    from paper_2409_09295_gb300.batch import BatchedReplay, HostStep, PlainReplay
     _abi.load()
 
     dev = torch.device("cuda", local)
@@ -212,17 +273,15 @@ def main():
 
     rep = BatchedReplay(g, cams, target_rgb, target_depth, lambda_depth=1.0)
     E_fwd, E_bwd, B = rep.eval_counts(blended=True)
-    rep.capture()
+    rep.capture()                          # the whole step: one CUDA graph
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    nst = len(rep.stages())
 
     for _ in range(args.warmup):
         rep.replay()
     torch.cuda.synchronize()
     assert rep.pipe.last_error() == 0, "duplicate capacity exceeded"
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
-           for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     clocks = Clocks(local)
     if world > 1:
         dist.barrier()
@@ -232,7 +291,9 @@ def main():
     torch.cuda.nvtx.range_push("timed")
     for k in range(args.steps):
         flush.zero_()                      # L2 flushed between timed steps
-        rep.replay(evs[k])
+        evs[k][0].record()
+        rep.replay()
+        evs[k][1].record()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     wall1 = time.perf_counter()
@@ -240,61 +301,44 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     assert rep.pipe.last_error() == 0, "duplicate capacity exceeded"
-    step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
-    stage_ms = {name: sum(e[i].elapsed_time(e[i + 1]) for e in evs) / args.steps
-                for i, (name, _) in enumerate(rep.graphs)}
+    step_ms = [e[0].elapsed_time(e[1]) for e in evs]
     V = len(cams)
     total_ms, evals = whole_job(sum(step_ms), (E_fwd + E_bwd) * args.steps, world, dev)
     value = evals / (total_ms / 1e3)
     views_per_s = V * args.steps * world / (total_ms / 1e3)
 
-    # ---- end to end through the C ABI with host buffers ---------------------------------
-    host_in = {k: torch.from_numpy(np.ascontiguousarray(scene[k], np.float32)).pin_memory()
-               for k in ("means", "scales", "quats", "opacities", "sh")}
-    host_cams = rep.camt.cpu().pin_memory()
-    host_tr = target_rgb.cpu().pin_memory()
-    host_td = target_depth.cpu().pin_memory()
-    out_loss = torch.empty(V, dtype=torch.float32).pin_memory()
-    out_dxi = torch.empty(V, 6, dtype=torch.float32).pin_memory()
-    h2d = sum(t.numel() * 4 for t in host_in.values()) + host_cams.numel() * 4 + \
-        host_tr.numel() * 4 + host_td.numel() * 4
-    d2h = out_loss.numel() * 4 + out_dxi.numel() * 4
+    # ---- per-stage times (diagnostic: the six stages as graphs of their own,
+    # events between them, same L2 flush; the step above is one graph) --------
+    nst = len(rep.stages())
+    sevs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 1)]
+            for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        rep.replay_stages(sevs[k])
+    torch.cuda.synchronize()
+    stage_ms = {name: sum(e[i].elapsed_time(e[i + 1]) for e in sevs) / args.steps
+                for i, (name, _) in enumerate(rep.stages())}
+    staged_ms = sum(e[0].elapsed_time(e[-1]) for e in sevs) / args.steps
 
-    # The parameters and cameras are uploaded first (projection reads them); the
-    # targets, first read by the loss stage, are uploaded on a second stream
-    # while projection, sort and blend run, and the loss stage waits for them.
-    main = torch.cuda.current_stream()
-    side = torch.cuda.Stream()
-
-    def e2e_step():
-        side.wait_stream(main)             # the previous step is done with the targets
-        for k, t in host_in.items():
-            g[k].copy_(t, non_blocking=True)
-        rep.camt.copy_(host_cams, non_blocking=True)
-        params_in = torch.cuda.Event()
-        params_in.record(main)
-        side.wait_event(params_in)         # no contention with the parameter upload
-        with torch.cuda.stream(side):
-            target_rgb.copy_(host_tr, non_blocking=True)
-            target_depth.copy_(host_td, non_blocking=True)
-        targets_in = torch.cuda.Event()
-        targets_in.record(side)
-        rep.replay(before={"loss": lambda: main.wait_event(targets_in)})
-        out_loss.copy_(rep.pipe.loss, non_blocking=True)
-        out_dxi.copy_(rep.pipe.dxi, non_blocking=True)
-
+    # ---- end to end with host buffers: uploads of parameters, cameras and
+    # targets from pinned memory, the step, and the read-back of the loss, the
+    # pose gradients and all parameter gradients, as one graph per step ------
+    hs = HostStep(rep)
+    h2d, d2h = hs.h2d_bytes, hs.d2h_bytes
     for _ in range(2):
-        e2e_step()
+        hs.step()
     torch.cuda.synchronize()
     e2e_ms = 0.0
     for _ in range(args.steps):
         flush.zero_()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record()
-        e2e_step()
+        hs.step()
         e.record()
         e.synchronize()
         e2e_ms += s.elapsed_time(e)
+    assert rep.pipe.last_error() == 0, "duplicate capacity exceeded"
+    assert torch.isfinite(hs.host_out["means"]).all()
     e2e_ms, e2e_evals = whole_job(e2e_ms, (E_fwd + E_bwd) * args.steps, world, dev)
     e2e_value = e2e_evals / (e2e_ms / 1e3)
 
@@ -353,10 +397,10 @@ def main():
             ach, peak = amount / sec / 1e9, hbm_peak
         roofs[name] = {"bound": bound, "kernel": kernels[name], "achieved": ach, "peak": peak,
                        "unit": unit, "frac": ach / peak, "ms": stage_ms[name]}
-    dom = "render_bwd"   # the largest share of the step (profiles/ launch list)
+    dom = "render_bwd"   # the largest share of the step in the ncu launch list
     roof = dict(roofs[dom])
     # DRAM bytes of one reverse-walk launch: ncu (dram__bytes_read.sum + write) of the
-    # current kernel on the 4-view case of profiles/render_kernels_4view_500k.md, 51.51 MB
+    # current kernel on the 4-view case (`bench.py --case render`), 51.51 MB
     # for 245.15M walked entries, scaled by entries to this launch (same scene, same
     # resolution)
     roof.update({"traffic": 51.51e6 * E_bwd / 245.15e6,
@@ -373,11 +417,18 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "flushed (256 MB write) between timed steps",
                        "tuning_fwd": rep.tuning_fwd, "tuning_bwd": rep.tuning_bwd,
-                       "graphs": "6 CUDA graphs per step (one per stage)"},
-            "views_per_s": views_per_s, "stage_ms": stage_ms, "rooflines": roofs,
+                       "graphs": "1 CUDA graph per step"},
+            "views_per_s": views_per_s, "stage_ms": stage_ms,
+            "stage_ms_note": ("diagnostic run of the same step as six stage graphs with "
+                              f"events between them ({staged_ms:.3f} ms per step); the "
+                              "rooflines use these stage times"),
+            "rooflines": roofs,
             "plain": plain_line, "speedup_vs_plain": value / plain_line["evals_per_s"],
             "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps,
+                    "note": "batch.HostStep, one graph per step: parameters, cameras and "
+                            "targets uploaded from pinned host memory, the step, and the loss, "
+                            "pose gradients and every parameter gradient read back"},
             "gpu_launches": None, "roofline": roof, "clocks": clk, "active_set": active_line,
             "mapping": mapping_line, "micro_peaks": micro, "prior": prior_line,
             "wall_s_timed": wall1 - wall0}
@@ -491,10 +542,15 @@ def micro_peaks():
         return min(t)
     it_f, it_e = 20000, 4000
     ms_f = best_ms(lambda: _abi.gevo_bench_fma(blocks, it_f, sink))
+    ms_f2 = best_ms(lambda: _abi.gevo_bench_fma2(blocks, it_f, sink))
     ms_e = best_ms(lambda: _abi.gevo_bench_ex2(blocks, it_e, sink))
+    ms_r = best_ms(lambda: _abi.gevo_bench_rcp(blocks, it_e, sink))
     return {"fp32_fma_tflops": blocks * 256 * 16 * it_f / (ms_f / 1e3) / 1e12,
+            "fp32x2_fma_tflops": blocks * 256 * 32 * it_f / (ms_f2 / 1e3) / 1e12,
             "ex2_per_s": blocks * 256 * 8 * it_e / (ms_e / 1e3),
-            "note": f"{blocks} blocks x 256 threads, 8 independent chains per thread"}
+            "rcp_per_s": blocks * 256 * 8 * it_e / (ms_r / 1e3),
+            "note": f"{blocks} blocks x 256 threads, 8 independent chains per thread "
+                    "(fp32x2: packed pairs, 16 FMAs per step)"}
 
 
 def prior_section(nb=32, H=240, W=320, steps=8):

@@ -23,6 +23,15 @@ gevo_status gevo_bench_fma(int32_t blocks, int32_t iters, float* sink, void* str
  * exponentials per thread. */
 gevo_status gevo_bench_ex2(int32_t blocks, int32_t iters, float* sink, void* stream);
 
+/* The FMA shape with the paired instruction (fma.rn.f32x2): 8 independent
+ * packed chains, 16 FMAs = 32 FLOP per thread and step.  Tells whether the
+ * paired form raises the FP32 rate or only halves the instructions issued. */
+gevo_status gevo_bench_fma2(int32_t blocks, int32_t iters, float* sink, void* stream);
+
+/* 8 independent chains x <- rcp.approx(x) + 0.5: 8 * iters reciprocals per
+ * thread (the MUFU operation of the reverse walk's transmittance recovery). */
+gevo_status gevo_bench_rcp(int32_t blocks, int32_t iters, float* sink, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -119,11 +119,12 @@ MAP = ["gevo_map_activate", "gevo_map_step", "gevo_pose_step", "gevo_prune_keep"
        "gevo_gather_rows"]
 EXPORTS = EXPORTS + MAP
 
-# Every symbol include/gevo_bench.h declares.
-BENCH = ["gevo_bench_fma", "gevo_bench_ex2"]
-EXPORTS = EXPORTS + BENCH
+# Every symbol include/gevo_bench.h declares (exported by libgevo_probes.so,
+# the measurement-only library, not by libgevo).
+BENCH = ["gevo_bench_fma", "gevo_bench_ex2", "gevo_bench_fma2", "gevo_bench_rcp"]
 
 _lib = None
+_probes = None
 
 
 def lib_path() -> str:
@@ -182,9 +183,6 @@ def load(build_if_missing: bool = True):
     L.gevo_prune_keep.argtypes = [i32, vp, vp, f32, vp, vp, vp, vp]
     L.gevo_gather_rows.argtypes = [i32, vp, vp, i32, vp, vp, vp]
     for name in MAP:
-        getattr(L, name).restype = ctypes.c_int
-    for name in BENCH:
-        getattr(L, name).argtypes = [i32, i32, vp, vp]
         getattr(L, name).restype = ctypes.c_int
     L.gevo_status_str.argtypes = [ctypes.c_int]
     L.gevo_status_str.restype = ctypes.c_char_p
@@ -513,10 +511,35 @@ def gevo_gather_rows(n_max, lst, counts, width, src, dst, stream=None):
         int(n_max), _p(lst), _p(counts), int(width), _p(src), _p(dst), _stream(stream)))
 
 
-# ---- measurement helpers (include/gevo_bench.h) -------------------------------------
+# ---- measurement helpers (include/gevo_bench.h, libgevo_probes.so) -------------------
+def load_probes():
+    """Load the measurement-only probe library (built with libgevo)."""
+    global _probes
+    if _probes is None:
+        load()
+        L = ctypes.CDLL(_build.PROBE_LIB)
+        for name in BENCH:
+            getattr(L, name).argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p]
+            getattr(L, name).restype = ctypes.c_int
+        _probes = L
+    return _probes
+
+
 def gevo_bench_fma(blocks, iters, sink, stream=None):
-    _check("gevo_bench_fma", load().gevo_bench_fma(int(blocks), int(iters), _p(sink), _stream(stream)))
+    _check("gevo_bench_fma", load_probes().gevo_bench_fma(int(blocks), int(iters), _p(sink),
+                                                          _stream(stream)))
+
+
+def gevo_bench_fma2(blocks, iters, sink, stream=None):
+    _check("gevo_bench_fma2", load_probes().gevo_bench_fma2(int(blocks), int(iters), _p(sink),
+                                                            _stream(stream)))
+
+
+def gevo_bench_rcp(blocks, iters, sink, stream=None):
+    _check("gevo_bench_rcp", load_probes().gevo_bench_rcp(int(blocks), int(iters), _p(sink),
+                                                          _stream(stream)))
 
 
 def gevo_bench_ex2(blocks, iters, sink, stream=None):
-    _check("gevo_bench_ex2", load().gevo_bench_ex2(int(blocks), int(iters), _p(sink), _stream(stream)))
+    _check("gevo_bench_ex2", load_probes().gevo_bench_ex2(int(blocks), int(iters), _p(sink), _stream(stream)))

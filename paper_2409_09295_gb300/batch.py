@@ -11,9 +11,12 @@ L1 + backward over all views at once:
     one set of ranges serve every view;
   - blending and its reverse walk run as one persistent grid over (view, tile)
     work items, heaviest tile first;
-  - every stage is captured into a CUDA graph once; replays need no host sync
+  - the whole step is captured into one CUDA graph; replays need no host sync
     (the duplicate capacity is sized by one untimed pass plus slack, and an
-    overflow is reported through the sticky error word).
+    overflow is reported through the sticky error word);
+  - `HostStep` wraps it for inputs and results in host memory: the uploads,
+    the step and the read-back of loss, pose and parameter gradients are one
+    graph too.
 `PlainReplay` is the unbatched reference point: one single-view pipeline per
 view, a host sync to size each sort, default launch shapes, no graph.
 """
@@ -70,7 +73,9 @@ class BatchedReplay:
         self.tune_log = []
         if autotune and (tuning_fwd is None or tuning_bwd is None):
             self.autotune(fwd=tuning_fwd is None, bwd=tuning_bwd is None)
-        self.graphs = None
+        self.graph = None
+        self.stage_graphs = None
+        self.bwd_graph = None
 
     # ---- stages with the chosen shapes ------------------------------------------------
     def _forward(self):
@@ -101,8 +106,8 @@ class BatchedReplay:
         self.pipe.project_bwd(self.g, self.camt, self.want_dxi)
 
     def stages(self):
-        """One step as six stages, each captured into its own graph so that every
-        stage can be timed with events between graph launches."""
+        """One step as six stages (one graph holds them all; the diagnostic
+        mode captures each on its own to time it)."""
         return [("project", self._project), ("bin_sort", self._bin_sort),
                 ("render_fwd", self._render_fwd), ("loss", self._loss),
                 ("render_bwd", self._render_bwd), ("project_bwd", self._project_bwd)]
@@ -141,8 +146,9 @@ class BatchedReplay:
         torch.cuda.synchronize()
 
     # ---- graphs ------------------------------------------------------------------------
-    def capture(self):
-        """Captures each stage into its own CUDA graph."""
+    def _warm(self):
+        """Two eager steps on a side stream: buffers and launch attributes set up
+        before any capture."""
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -150,30 +156,66 @@ class BatchedReplay:
                 self.step_eager()
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
-        self.graphs = []
+
+    def capture(self):
+        """Captures the whole step (projection, sort, blend, loss, reverse walk,
+        projection backward) into one CUDA graph."""
+        self._warm()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step_eager()
+        torch.cuda.synchronize()
+
+    def replay(self):
+        """One step: one graph launch on the current stream, no host sync."""
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def capture_stages(self):
+        """Diagnostic mode: each stage in a graph of its own, so that stages can
+        be timed with events recorded between the launches."""
+        self._warm()
+        self.stage_graphs = []
         for name, f in self.stages():
             gph = torch.cuda.CUDAGraph()
             with torch.cuda.graph(gph):
                 f()
-            self.graphs.append((name, gph))
+            self.stage_graphs.append((name, gph))
         torch.cuda.synchronize()
 
-    def replay(self, events=None, before=None):
-        """One step.  events: optional list of len(stages) + 1 timing events
-        recorded between the stage graphs on the current stream.  before:
-        optional {stage name: callable} run on the host right before that
-        stage's graph is launched, e.g. to make the current stream wait for an
-        upload the stage reads (the targets are first read by "loss")."""
-        if self.graphs is None:
-            self.capture()
-        if events is not None:
-            events[0].record()
-        for i, (name, gph) in enumerate(self.graphs):
-            if before and name in before:
-                before[name]()
+    def replay_stages(self, events):
+        """The step as its six stage graphs with events[0..6] recorded around
+        them (len(stages) + 1 events) on the current stream."""
+        if self.stage_graphs is None:
+            self.capture_stages()
+        events[0].record()
+        for i, (_, gph) in enumerate(self.stage_graphs):
             gph.replay()
-            if events is not None:
-                events[i + 1].record()
+            events[i + 1].record()
+
+    def replay_backward(self):
+        """The backward alone, from whatever upstream gradients pipe.dL_drgb
+        (and pipe.dL_ddepth) hold: record gradients zeroed, reverse walk,
+        projection backward (one graph)."""
+        if self.bwd_graph is None:
+            # warm the three calls on a side stream (not whole steps: the loss
+            # stage would overwrite the caller's upstream gradients)
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                self.pipe.grad2d_zero()
+                self._render_bwd()
+                self._project_bwd()
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            self.bwd_graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.bwd_graph):
+                self.pipe.grad2d_zero()
+                self._render_bwd()
+                self._project_bwd()
+            torch.cuda.synchronize()
+        self.bwd_graph.replay()
 
     def eval_counts(self, blended=False):
         """(E_fwd, E_bwd): list entries examined by the blend (including skips and
@@ -189,6 +231,84 @@ class BatchedReplay:
         torch.cuda.synchronize()
         out = (int(p.n_eval.sum(dtype=torch.int64)), int(p.n_contrib.sum(dtype=torch.int64)))
         return out + (int(nb.sum(dtype=torch.int64)),) if blended else out
+
+
+class HostStep:
+    """End-to-end step for a caller whose Gaussians, cameras and targets live in
+    host memory: fill `host_in` (parameters and cameras) and `host_targets`
+    (rendered target RGB and depth) -- pinned buffers owned by this object --
+    call step(), synchronise, and read `host_out` (loss per view, dL/dxi per
+    view, and the parameter gradients).
+
+    One graph per step: the parameters and cameras are copied up first (the
+    projection reads them); the targets, first read by the loss, are copied up
+    on a second stream while projection, sort and blend run; after the
+    projection backward the loss, the pose gradients and the 59 N parameter
+    gradients are copied back."""
+
+    def __init__(self, rep: BatchedReplay):
+        self.rep = rep
+        p = rep.pipe
+        keys = [k for k in ("means", "scales", "quats", "opacities", "sh", "rgb") if k in rep.g]
+        self.host_in = {k: torch.empty(rep.g[k].shape, dtype=torch.float32).pin_memory()
+                        for k in keys}
+        self.host_in["cams"] = torch.empty(rep.camt.shape, dtype=torch.float32).pin_memory()
+        self.host_targets = {"rgb": torch.empty(rep.target_rgb.shape).pin_memory()}
+        if rep.target_depth is not None:
+            self.host_targets["depth"] = torch.empty(rep.target_depth.shape).pin_memory()
+        self.host_out = {"loss": torch.empty(p.loss.shape).pin_memory(),
+                         "dxi": torch.empty(p.dxi.shape).pin_memory()}
+        for k, v in p.grads.items():
+            self.host_out[k] = torch.empty(v.shape).pin_memory()
+        self.h2d_bytes = sum(t.numel() * 4 for t in self.host_in.values()) + \
+            sum(t.numel() * 4 for t in self.host_targets.values())
+        self.d2h_bytes = sum(t.numel() * 4 for t in self.host_out.values())
+        for k, t in self.host_in.items():
+            t.copy_(rep.camt if k == "cams" else rep.g[k])
+        self.host_targets["rgb"].copy_(rep.target_rgb)
+        if "depth" in self.host_targets:
+            self.host_targets["depth"].copy_(rep.target_depth)
+        self.graph = None
+
+    def _body(self):
+        rep, p = self.rep, self.rep.pipe
+        main = torch.cuda.current_stream()
+        for k, t in self.host_in.items():
+            (rep.camt if k == "cams" else rep.g[k]).copy_(t, non_blocking=True)
+        side = self.side
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            rep.target_rgb.copy_(self.host_targets["rgb"], non_blocking=True)
+            if "depth" in self.host_targets:
+                rep.target_depth.copy_(self.host_targets["depth"], non_blocking=True)
+        rep._project()
+        rep._bin_sort()
+        rep._render_fwd()
+        main.wait_stream(side)
+        rep._loss()
+        rep._render_bwd()
+        rep._project_bwd()
+        self.host_out["loss"].copy_(p.loss, non_blocking=True)
+        self.host_out["dxi"].copy_(p.dxi, non_blocking=True)
+        for k, v in p.grads.items():
+            self.host_out[k].copy_(v, non_blocking=True)
+
+    def capture(self):
+        self.side = torch.cuda.Stream()
+        self.rep._warm()
+        for _ in range(2):
+            self._body()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._body()
+        torch.cuda.synchronize()
+
+    def step(self):
+        """Launches the step; host_out is valid after the current stream syncs."""
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
 
 
 class PlainReplay:

@@ -3,6 +3,9 @@
 Each translation unit is compiled in parallel, then linked with -shared; the
 result lands next to this file and is git-ignored.  No torch extension
 machinery is involved: the library exports plain `extern "C"` symbols.
+A second, measurement-only library, libgevo_probes.so (include/gevo_bench.h:
+FP32 FMA and ex2 throughput probes that bench.py uses to check the derived
+peaks), is built the same way and is not part of libgevo.
 """
 from __future__ import annotations
 
@@ -17,7 +20,9 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgevo.so")
-SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "loss.cu", "active.cu", "optim.cu", "peaks.cu", "gemm_tc.cu", "unet.cu", "init.cu"]
+SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "loss.cu", "active.cu", "optim.cu", "gemm_tc.cu", "unet.cu", "init.cu"]
+PROBE_LIB = os.path.join(HERE, "libgevo_probes.so")
+PROBE_SOURCES = ["peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
               "--expt-relaxed-constexpr"]
@@ -35,10 +40,11 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    return os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps()
+    return all(os.path.exists(p) and os.path.getmtime(p) >= _deps() for p in (LIB, PROBE_LIB))
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """Builds both libraries (if stale) and returns the path of libgevo.so."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
@@ -54,14 +60,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             print(r.stdout, r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    def link(objs, out):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out)
+
+    srcs = SOURCES + PROBE_SOURCES
+    with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        objs = dict(zip(srcs, ex.map(compile_one, srcs)))
+    link([objs[s] for s in SOURCES], LIB)
+    link([objs[s] for s in PROBE_SOURCES], PROBE_LIB)
     return LIB
 
 

@@ -225,6 +225,24 @@ class Pipeline:
     def last_error(self) -> int:
         return abi.gevo_last_error(self.ws)
 
+    # ---- what a backward pass reads from its forward --------------------------------
+    def save_state(self) -> dict:
+        """Copies of the buffers the reverse walk and the projection backward read
+        from the forward pass: projection records, sorted values, tile ranges,
+        T_final and n_contrib (alpha is not kept: the walk recomputes it).  The
+        pipeline's own buffers stay where they are (captured graphs keep their
+        addresses); a later forward overwrites them, not the copies."""
+        return dict(proj={k: v.clone() for k, v in self.proj.items()}, vals=self.vals.clone(),
+                    ranges=self.ranges.clone(), T_final=self.T_final.clone(),
+                    n_contrib=self.n_contrib.clone())
+
+    def swap_state(self, state: dict) -> dict:
+        """Installs saved forward buffers and returns the ones they replace."""
+        old = {k: getattr(self, k) for k in state}
+        for k, v in state.items():
+            setattr(self, k, v)
+        return old
+
     def ensure_capacity(self, g, cams, slack=1.25):
         """Host-synchronising sizing pass: project + count, then grow the duplicate
         capacity if needed.  Returns the duplicate count D."""
@@ -243,8 +261,14 @@ class GevoRasterize(torch.autograd.Function):
     colours: rgb [N,3] or SH [N,K,3] (as the pipeline was built).  twist: [V,6]
     zeros standing for a left se(3) perturbation of each view's pose; its
     gradient is dL/dxi.  Outputs are the planar view-major buffers described in
-    include/gevo.h (use Pipeline.view_rgb / view_plane to slice views).  The
-    backward recomputes alpha from the kept n_contrib and T_final."""
+    include/gevo.h (use Pipeline.view_rgb / view_plane to slice views).
+
+    Each call keeps its own copy of what the backward reads (projection records,
+    sorted values, ranges, T_final and n_contrib; not alpha, which the backward
+    recomputes), so several forwards through one pipeline may precede their
+    backwards: E_pc of Eq. 6 renders the current and the past views before one
+    backward.  The inputs are saved for backward, so modifying them in place
+    before the backward raises torch's usual error."""
 
     @staticmethod
     def forward(ctx, means, scales, quats, opacities, colours, twist, pipe, cams, bg):
@@ -253,16 +277,24 @@ class GevoRasterize(torch.autograd.Function):
                  sh_degree=pipe.sh_degree)
         g["rgb" if pipe.colour == "rgb" else "sh"] = colours.detach().contiguous()
         pipe.forward(g, cams, bg)
-        ctx.pipe, ctx.g, ctx.cams, ctx.bg = pipe, g, cams, bg
+        ctx.save_for_backward(means, scales, quats, opacities, colours)
+        ctx.pipe, ctx.g, ctx.cams, ctx.bg = pipe, g, cams.clone(), bg
+        ctx.state = pipe.save_state()
         return pipe.rgb.clone(), pipe.depth.clone(), pipe.T_final.clone()
 
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_T):
+        ctx.saved_tensors   # raises if an input was modified in place since the forward
         pipe = ctx.pipe
         z = lambda t, like: (t.contiguous() if t is not None else torch.zeros_like(like))
-        pipe.render_bwd(z(g_rgb, pipe.rgb), z(g_depth, pipe.depth),
-                        g_T.contiguous() if g_T is not None else None, ctx.bg)
-        pipe.project_bwd(ctx.g, ctx.cams, want_dxi=True)
+        keep = pipe.swap_state(ctx.state)
+        try:
+            pipe.render_bwd(z(g_rgb, pipe.rgb), z(g_depth, pipe.depth),
+                            g_T.contiguous() if g_T is not None else None, ctx.bg)
+            pipe.project_bwd(ctx.g, ctx.cams, want_dxi=True)
+        finally:
+            pipe.swap_state(keep)
+        ctx.state = None
         gr = pipe.grads
         col = gr["rgb"] if pipe.colour == "rgb" else gr["sh"]
         return (gr["means"].clone(), gr["scales"].clone(), gr["quats"].clone(),
