@@ -1,8 +1,7 @@
 """Parity of the active-set path of the global stage (Section III-B2) with the
 FP64 oracle: the per-pixel error, the per-Gaussian rendering error E_k(g) of
 Eq. 5 fused into the reverse walk, the active set (bit-exact), and the masked
-reverse walk and projection backward (gradient tolerance of the design notes:
-relative L2 <= 1e-3 per tensor, |g - ref| <= 1e-3 |ref| + 1e-3 rms(ref) per
+reverse walk and projection backward (gradient tolerance: relative L2 <= 1e-3 per tensor, |g - ref| <= 1e-3 |ref| + 1e-3 rms(ref) per
 element; rows of inactive Gaussians untouched, bit for bit).
 
 E_k(g) = sum_u w(g, u) e(u) is a weighted sum of exactly the kind the colour

@@ -1,19 +1,22 @@
 """Parity at the benchmark's full size and in the launch configuration bench.py
 times: 500k Gaussians (SH 3), 16 uneven views (12 x 640x480, 4 x 320x240) in one
-batched layout, autotuned shapes, every stage replayed from its captured CUDA
-graph.  The FP64 oracle renders two of the views (one of each size) in full and
-back-propagates seeded upstream gradients through them; the GPU's images,
-contributor counts, record gradients, parameter gradients and pose gradients of
-those views must agree with it within the tolerances of the smaller parity tests
-(images: 2e-4 maximum, 1e-6 median on pixels no fragile decision touches;
-gradients: relative L2 <= 1e-3 and |g - ref| <= 1e-3 |ref| + 1e-3 rms(ref))."""
+batched layout, autotuned shapes, the whole step replayed from its captured CUDA
+graph.  The FP64 oracle renders all 16 views in full (split across host
+threads) and back-propagates seeded upstream gradients through every one of
+them; the GPU's images, contributor counts, record gradients of every view,
+parameter gradients summed over the 16 views (the FP32 atomics of every view
+land in the same rows) and every view's pose gradient must agree with it within
+the tolerances of the smaller parity tests (images: 2e-4 maximum, 1e-6 median
+on pixels no fragile decision touches; gradients: relative L2 <= 1e-3 and
+|g - ref| <= 1e-3 |ref| + 1e-3 rms(ref), rows of Gaussians with a fragile
+projection decision in the relative L2 check only)."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
-import oracle  # noqa: E402
-from gpu_helpers import grad_close  # noqa: E402
+import oracle_par  # noqa: E402
+from gpu_helpers import check_view_images, excluded_pixels, grad_close  # noqa: E402
 from paper_2409_09295_gb300 import scenes  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -24,17 +27,16 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2409_09295_gb300 import raster  # noqa: E402
 from paper_2409_09295_gb300.batch import BatchedReplay  # noqa: E402
 
-SAMPLED = (0, 12)
-
 
 def _np(t):
     return t.detach().cpu().numpy()
 
 
-def test_benchmark_workload_sampled_views_match_oracle():
+def test_benchmark_workload_all_views_match_oracle():
     w = scenes.workload(2)
     scene, cams = w["scene"], w["cams"]
     n = scene["means"].shape[0]
+    V = len(cams)
     g = raster.gaussians_to_device(scene)
     P_all = sum(c["W"] * c["H"] for c in cams)
     zr = torch.zeros(3 * P_all, device="cuda")
@@ -46,44 +48,24 @@ def test_benchmark_workload_sampled_views_match_oracle():
     pipe = rep.pipe
     assert pipe.last_error() == 0
 
-    cams2 = [cams[v] for v in SAMPLED]
-    outs, projs, b = oracle.render_views(scene, cams2)
-    masks = []
-    for k, v in enumerate(SAMPLED):
-        W, H = cams[v]["W"], cams[v]["H"]
-        m = outs[k]["fragile"] != 0
-        p = projs[k]
-        rad_g = _np(pipe.proj["radius"])[v * n:(v + 1) * n]
-        tt_g = _np(pipe.proj["tiles_touched"])[v * n:(v + 1) * n]
-        tx, ty = (W + 15) // 16, (H + 15) // 16
-        differs = (p["fragile"] != 0) & ((rad_g != p["radius"]) | (tt_g != p["tiles_touched"]))
-        for i in np.nonzero(differs)[0]:
-            r = max(int(p["radius"][i]), int(rad_g[i]), 1)
-            rc = oracle.rect_f32(p["xy"][i, 0], p["xy"][i, 1], r, tx, ty)
-            m[rc[1] * 16:rc[3] * 16, rc[0] * 16:rc[2] * 16] = True
-        masks.append(m)
-        ok = ~m
-        assert ok.mean() > 0.9, ok.mean()
-        rgb = _np(pipe.view_rgb(pipe.rgb, v))
-        err = np.abs(rgb - outs[k]["rgb"])[:, ok]
-        assert err.max() <= 2e-4, err.max()
-        assert np.median(err) <= 1e-6
-        np.testing.assert_array_equal(_np(pipe.view_plane(pipe.n_contrib, v))[ok], outs[k]["n_contrib"][ok])
-        np.testing.assert_allclose(_np(pipe.view_plane(pipe.T_final, v))[ok], outs[k]["T"][ok], atol=2e-4)
+    outs, projs, b = oracle_par.render_views(scene, cams)
+    assert int(pipe.n_dup.item()) > 0.99 * b["n_dup"]
+    masks = excluded_pixels(pipe, n, cams, list(range(V)), outs, projs)
+    for v in range(V):
+        check_view_images(pipe, v, outs[v], masks[v])
 
-    # seeded upstream gradients on the two views (zero elsewhere and on masked
-    # pixels), then the captured reverse-walk and projection-backward graphs
+    # seeded upstream gradients on every view (zero on excluded pixels), then
+    # the reverse-walk and projection-backward stages of the captured step
     rs = np.random.default_rng(29)
     gC = np.zeros(3 * P_all, np.float32)
     gD = np.zeros(P_all, np.float32)
     gCs, gDs = [], []
-    for k, v in enumerate(SAMPLED):
-        W, H = cams[v]["W"], cams[v]["H"]
-        c = rs.normal(size=(3, H, W)) * 1e-3
-        d = rs.normal(size=(H, W)) * 1e-4
-        c[:, masks[k]] = 0
-        d[masks[k]] = 0
-        c, d = c.astype(np.float32), d.astype(np.float32)
+    for v, cam in enumerate(cams):
+        W, H = cam["W"], cam["H"]
+        c = (rs.normal(size=(3, H, W)) * 1e-3).astype(np.float32)
+        d = (rs.normal(size=(H, W)) * 1e-4).astype(np.float32)
+        c[:, masks[v]] = 0
+        d[masks[v]] = 0
         p0, p1 = pipe.pix_base[v], pipe.pix_base[v + 1]
         gC[3 * p0:3 * p1] = c.reshape(-1)
         gD[p0:p1] = d.reshape(-1)
@@ -91,25 +73,22 @@ def test_benchmark_workload_sampled_views_match_oracle():
         gDs.append(d.astype(np.float64))
     pipe.dL_drgb.copy_(torch.from_numpy(gC).cuda())
     pipe.dL_ddepth.copy_(torch.from_numpy(gD).cuda())
-    pipe.grad2d_zero()
-    for name, gph in rep.graphs:
-        if name in ("render_bwd", "project_bwd"):
-            gph.replay()
+    rep.replay_backward()
     torch.cuda.synchronize()
-    acc, dxi, g2ds = oracle.backward_views(scene, cams2, projs, b, gCs, gDs, None)
-    for k, v in enumerate(SAMPLED):
-        vis = projs[k]["radius"] > 0
+    acc, dxi, g2ds = oracle_par.backward_views(scene, cams, projs, b, gCs, gDs, None)
+    for v in range(V):
+        vis = projs[v]["radius"] > 0
         sl = slice(v * n, (v + 1) * n)
         gxy = _np(pipe.grad2d["xy"])[sl][vis]
         gco = _np(pipe.grad2d["conic_opacity"])[sl][vis]
         grz = _np(pipe.grad2d["rgb_depth"])[sl][vis]
-        grad_close(gxy, g2ds[k]["xy"][vis], f"view {v} dxy")
-        grad_close(gco[:, :3], g2ds[k]["conic"][vis], f"view {v} dconic")
-        grad_close(gco[:, 3], g2ds[k]["opacity"][vis], f"view {v} dopacity")
-        grad_close(grz[:, :3], g2ds[k]["rgb"][vis], f"view {v} drgb")
-        grad_close(grz[:, 3], g2ds[k]["depth"][vis], f"view {v} ddepth")
+        grad_close(gxy, g2ds[v]["xy"][vis], f"view {v} dxy")
+        grad_close(gco[:, :3], g2ds[v]["conic"][vis], f"view {v} dconic")
+        grad_close(gco[:, 3], g2ds[v]["opacity"][vis], f"view {v} dopacity")
+        grad_close(grz[:, :3], g2ds[v]["rgb"][vis], f"view {v} drgb")
+        grad_close(grz[:, 3], g2ds[v]["depth"][vis], f"view {v} ddepth")
+    frag = np.any([p["fragile"] != 0 for p in projs], axis=0)
     for key in acc:
-        grad_close(_np(pipe.grads[key]), acc[key], key)
-    grad_close(_np(pipe.dxi)[list(SAMPLED)], dxi, "dxi")
-    others = [v for v in range(len(cams)) if v not in SAMPLED]
-    assert (_np(pipe.dxi)[others] == 0).all()
+        grad_close(_np(pipe.grads[key]), acc[key], key, rows_skip=frag)
+    for v in range(V):
+        grad_close(_np(pipe.dxi)[v], dxi[v], f"dxi view {v}")

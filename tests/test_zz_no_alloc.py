@@ -9,6 +9,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from paper_2409_09295_gb300 import scenes  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +50,12 @@ def test_noalloc_sort_matches_workspace_sort_on_consecutive_calls():
         assert torch.equal(ranges, pipe.ranges)
         assert torch.equal(keys[:D], pipe.keys[:D])
         assert torch.equal(vals[:D], pipe.vals[:D])
+        # and, since it runs other binning kernels, bit for bit against the oracle
+        ref = oracle.bin_f32(sizes, rec["xy"], rec["radius"], rec["depth"])
+        assert ref["n_dup"] == D
+        np.testing.assert_array_equal(ranges.cpu().numpy().view(np.uint32), ref["ranges"])
+        np.testing.assert_array_equal(keys[:D].cpu().numpy().view(np.uint64), ref["keys"])
+        np.testing.assert_array_equal(vals[:D].cpu().numpy().view(np.uint32), ref["vals"])
 
 
 def test_noalloc_sort_reports_overflow_through_the_count():
