@@ -20,6 +20,8 @@
 // skip / clamp / stop decisions.
 #include "gevo_internal.cuh"
 
+#include <type_traits>
+
 namespace gevo {
 
 
@@ -134,6 +136,106 @@ __device__ __forceinline__ void tile_of(const gevo_layout& L, int tile, int& v, 
     y0 = (local / tx) * kTile;
 }
 
+// One spelling for scalar and paired FP32 arithmetic, so that a kernel body
+// written over V = float (one pixel) or V = f2 (two pixels of a column, the
+// paired f32x2 instructions) computes exactly the same binary32 results.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ f2 vfma(f2 a, f2 b, f2 c) { return f2_fma(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ f2 vmul(f2 a, f2 b) { return f2_mul(a, b); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ f2 vadd(f2 a, f2 b) { return f2_add(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ f2 vsub(f2 a, f2 b) { return f2_sub(a, b); }
+template <class V> __device__ __forceinline__ V vsplat(float a);
+template <> __device__ __forceinline__ float vsplat<float>(float a) { return a; }
+template <> __device__ __forceinline__ f2 vsplat<f2>(float a) { return f2_splat(a); }
+__device__ __forceinline__ float vlane(float x, int) { return x; }
+__device__ __forceinline__ float vlane(f2 x, int i) { return i ? f2_hi(x) : f2_lo(x); }
+template <class V> __device__ __forceinline__ V vpack(const float* a);
+template <> __device__ __forceinline__ float vpack<float>(const float* a) { return a[0]; }
+template <> __device__ __forceinline__ f2 vpack<f2>(const float* a) { return f2_make(a[0], a[1]); }
+template <class V> struct VW { static constexpr int n = 1; };
+template <> struct VW<f2> { static constexpr int n = 2; };
+
+// Skip test of one pixel-entry: with the log2 exponent p2 of the Gaussian
+// falloff and l = log2(1 / (255 o)), an entry is skipped unless l <= p2 <= 0
+// (p2 > 0 is skipped by definition; p2 < l means alpha < 1/255).  The two
+// bounds are one window test |p2 + m| <= m with m = -l / 2 =
+// log2(255 o) / 2 stored per staged entry (m < 0 when o < 1/255: nothing
+// passes).  The same window test decides the reverse walk's entries.
+__device__ __forceinline__ bool window_ok(float d, float m)
+{
+    return fabsf(d) <= m;
+}
+
+// A staged list entry, every value held twice (as a pair), so that the walk
+// loads its operands straight into paired registers: mean (x, y), pre-scaled
+// conic (a', b', c'), opacity o, m = log2(255 o) / 2 of the window test, and
+// colour and depth.
+struct Staged {
+    ulonglong2 p0;   // (x, x) (y, y)
+    ulonglong2 p1;   // (a', a') (b', b')
+    ulonglong2 p2;   // (c', c') (o, o)
+    ulonglong2 p3;   // (m, m) (r, r)
+    ulonglong2 p4;   // (g, g) (b, b)
+    unsigned long long p5;   // (z, z)
+};
+
+__device__ __forceinline__ ulonglong2 pair2(float a, float b)
+{
+    return make_ulonglong2(f2_splat(a).v, f2_splat(b).v);
+}
+
+__device__ __forceinline__ void stage_entry(Staged& e, float2 m, float4 c, float4 r)
+{
+    const float4 cs = prescale(c);
+    e.p0 = pair2(m.x, m.y);
+    e.p1 = pair2(cs.x, cs.y);
+    e.p2 = pair2(cs.z, cs.w);
+    e.p3 = pair2(0.5f * __log2f(255.f * c.w), r.x);
+    e.p4 = pair2(r.y, r.z);
+    e.p5 = f2_splat(r.w).v;
+}
+
+template <class V> __device__ __forceinline__ V vget(unsigned long long x);
+template <> __device__ __forceinline__ float vget<float>(unsigned long long x) { return f2_lo(f2{x}); }
+template <> __device__ __forceinline__ f2 vget<f2>(unsigned long long x) { return f2{x}; }
+
+// The operands of one staged entry at a thread's column px (pxv = px as V).
+template <class V>
+struct EntryOps {
+    V my, cz, cx, cy, cw, mw, rx, ry, rb, rw, dx;
+    float dxs, a, b, c, o, m;
+};
+
+template <class V>
+__device__ __forceinline__ EntryOps<V> entry_ops(const Staged& e, V pxv)
+{
+    const ulonglong2 p0 = e.p0, p1 = e.p1, p2 = e.p2, p3 = e.p3, p4 = e.p4;
+    const unsigned long long p5 = e.p5;
+    EntryOps<V> q;
+    const V mx = vget<V>(p0.x), aa = vget<V>(p1.x), bb = vget<V>(p1.y);
+    q.my = vget<V>(p0.y);
+    q.dx = vsub(mx, pxv);
+    q.cx = vmul(vmul(aa, q.dx), q.dx);   // a' dx^2
+    q.cy = vmul(bb, q.dx);               // b' dx
+    q.cz = vget<V>(p2.x);
+    q.cw = vget<V>(p2.y);
+    q.mw = vget<V>(p3.x);
+    q.rx = vget<V>(p3.y);
+    q.ry = vget<V>(p4.x);
+    q.rb = vget<V>(p4.y);
+    q.rw = vget<V>(p5);
+    q.dxs = vlane(q.dx, 0);
+    q.a = f2_lo(f2{p1.x});
+    q.b = f2_lo(f2{p1.y});
+    q.c = f2_lo(f2{p2.x});
+    q.o = f2_lo(f2{p2.y});
+    q.m = f2_lo(f2{p3.x});
+    return q;
+}
+
 // ACT: also record, per pixel, where the reverse walk of an active-set
 // backward has to start: 1 + the list position of the last blended entry of an
 // active Gaussian (0 if none), the transmittance right after it, and the colour
@@ -142,6 +244,14 @@ __device__ __forceinline__ void tile_of(const gevo_layout& L, int tile, int& v, 
 // needs no difference of two sums; the bookkeeping runs only at active
 // entries (a warp-uniform branch), and the pixel colour is the sum of the two
 // parts.
+//
+// Per pixel-entry the arithmetic runs on pairs of pixels (f32x2) where a thread
+// has two or more: the exponent (2 FMAs), the window offset, o G, the
+// candidate T (1 - alpha), and the branch-free blend bookkeeping: with
+// b = -alpha where the entry blends at the pixel and 0 elsewhere,
+//   -C <- -C + (b T) c (colour and depth summed negated, b T = -alpha T)
+//   T <- T + b T       (blended: T (1 - alpha); else unchanged)
+// The decisions themselves (window test, stop, done) stay per pixel.
 template <int PPT, bool COUNT, bool ACT>
 __global__ void __launch_bounds__(256 / PPT)
 k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
@@ -154,14 +264,15 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
              float* __restrict__ act_T, float4* __restrict__ act_rest,
              uint32_t* __restrict__ out_nb)
 {
+    using V = typename std::conditional<(PPT >= 2), f2, float>::type;
+    constexpr int W2 = VW<V>::n;
+    constexpr int NV = PPT / W2;
     constexpr int NT = 256 / PPT;
     // staging batch: one record per thread (measured on the benchmark: 64
     // entries at 64 threads beat 32, 96, 128 and 256 -- a block leaves its tile
     // as soon as all its pixels stopped, which happens early in most lists)
     constexpr int kBatch = NT;
-    __shared__ float2 s_xy[kBatch];
-    __shared__ float4 s_co[kBatch];
-    __shared__ float4 s_rz[kBatch];
+    __shared__ Staged s_e[kBatch];
     __shared__ uint32_t s_mask[kBatch];
     __shared__ uint32_t s_act[ACT ? kBatch : 1];
     __shared__ uint16_t s_list[NT / 32][kBatch];
@@ -191,18 +302,27 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
         const uint2 rg = ranges[tile];
         const size_t vbase = (size_t)v * n;
 
-        float T[PPT], C0[PPT], C1[PPT], C2[PPT], Dp[PPT];
-        float B0[PPT], B1[PPT], B2[PPT], BD[PPT], Ta[PPT];   // colour, depth through the last active entry
+        // per pixel pair: T, Tf, negated colour / depth sums; pixel rows
+        V T[NV], Cn0[NV], Cn1[NV], Cn2[NV], Dn[NV], pyv[NV];
+        float B0[PPT], B1[PPT], B2[PPT], BD[PPT], Ta[PPT];   // (negated) sums through the last active entry
         uint32_t last[PPT], cnt[PPT], la[PPT], nbl[PPT];
         bool done[PPT];
 #pragma unroll
+        for (int h = 0; h < NV; h++) {
+            float yy[W2];
+#pragma unroll
+            for (int i = 0; i < W2; i++) yy[i] = (float)(py0 + h * W2 + i);
+            T[h] = vsplat<V>(1.f);
+            pyv[h] = vpack<V>(yy);
+            Cn0[h] = Cn1[h] = Cn2[h] = Dn[h] = vsplat<V>(0.f);
+        }
+#pragma unroll
         for (int k = 0; k < PPT; k++) {
-            T[k] = 1.f; C0[k] = C1[k] = C2[k] = Dp[k] = 0.f;
             last[k] = 0u; cnt[k] = 0u; nbl[k] = 0u;
-            done[k] = !(px < W && py0 + k < H);
+            done[k] = !(px < W && py0 + k < H);   // outside the image: nothing to blend
             if (ACT) { B0[k] = B1[k] = B2[k] = BD[k] = 0.f; Ta[k] = 1.f; la[k] = 0u; }
         }
-        const float fpx = (float)px;
+        const V pxv = vsplat<V>((float)px);
 
         for (uint32_t b = rg.x; b < rg.y; b += kBatch) {
             bool mine = true;
@@ -215,9 +335,7 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 const size_t id = vbase + gid;
                 const float2 m = xy[id];
                 const float4 c = co[id];
-                s_xy[j] = m;
-                s_co[j] = prescale(c);
-                s_rz[j] = rz[id];
+                stage_entry(s_e[j], m, c, rz[id]);
                 s_mask[j] = strip_mask(m, c, (float)x0, (float)y0, NT / 32, WROWS);
                 if (ACT) s_act[j] = (__ldg(active + (gid >> 5)) >> (gid & 31)) & 1u;
             }
@@ -243,86 +361,100 @@ k_render_fwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 for (int k = 0; k < PPT; k++) all = all && done[k];
                 if (all) break;
                 const int j = s_list[warp][q];
-                const float2 m = s_xy[j];
-                const float4 c = s_co[j];
-                const float4 r = s_rz[j];
-                const float dx = __fsub_rn(m.x, fpx);
                 const uint32_t pos1 = b + j - rg.x + 1;
-                // the PPT pixels are independent: evaluate them branch-free so
-                // their dependency chains interleave
-                float p2[PPT], G[PPT];
-                const float2 col = power2_col(c, dx);
+                const EntryOps<V> e = entry_ops<V>(s_e[j], pxv);
 #pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    const float dy = __fsub_rn(m.y, (float)(py0 + k));
-                    p2[k] = power2_at(c, col, dy);
-                }
+                for (int h = 0; h < NV; h++) {
+                    const V dy = vsub(e.my, pyv[h]);
+                    const V p2 = vfma(vfma(e.cz, dy, e.cy), dy, e.cx);
+                    const V dwin = vadd(p2, e.mw);
+                    float g[W2];
 #pragma unroll
-                for (int k = 0; k < PPT; k++) G[k] = ex2_approx(p2[k]);
+                    for (int i = 0; i < W2; i++) g[i] = ex2_approx(vlane(p2, i));
+                    const V og = vmul(e.cw, vpack<V>(g));
+                    float na[W2], bn[W2];
 #pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(c.w, G[k]));
-                    const bool ok = !done[k] && !(p2[k] > 0.f) && !(alpha < kAlphaMin);
-                    const float Tn = __fmaf_rn(-alpha, T[k], T[k]);   // T (1 - alpha), one rounding
-                    const bool stop = ok && Tn < kTStop;
-                    const bool bl = ok && !stop;
-                    done[k] = done[k] || stop;
-                    // entries examined = the stopping entry's position (entries
-                    // past the stop, masked or not, are not examined)
-                    if (COUNT && stop) cnt[k] = pos1;
-                    const float w = bl ? __fmul_rn(alpha, T[k]) : 0.f;
-                    C0[k] = __fmaf_rn(w, r.x, C0[k]);
-                    C1[k] = __fmaf_rn(w, r.y, C1[k]);
-                    C2[k] = __fmaf_rn(w, r.z, C2[k]);
-                    Dp[k] = __fmaf_rn(w, r.w, Dp[k]);
-                    T[k] = bl ? Tn : T[k];
-                    last[k] = bl ? pos1 : last[k];
-                    if (COUNT) nbl[k] += bl ? 1u : 0u;
+                    for (int i = 0; i < W2; i++) na[i] = fmaxf(-kAlphaMax, -vlane(og, i));   // -alpha
+                    const V tn = vfma(vpack<V>(na), T[h], T[h]);                             // T (1 - alpha)
+#pragma unroll
+                    for (int i = 0; i < W2; i++) {
+                        const int k = h * W2 + i;
+                        const bool ok = !done[k] && window_ok(vlane(dwin, i), e.m);
+                        const bool bl = ok && !(vlane(tn, i) < kTStop);
+                        const bool stop = ok && !bl;
+                        if (COUNT && stop) cnt[k] = pos1;
+                        if (COUNT) nbl[k] += bl ? 1u : 0u;
+                        done[k] = done[k] || stop;
+                        bn[i] = bl ? na[i] : 0.f;
+                        last[k] = bl ? pos1 : last[k];
+                    }
+                    const V bnv = vpack<V>(bn);            // -alpha where blended, else 0
+                    const V nw = vmul(bnv, T[h]);          // -alpha T
+                    T[h] = vfma(bnv, T[h], T[h]);          // blended: T (1 - alpha), else T
+                    Cn0[h] = vfma(nw, e.rx, Cn0[h]);
+                    Cn1[h] = vfma(nw, e.ry, Cn1[h]);
+                    Cn2[h] = vfma(nw, e.rb, Cn2[h]);
+                    Dn[h] = vfma(nw, e.rw, Dn[h]);
                 }
                 if (ACT && s_act[j]) {
                     // an active entry: move the part since the previous one
-                    // into the part up to here (C holds the part since)
+                    // into the part up to here (Cn holds the part since)
 #pragma unroll
-                    for (int k = 0; k < PPT; k++) {
-                        const bool at = last[k] == pos1;   // blended right here
-                        B0[k] = at ? __fadd_rn(B0[k], C0[k]) : B0[k];
-                        B1[k] = at ? __fadd_rn(B1[k], C1[k]) : B1[k];
-                        B2[k] = at ? __fadd_rn(B2[k], C2[k]) : B2[k];
-                        BD[k] = at ? __fadd_rn(BD[k], Dp[k]) : BD[k];
-                        C0[k] = at ? 0.f : C0[k];
-                        C1[k] = at ? 0.f : C1[k];
-                        C2[k] = at ? 0.f : C2[k];
-                        Dp[k] = at ? 0.f : Dp[k];
-                        Ta[k] = at ? T[k] : Ta[k];
-                        la[k] = at ? pos1 : la[k];
+                    for (int h = 0; h < NV; h++) {
+                        float c0[W2], c1[W2], c2[W2], dd[W2];
+#pragma unroll
+                        for (int i = 0; i < W2; i++) {
+                            const int k = h * W2 + i;
+                            const bool at = last[k] == pos1;   // blended right here
+                            const float x0_ = vlane(Cn0[h], i), x1_ = vlane(Cn1[h], i),
+                                        x2_ = vlane(Cn2[h], i), xd = vlane(Dn[h], i);
+                            B0[k] = at ? __fadd_rn(B0[k], x0_) : B0[k];
+                            B1[k] = at ? __fadd_rn(B1[k], x1_) : B1[k];
+                            B2[k] = at ? __fadd_rn(B2[k], x2_) : B2[k];
+                            BD[k] = at ? __fadd_rn(BD[k], xd) : BD[k];
+                            c0[i] = at ? 0.f : x0_;
+                            c1[i] = at ? 0.f : x1_;
+                            c2[i] = at ? 0.f : x2_;
+                            dd[i] = at ? 0.f : xd;
+                            Ta[k] = at ? vlane(T[h], i) : Ta[k];
+                            la[k] = at ? pos1 : la[k];
+                        }
+                        Cn0[h] = vpack<V>(c0);
+                        Cn1[h] = vpack<V>(c1);
+                        Cn2[h] = vpack<V>(c2);
+                        Dn[h] = vpack<V>(dd);
                     }
                 }
             }
         }
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
+            const int h = k / W2, i = k % W2;
             const int py = py0 + k;
             if (px < W && py < H) {
                 const size_t pix = (size_t)py * W + px;
                 const size_t gp = (size_t)L.pix_base[v] + pix;
+                const float Tk = vlane(T[h], i);
+                float c0 = -vlane(Cn0[h], i), c1 = -vlane(Cn1[h], i), c2 = -vlane(Cn2[h], i),
+                      dp = -vlane(Dn[h], i);
                 if (ACT) {
-                    // C, Dp hold the part behind the last active entry
+                    // c0..dp hold the part behind the last active entry
                     act_last[gp] = la[k];
                     act_T[gp] = Ta[k];
-                    act_rest[gp] = la[k] ? make_float4(__fmaf_rn(T[k], bg0, C0[k]), __fmaf_rn(T[k], bg1, C1[k]),
-                                                       __fmaf_rn(T[k], bg2, C2[k]), Dp[k])
+                    act_rest[gp] = la[k] ? make_float4(__fmaf_rn(Tk, bg0, c0), __fmaf_rn(Tk, bg1, c1),
+                                                       __fmaf_rn(Tk, bg2, c2), dp)
                                          : make_float4(0.f, 0.f, 0.f, 0.f);
-                    C0[k] = __fadd_rn(B0[k], C0[k]);
-                    C1[k] = __fadd_rn(B1[k], C1[k]);
-                    C2[k] = __fadd_rn(B2[k], C2[k]);
-                    Dp[k] = __fadd_rn(BD[k], Dp[k]);
+                    c0 = __fsub_rn(c0, B0[k]);
+                    c1 = __fsub_rn(c1, B1[k]);
+                    c2 = __fsub_rn(c2, B2[k]);
+                    dp = __fsub_rn(dp, BD[k]);
                 }
                 float* rgb = out_rgb + 3 * (size_t)L.pix_base[v];
-                rgb[pix] = __fmaf_rn(T[k], bg0, C0[k]);
-                rgb[P + pix] = __fmaf_rn(T[k], bg1, C1[k]);
-                rgb[2 * P + pix] = __fmaf_rn(T[k], bg2, C2[k]);
-                out_d[gp] = Dp[k];
-                out_T[gp] = T[k];
+                rgb[pix] = __fmaf_rn(Tk, bg0, c0);
+                rgb[P + pix] = __fmaf_rn(Tk, bg1, c1);
+                rgb[2 * P + pix] = __fmaf_rn(Tk, bg2, c2);
+                out_d[gp] = dp;
+                out_T[gp] = Tk;
                 out_nc[gp] = last[k];
                 if (COUNT) {
                     out_ne[gp] = cnt[k] ? cnt[k] : rg.y - rg.x;   // never stopped: the whole list
@@ -430,8 +562,18 @@ __device__ __forceinline__ float warp_reduce12(const float v[12], int& slot)
 // EXT adds the per-Gaussian error of Eq. 5 (pix_err -> gauss_err) and the
 // active-set mask: inactive entries (a warp-uniform property, the entry is the
 // same for the whole warp) only recover T and the suffix colour.
+//
+// Per pixel-entry the arithmetic runs on pairs of pixels (f32x2) where a thread
+// has two or more, branch-free: a pixel where the entry is not blended (list
+// position at or past n_contrib, or outside the window test of the forward
+// pass) takes alpha = 0 -- T / (1 - 0) = T (the hardware reciprocal of 1 is
+// exact), the suffix scalar and every sum unchanged -- and the derivatives
+// through alpha are kept only where o G <= 0.99 (alpha not clamped).
+#ifndef GEVO_BWD8_MINB
+#define GEVO_BWD8_MINB 16   // 32-thread walk: at most 128 registers (measured best of 1, 16, 20)
+#endif
 template <int PPT, bool DD, bool DT, bool EXT>
-__global__ void __launch_bounds__(256 / PPT)
+__global__ void __launch_bounds__(256 / PPT, (PPT == 8 ? GEVO_BWD8_MINB : 1))
 k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
              const float4* __restrict__ rz, const uint32_t* __restrict__ vals,
              const uint2* __restrict__ ranges, float bg0, float bg1, float bg2,
@@ -443,18 +585,21 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
              const uint32_t* __restrict__ active, const uint32_t* __restrict__ act_last,
              const float* __restrict__ act_T, const float4* __restrict__ act_rest)
 {
+    using V = typename std::conditional<(PPT >= 2), f2, float>::type;
+    constexpr int W2 = VW<V>::n;
+    constexpr int NV = PPT / W2;
     constexpr int NT = 256 / PPT;
     constexpr int NW = NT / 32;
     // staging batch: half a record per thread (measured on the benchmark: 32
     // entries at 64 threads beat 64, 96, 128 and 256; the walk starts near each
     // warp's last blended position, so short batches waste less)
     constexpr int kBatch = NT >= 64 ? NT / 2 : NT;
-    __shared__ float2 s_xy[kBatch];
-    __shared__ float4 s_co[kBatch];
-    __shared__ float4 s_rz[kBatch];
+    __shared__ Staged s_e[kBatch];
     __shared__ uint32_t s_mask[kBatch];
     __shared__ uint32_t s_id[kBatch];
-    constexpr int NG = EXT ? 11 : 10;   // per-entry sums: 10 gradients (+ the error weight)
+    // per-entry sums: the six moment products, colour and depth (10), the
+    // opacity term with dL/dT_final, the error weight of Eq. 5
+    constexpr int NG = 10 + (DT ? 1 : 0) + (EXT ? 1 : 0);
     __shared__ float s_g[kBatch][NG];
     __shared__ uint16_t s_list[NW][kBatch];
     __shared__ uint32_t s_item;
@@ -483,32 +628,32 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
         const int py0 = y0 + (tid >> 4) * PPT;
         const uint2 rg = ranges[tile];
         const size_t vbase = (size_t)v * n;
-        const float fpx = (float)px;
+        const V pxv = vsplat<V>((float)px);
 
         // Only the projection of the suffix colour and depth S onto the
         // pixel's upstream gradient, Pg = dL/dC . S (+ dL/dD S_D), enters
         // dL/dalpha = T_i (dL/dC . c + dL/dD z - Pg), and it follows
         // S <- S + alpha (c - S) as Pg <- Pg + alpha (q - Pg), q = dL/dC . c +
         // dL/dD z: one scalar per pixel instead of four.
-        float T[PPT], Pg[PPT];
-        float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gTT[PPT], pe[PPT];
+        float Tk[PPT], Pk[PPT], g0[PPT], g1[PPT], g2[PPT], gdd[PPT], gtt[PPT], pek[PPT], yk[PPT];
         uint32_t last[PPT];
         uint32_t mymax = 0;
 #pragma unroll
         for (int k = 0; k < PPT; k++) {
             const int py = py0 + k;
-            Pg[k] = 0.f;
+            Pk[k] = 0.f;
+            yk[k] = (float)py;
             if (px < W && py < H) {
                 const size_t pix = (size_t)py * W + px;
                 const size_t gp = (size_t)L.pix_base[v] + pix;
                 const float* g3 = dL_drgb + 3 * (size_t)L.pix_base[v];
-                T[k] = T_final[gp];
+                Tk[k] = T_final[gp];
                 last[k] = n_contrib[gp];
-                gC0[k] = g3[pix]; gC1[k] = g3[P + pix]; gC2[k] = g3[2 * P + pix];
-                gD[k] = DD ? dL_dd[gp] : 0.f;
-                gTT[k] = DT ? dL_dT[gp] * T[k] : 0.f;
-                pe[k] = (EXT && pix_err) ? pix_err[gp] : 0.f;
-                Pg[k] = gC0[k] * bg0 + gC1[k] * bg1 + gC2[k] * bg2;
+                g0[k] = g3[pix]; g1[k] = g3[P + pix]; g2[k] = g3[2 * P + pix];
+                gdd[k] = DD ? dL_dd[gp] : 0.f;
+                gtt[k] = DT ? dL_dT[gp] * Tk[k] : 0.f;
+                pek[k] = (EXT && pix_err) ? pix_err[gp] : 0.f;
+                Pk[k] = g0[k] * bg0 + g1[k] * bg1 + g2[k] * bg2;
                 if (EXT && act_last) {
                     // start at the last active entry: what lies behind it is
                     // summarised by the transmittance after it and the colour
@@ -517,15 +662,28 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                     if (last[k]) {
                         const float Ta = act_T[gp];
                         const float4 q = act_rest[gp];
-                        T[k] = Ta;
-                        Pg[k] = __fdiv_rn(gC0[k] * q.x + gC1[k] * q.y + gC2[k] * q.z + gD[k] * q.w, Ta);
+                        Tk[k] = Ta;
+                        Pk[k] = __fdiv_rn(g0[k] * q.x + g1[k] * q.y + g2[k] * q.z + gdd[k] * q.w, Ta);
                     }
                 }
             } else {
-                T[k] = 1.f; last[k] = 0u;
-                gC0[k] = gC1[k] = gC2[k] = gD[k] = gTT[k] = pe[k] = 0.f;
+                Tk[k] = 1.f; last[k] = 0u;
+                g0[k] = g1[k] = g2[k] = gdd[k] = gtt[k] = pek[k] = 0.f;
             }
             mymax = max(mymax, last[k]);
+        }
+        V T[NV], Pg[NV], gC0[NV], gC1[NV], gC2[NV], gD[NV], gTT[NV], pe[NV], pyv[NV];
+#pragma unroll
+        for (int h = 0; h < NV; h++) {
+            T[h] = vpack<V>(Tk + h * W2);
+            Pg[h] = vpack<V>(Pk + h * W2);
+            gC0[h] = vpack<V>(g0 + h * W2);
+            gC1[h] = vpack<V>(g1 + h * W2);
+            gC2[h] = vpack<V>(g2 + h * W2);
+            gD[h] = vpack<V>(gdd + h * W2);
+            gTT[h] = vpack<V>(gtt + h * W2);
+            pe[h] = vpack<V>(pek + h * W2);
+            pyv[h] = vpack<V>(yk + h * W2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
@@ -535,6 +693,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
 #pragma unroll
         for (int w = 0; w < NW; w++) bmax = max(bmax, s_max[w]);
 
+        const V one = vsplat<V>(1.f);
         const uint32_t end = rg.x + bmax;
         for (uint32_t bend = end; bend > rg.x; bend -= min((uint32_t)kBatch, bend - rg.x)) {
             const uint32_t bstart = bend - min((uint32_t)kBatch, bend - rg.x);
@@ -548,9 +707,7 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 // ids are < 2^31 (n is an int32): the top bit marks inactive entries
                 const bool inactive = EXT && active && !((__ldg(active + (id >> 5)) >> (id & 31)) & 1u);
                 s_id[j] = id | (inactive ? 0x80000000u : 0u);
-                s_xy[j] = m;
-                s_co[j] = prescale(c);
-                s_rz[j] = rz[gid];
+                stage_entry(s_e[j], m, c, rz[gid]);
                 s_mask[j] = strip_mask(m, c, (float)x0, (float)y0, NT / 32, WROWS);
 #pragma unroll
                 for (int q = 0; q < NG; q++) s_g[j][q] = 0.f;
@@ -576,114 +733,112 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
             for (int q = nl - 1; q >= 0; q--) {
                 const int j = s_list[warp][q];
                 const uint32_t pos = boff + j;   // list position
-                const float2 m = s_xy[j];
-                const float4 c = s_co[j];
-                const float dx = __fsub_rn(m.x, fpx);
-                float p2[PPT], G[PPT], dyk[PPT];
-                const float2 col = power2_col(c, dx);
-#pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    dyk[k] = __fsub_rn(m.y, (float)(py0 + k));
-                    p2[k] = power2_at(c, col, dyk[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < PPT; k++) G[k] = ex2_approx(p2[k]);
-                // no warp-wide skip when no pixel uses the entry: the vote
-                // separates the test from the update, and measured slower
-                float al[PPT];
-                bool use[PPT];
-#pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    al[k] = fminf(kAlphaMax, __fmul_rn(c.w, G[k]));
-                    use[k] = pos < last[k] && !(p2[k] > 0.f) && !(al[k] < kAlphaMin);
-                }
-                const float4 r = s_rz[j];
+                const EntryOps<V> e = entry_ops<V>(s_e[j], pxv);
+                const float dx = e.dxs;
                 const bool act = !EXT || !(s_id[j] >> 31);
+                // per-thread sums over its pixels (pairs), reduced below
+                V s0 = vsplat<V>(0.f), s1 = s0, s2 = s0, so = s0, sr = s0, sg = s0, sb = s0,
+                  sz = s0, se = s0;
+#pragma unroll
+                for (int h = 0; h < NV; h++) {
+                    const V dy = vsub(e.my, pyv[h]);
+                    const V p2 = vfma(vfma(e.cz, dy, e.cy), dy, e.cx);
+                    const V dwin = vadd(p2, e.mw);
+                    float g[W2], al[W2];
+                    bool kk[W2];
+#pragma unroll
+                    for (int i = 0; i < W2; i++) g[i] = ex2_approx(vlane(p2, i));
+                    const V G = vpack<V>(g);
+                    const V og = vmul(e.cw, G);
+#pragma unroll
+                    for (int i = 0; i < W2; i++) {
+                        const int k = h * W2 + i;
+                        const float ogi = vlane(og, i);
+                        const bool use = pos < last[k] && window_ok(vlane(dwin, i), e.m);
+                        kk[i] = use && ogi <= kAlphaMax;      // alpha not clamped
+                        al[i] = use ? fminf(kAlphaMax, ogi) : 0.f;
+                    }
+                    const V alpha = vpack<V>(al);                    // 0 where unused
+                    const V om = vsub(one, alpha);
+                    float ri[W2];
+#pragma unroll
+                    for (int i = 0; i < W2; i++) ri[i] = rcp_approx(vlane(om, i));
+                    const V inv = vpack<V>(ri);
+                    const V Ti = vmul(T[h], inv);
+                    T[h] = Ti;
+                    const V w = vmul(alpha, Ti);
+                    // (c - S) . dL/dC, shared by dL/dalpha = T_i gd and the suffix update
+                    V qc = vmul(gC0[h], e.rx);
+                    qc = vfma(gC1[h], e.ry, qc);
+                    qc = vfma(gC2[h], e.rb, qc);
+                    if (DD) qc = vfma(gD[h], e.rw, qc);
+                    const V gd = vsub(qc, Pg[h]);
+                    Pg[h] = vfma(alpha, gd, Pg[h]);
+                    if (EXT && !act) {
+                        if (pix_err) se = vfma(w, pe[h], se);
+                        continue;
+                    }
+                    if (EXT) se = vfma(w, pe[h], se);
+                    sr = vfma(gC0[h], w, sr);
+                    sg = vfma(gC1[h], w, sg);
+                    sb = vfma(gC2[h], w, sb);
+                    if (DD) sz = vfma(gD[h], w, sz);
+                    V dp;
+                    float dd[W2];
+                    if (DT) {
+                        // dL/dalpha = gd T_i - dL/dT_final T_final / (1 - alpha)
+                        const V dLda = vsub(vmul(gd, Ti), vmul(gTT[h], inv));
+#pragma unroll
+                        for (int i = 0; i < W2; i++) dd[i] = kk[i] ? vlane(dLda, i) : 0.f;
+                        const V kd = vpack<V>(dd);
+                        so = vfma(kd, G, so);
+                        dp = vmul(kd, alpha);
+                    } else {
+                        const V gw = vmul(gd, w);
+#pragma unroll
+                        for (int i = 0; i < W2; i++) dd[i] = kk[i] ? vlane(gw, i) : 0.f;
+                        dp = vpack<V>(dd);
+                    }
+                    const V t = vmul(dp, dy);
+                    s0 = vadd(s0, dp);
+                    s1 = vadd(s1, t);
+                    s2 = vfma(t, dy, s2);
+                }
+                float m0 = vlane(s0, 0), m1 = vlane(s1, 0), m2 = vlane(s2, 0);
+                float a_o = vlane(so, 0), a_r = vlane(sr, 0), a_g = vlane(sg, 0),
+                      a_b = vlane(sb, 0), a_z = vlane(sz, 0), a_e = vlane(se, 0);
+#pragma unroll
+                for (int i = 1; i < W2; i++) {
+                    m0 += vlane(s0, i); m1 += vlane(s1, i); m2 += vlane(s2, i);
+                    a_o += vlane(so, i); a_r += vlane(sr, i); a_g += vlane(sg, i);
+                    a_b += vlane(sb, i); a_z += vlane(sz, i); a_e += vlane(se, i);
+                }
                 if (EXT && !act) {
                     // inactive: transmittance and suffix colour only (+ the error weight)
-                    float a_e = 0.f;
-#pragma unroll
-                    for (int k = 0; k < PPT; k++) {
-                        const float alpha = use[k] ? al[k] : 0.f;
-                        const float om = 1.f - alpha;
-                        const float Ti = use[k] ? T[k] * rcp_approx(om) : T[k];
-                        T[k] = Ti;
-                        a_e += alpha * Ti * pe[k];
-                        float qc = gC0[k] * r.x + gC1[k] * r.y + gC2[k] * r.z;
-                        if (DD) qc += gD[k] * r.w;
-                        Pg[k] += alpha * (qc - Pg[k]);
-                    }
                     if (pix_err) {
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) a_e += __shfl_xor_sync(0xffffffffu, a_e, o);
-                        if ((threadIdx.x & 31) == 0 && a_e != 0.f) atomicAdd(&s_g[j][NG - 1], a_e);
+                        if (lane == 0 && a_e != 0.f) atomicAdd(&s_g[j][NG - 1], a_e);
                     }
                     continue;
                 }
                 // A thread's pixels share the column, so dx is the same for all
                 // of them: the conic and mean gradients are linear in the
                 // per-pixel dp = dL/dalpha * alpha with coefficients in 1, dy,
-                // dy^2, so the pixel loop keeps three moments and the
-                // coefficients are applied once per entry.
-                float m0 = 0.f, m1 = 0.f, m2 = 0.f, a_o = 0.f;
-                float a_r = 0.f, a_g = 0.f, a_b = 0.f, a_z = 0.f, a_e = 0.f;
-                // branch-free over the pixels: an unused pixel takes alpha = 0,
-                // which leaves T and the suffix unchanged and adds zeros
-#pragma unroll
-                for (int k = 0; k < PPT; k++) {
-                    const float alpha = use[k] ? al[k] : 0.f;
-                    const float dy = dyk[k];
-                    const float om = 1.f - alpha;
-                    const float inv = rcp_approx(om);
-                    const float Ti = use[k] ? T[k] * inv : T[k];
-                    T[k] = Ti;
-                    const float w = alpha * Ti;
-                    if (EXT) a_e += w * pe[k];
-                    // (c - S) . dL/dC, shared by dL/dalpha = T_i gd
-                    // (- dL/dT_final T_final / (1 - alpha)) and the suffix update
-                    float qc = gC0[k] * r.x + gC1[k] * r.y + gC2[k] * r.z;
-                    if (DD) qc += gD[k] * r.w;
-                    const float gd = qc - Pg[k];
-                    Pg[k] += alpha * gd;
-                    a_r += gC0[k] * w; a_g += gC1[k] * w; a_b += gC2[k] * w;
-                    if (DD) a_z += gD[k] * w;
-                    // dp = dL/dalpha * alpha on unclamped pixels
-                    const bool unclamped = use[k] && __fmul_rn(c.w, G[k]) <= kAlphaMax;
-                    float dp;
-                    if (DT) {
-                        const float dLda = gd * Ti - gTT[k] * inv;
-                        a_o += unclamped ? dLda * G[k] : 0.f;
-                        dp = unclamped ? dLda * alpha : 0.f;
-                    } else {
-                        dp = unclamped ? gd * w : 0.f;
-                    }
-                    const float t = dp * dy;
-                    m0 += dp;
-                    m1 += t;
-                    m2 += t * dy;
-                }
-                // without dL/dT_final, dL/do = sum dL/dalpha G = m0 / o (alpha = o G
-                // on every unclamped pixel), one product per entry
-                if (!DT) a_o = m0 * rcp_approx(c.w);
-                // d alpha / d(a, b, c) = alpha (-dx^2 / 2, -dx dy, -dy^2 / 2);
-                // d alpha / d(mean) = alpha ln2 (2 a' dx + b' dy, 2 c' dy + b' dx)
-                // with the pre-scaled conic (a', b', c')
-                const float a_ca = -0.5f * dx * dx * m0;
-                const float a_cb = -dx * m1;
-                const float a_cc = -0.5f * m2;
-                const float a_xy0 = kLn2 * (2.f * c.x * dx * m0 + c.y * m1);
-                const float a_xy1 = kLn2 * (2.f * c.z * m1 + c.y * dx * m0);
-                if (EXT) {
-                    const float vals12[12] = {a_xy0, a_xy1, a_ca, a_cb, a_cc, a_o,
-                                              a_r,   a_g,   a_b,  a_z,  a_e,  0.f};
-                    int slot;
-                    const float tot = warp_reduce12(vals12, slot);
-                    if (slot >= 0 && slot < NG && tot != 0.f) atomicAdd(&s_g[j][slot], tot);
-                } else {
-                    const float vals10[10] = {a_xy0, a_xy1, a_ca, a_cb, a_cc, a_o, a_r, a_g, a_b, a_z};
-                    int slot;
-                    const float tot = warp_reduce10(vals10, slot);
+                // dy^2 (the moments m0, m1, m2), and across the warp's columns in
+                // 1, dx, dx^2.  The warp sums the six products m0, dx m0, dx^2 m0,
+                // m1, dx m1, m2, and the gradients are formed from their totals
+                // once per entry when the batch is flushed.
+                const float S1 = dx * m0;
+                const float vals[12] = {m0, S1, dx * S1, m1, dx * m1, m2, a_r, a_g, a_b, a_z,
+                                        DT ? a_o : a_e, a_e};
+                int slot;
+                if (NG == 10) {
+                    const float tot = warp_reduce10(vals, slot);
                     if (slot >= 0 && tot != 0.f) atomicAdd(&s_g[j][slot], tot);
+                } else {
+                    const float tot = warp_reduce12(vals, slot);
+                    if (slot >= 0 && slot < NG && tot != 0.f) atomicAdd(&s_g[j][slot], tot);
                 }
             }
             __syncthreads();
@@ -694,10 +849,22 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 bool nz = false;
 #pragma unroll
                 for (int q = 0; q < 10; q++) nz = nz || gg[q] != 0.f;
+                if (DT) nz = nz || gg[10] != 0.f;
                 if (!nz) continue;
+                // d alpha / d(a, b, c) = alpha (-dx^2 / 2, -dx dy, -dy^2 / 2);
+                // d alpha / d(mean) = alpha ln2 (2 a' dx + b' dy, 2 c' dy + b' dx)
+                // with the pre-scaled conic (a', b', c'); without dL/dT_final,
+                // dL/do = sum dL/dalpha G = m0 / o (alpha = o G on every
+                // unclamped pixel)
+                const float ca = f2_lo(f2{s_e[j].p1.x}), cb = f2_lo(f2{s_e[j].p1.y});
+                const float cc = f2_lo(f2{s_e[j].p2.x}), op = f2_lo(f2{s_e[j].p2.y});
+                const float S0 = gg[0], S1 = gg[1], S2 = gg[2], S3 = gg[3], S4 = gg[4], S5 = gg[5];
+                const float gx = kLn2 * (2.f * ca * S1 + cb * S3);
+                const float gy = kLn2 * (2.f * cc * S3 + cb * S1);
+                const float go = DT ? gg[10] : S0 * rcp_approx(op);
                 const size_t gid = vbase + (EXT ? (s_id[j] & 0x7FFFFFFFu) : s_id[j]);
-                atomicAdd(g_xy + gid, make_float2(gg[0], gg[1]));
-                atomicAdd(g_co + gid, make_float4(gg[2], gg[3], gg[4], gg[5]));
+                atomicAdd(g_xy + gid, make_float2(gx, gy));
+                atomicAdd(g_co + gid, make_float4(-0.5f * S2, -S4, -0.5f * S5, go));
                 atomicAdd(g_rz + gid, make_float4(gg[6], gg[7], gg[8], gg[9]));
             }
         }
@@ -807,7 +974,7 @@ extern "C" gevo_status gevo_render_fwd(const gevo_layout* layout, int32_t n, con
                                        uint32_t* n_contrib, uint32_t* n_eval,
                                        const gevo_tuning* tuning, void* workspace, void* stream)
 {
-    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+    if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
         !proj->rgb_depth || !ranges || !bg || !rgb || !depth || !T_final || !n_contrib ||
         !workspace || !gevo_aligned(workspace, 256) || !valid_tuning(tuning) ||
         !gevo_aligned(ranges, 8) || !gevo_aligned(proj->conic_opacity, 16) ||
@@ -832,7 +999,7 @@ extern "C" gevo_status gevo_render_fwd_counts(const gevo_layout* layout, int32_t
                                               const gevo_tuning* tuning, void* workspace,
                                               void* stream)
 {
-    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+    if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
         !proj->rgb_depth || !vals || !ranges || !bg || !rgb || !depth || !T_final || !n_contrib ||
         !n_eval || !n_blend || !workspace || !gevo_aligned(workspace, 256) ||
         !valid_tuning(tuning) || !gevo_aligned(ranges, 8) ||
@@ -857,7 +1024,7 @@ extern "C" gevo_status gevo_render_fwd_active(const gevo_layout* layout, int32_t
                                               const gevo_tuning* tuning, void* workspace,
                                               void* stream)
 {
-    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+    if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
         !proj->rgb_depth || !vals || !ranges || !bg || !rgb || !depth || !T_final || !n_contrib ||
         !active || !state || !state->last || !state->T || !state->rest || !workspace ||
         !gevo_aligned(workspace, 256) || !valid_tuning(tuning) || !gevo_aligned(ranges, 8) ||
@@ -882,7 +1049,7 @@ extern "C" gevo_status gevo_render_bwd(const gevo_layout* layout, int32_t n, con
                                        gevo_grad2d* out, const gevo_tuning* tuning,
                                        void* workspace, void* stream)
 {
-    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+    if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
         !proj->rgb_depth || !proj->radius || !vals || !ranges || !bg || !T_final || !n_contrib ||
         !dL_drgb || !out || !out->xy || !out->conic_opacity || !out->rgb_depth || !workspace ||
         !gevo_aligned(workspace, 256) || !valid_tuning(tuning) || !gevo_aligned(ranges, 8) ||
@@ -910,7 +1077,7 @@ extern "C" gevo_status gevo_render_bwd_active(const gevo_layout* layout, int32_t
                                               const gevo_tuning* tuning, void* workspace,
                                               void* stream)
 {
-    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
+    if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->conic_opacity ||
         !proj->rgb_depth || !proj->radius || !vals || !ranges || !bg || !T_final || !n_contrib ||
         !dL_drgb || !out || !out->xy || !out->conic_opacity || !out->rgb_depth || !workspace ||
         !gevo_aligned(workspace, 256) || !valid_tuning(tuning) || !gevo_aligned(ranges, 8) ||
@@ -936,7 +1103,7 @@ extern "C" gevo_status gevo_render_bwd_active(const gevo_layout* layout, int32_t
 extern "C" gevo_status gevo_grad2d_zero(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
                                         gevo_grad2d* out, void* stream)
 {
-    if (!layout || layout->n_views < 1 || n < 0 || !proj || !proj->radius || !out || !out->xy ||
+    if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->radius || !out || !out->xy ||
         !out->conic_opacity || !out->rgb_depth || !gevo_aligned(out->conic_opacity, 16) ||
         !gevo_aligned(out->rgb_depth, 16) || !gevo_aligned(out->xy, 8))
         return GEVO_ERR_INVALID;
