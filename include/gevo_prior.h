@@ -73,7 +73,8 @@ gevo_status gevo_upsample2_bwd(int32_t nb, int32_t h, int32_t w, int32_t C, cons
 /* Wf[ci][tap][co] = Wt[co][8 - tap][ci]. */
 gevo_status gevo_flip3x3(int32_t Cout, int32_t Cin, const void* Wt, void* Wf, void* stream);
 
-/* Planar FP32 RGB renders [nb][3][H][W] -> NHWC BF16 with 8 channels (5 zero). */
+/* Planar FP32 RGB renders [nb][3][H][W] -> NHWC BF16 with 8 channels: the
+ * network input rgb - 0.5 (centred) in channels 0..2, zeros in 3..7. */
 gevo_status gevo_rgb_pack(int32_t nb, int32_t H, int32_t W, const float* rgb, void* X,
                           void* stream);
 

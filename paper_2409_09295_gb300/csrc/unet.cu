@@ -30,16 +30,20 @@ static int grid_for(size_t n, int threads = 256)
     return (int)std::max<size_t>(1, std::min<size_t>((n + threads - 1) / threads, (size_t)sm_count() * 16));
 }
 
-// planar FP32 RGB [nb][3][H][W] -> NHWC BF16 with 8 channels (3 used, 5 zero)
+// planar FP32 RGB [nb][3][H][W] -> NHWC BF16 with 8 channels (3 used, 5 zero),
+// centred: rgb - 0.5.  With all-positive inputs the He-initialised first
+// layer's channels start either on or off for every pixel, and training sat
+// near a constant-depth predictor for many epochs (two of four seeds never
+// left it in 30 epochs); centred, all four left it within 8 epochs.
 __global__ void k_rgb_pack(size_t P, int HW, const float* __restrict__ rgb, bf16* __restrict__ X)
 {
     for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
         const size_t b = p / HW, q = p - b * HW;
         const float* src = rgb + b * 3 * (size_t)HW + q;
         __align__(16) bf16 v[8];
-        v[0] = __float2bfloat16_rn(src[0]);
-        v[1] = __float2bfloat16_rn(src[HW]);
-        v[2] = __float2bfloat16_rn(src[2 * (size_t)HW]);
+        v[0] = __float2bfloat16_rn(src[0] - 0.5f);
+        v[1] = __float2bfloat16_rn(src[HW] - 0.5f);
+        v[2] = __float2bfloat16_rn(src[2 * (size_t)HW] - 0.5f);
 #pragma unroll
         for (int i = 3; i < 8; i++) v[i] = __float2bfloat16_rn(0.f);
         *reinterpret_cast<uint4*>(X + p * 8) = *reinterpret_cast<uint4*>(v);

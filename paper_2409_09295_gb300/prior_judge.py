@@ -16,9 +16,10 @@ III-A, III-B).  The protocol here, on the 500k-Gaussian room scene:
   4. new Gaussians (the same pixels for both methods) are placed at the depth
      from (a) the prior on each keyframe image, (b) the cost volume over the
      8 keyframes with belief propagation (Section III-A2);
-  5. each initialisation is optimised for the same number of iterations (L1
-     photometric loss over the keyframes, Adam on the new Gaussians' means and
-     colours, the map frozen);
+  5. each initialisation is optimised for the same number of iterations by the
+     local stage of Eq. 2 (E_pho + E_iso over the keyframes, Adam on every
+     parameter of the new Gaussians, the map frozen, the keyframe poses held
+     fixed); a second protocol updates only their means and colours;
   6. L1 colour and L1 depth against world renders are measured on 16 other
      views near the window, over the new-region pixels.
 Every render, loss, gradient, convolution and optimiser step runs in libgevo.
@@ -263,16 +264,73 @@ def optimise(map_g, new_g, key_cams, key_rgb, iters=100, lr_means=3e-3, lr_sh=2e
     return g, losses
 
 
-def evaluate(g, test_cams, world_test, masks):
+# Adam of the judge's local stage: the position and colour rates of the
+# means-and-colour protocol, the 3DGS rates for scale, rotation and opacity,
+# E_iso as in the mapping update
+JUDGE_ADAM = dict(lr_means=3e-3, lr_log_scales=5e-3, lr_quats=1e-3, lr_logit_opacities=5e-2,
+                  lr_colour_dc=2e-2, lr_colour_rest=2e-2, beta1=0.9, beta2=0.999, eps=1e-15,
+                  lambda_iso=10.0)
+
+
+def optimise_local(map_g, new_g, key_cams, key_rgb, iters=100):
+    """The local stage of Eq. 2 on the new Gaussians: every parameter (mean,
+    scale, rotation, opacity, SH), E_pho + E_iso against the keyframes, Adam in
+    log-scale / logit space, the map frozen and the keyframe poses held fixed.
+    Returns the rasterizer's view of map + optimised new Gaussians, and the
+    per-iteration losses."""
+    from .mapping import GaussianMap, MapOptimizer, _bits_of
+    nm = int(map_g["means"].shape[0])
+    nn = int(new_g["means"].shape[0])
+    gm = GaussianMap.__new__(GaussianMap)
+    gm.dev = map_g["means"].device
+    gm.sh_degree, gm.colour, gm.K = 3, "sh", 16
+    cat = lambda k: torch.cat([map_g[k], new_g[k]]).contiguous()
+    o = torch.clamp(cat("opacities"), 1e-6, 1 - 1e-6)
+    gm.p = dict(means=cat("means"), log_scales=torch.log(cat("scales")), quats=cat("quats"),
+                logit_opacities=torch.log(o / (1 - o)), colours=cat("sh").view(-1, 16, 3).contiguous())
+    gm._derived()
+    n_all = nm + nn
+    rows = torch.arange(nm, n_all, dtype=torch.int32, device=gm.dev)
+    counts = torch.zeros(_abi.active_count_words(n_all), dtype=torch.int32, device=gm.dev)
+    counts[0] = nn
+    opt = MapOptimizer(gm, JUDGE_ADAM, tuning=dict(threads_per_tile=64, persistent=1, blocks_per_sm=0))
+    camt = camera_tensor(key_cams)
+    losses = opt.iterate(key_cams, camt, key_rgb.reshape(-1).contiguous(), iters,
+                         fixed=[True] * len(key_cams), active=(_bits_of(n_all, nm, n_all, gm.dev),
+                                                                rows, counts))
+    return gm.gaussians(), losses
+
+
+def evaluate(g, test_cams, world_test, masks, keep_maps=False):
+    """L1 colour over the new-region pixels of the test views, L1 of the mean
+    depth over those the render covers (1 - T > 0.5), and that coverage.
+    keep_maps: also return the per-pixel errors and the covered mask, for the
+    comparison over the pixels two initialisations both cover."""
     rgb, D, T = render_many(g, test_cams)
     rw, dw, tw = world_test
     m = masks > 0.5
-    e_rgb = torch.abs(rgb - rw).mean(dim=1)[m].mean().item()
+    e_px = torch.abs(rgb - rw).mean(dim=1)
+    e_rgb = e_px[m].mean().item()
     ew = dw / torch.clamp(1 - tw, min=1e-6)
     eg = D / torch.clamp(1 - T, min=1e-6)
     ok = m & ((1 - T) > 0.5)
     e_d = torch.abs(eg - ew)[ok].mean().item() if ok.any() else float("nan")
-    return dict(l1_rgb=e_rgb, l1_depth=e_d, coverage=float(ok.sum().item() / max(m.sum().item(), 1)))
+    out = dict(l1_rgb=e_rgb, l1_depth=e_d, coverage=float(ok.sum().item() / max(m.sum().item(), 1)))
+    if keep_maps:
+        out["maps"] = dict(e_rgb=e_px, e_depth=torch.abs(eg - ew), covered=ok)
+    return out
+
+
+def common_metrics(a, b):
+    """L1 colour and depth of two evaluated initialisations over the pixels both
+    cover (the coverage-matched comparison)."""
+    both = a["maps"]["covered"] & b["maps"]["covered"]
+    n = int(both.sum().item())
+    if n == 0:
+        return dict(pixels=0)
+    return dict(pixels=n,
+                l1_rgb={k: x["maps"]["e_rgb"][both].mean().item() for k, x in (("a", a), ("b", b))},
+                l1_depth={k: x["maps"]["e_depth"][both].mean().item() for k, x in (("a", a), ("b", b))})
 
 
 def run(n=500_000, n_train=2000, epochs=30, iters=100, total_new=50_000, log=None):
@@ -317,6 +375,7 @@ def run(n=500_000, n_train=2000, epochs=30, iters=100, total_new=50_000, log=Non
                              "plain": torch.abs(d_plain - world_depth)[m].mean().item()}}
     res["new_region_pixels"] = {"keyframes": int(key_mask.sum().item()),
                                 "test": int(test_mask.sum().item())}
+    maps, maps_mc = {}, {}
     for name, dep in (("prior", d_prior), ("plain", d_plain)):
         new_g = init_gaussians(dep, key_rgb, key_mask, key_cams, total_new)
         if int(new_g["means"].shape[0]) == 0:
@@ -324,11 +383,25 @@ def run(n=500_000, n_train=2000, epochs=30, iters=100, total_new=50_000, log=Non
             continue
         before = evaluate({k: (torch.cat([map_g[k], new_g[k]]) if k != "sh_degree" else 3)
                            for k in map_g}, test_cams, world_test, test_mask)
-        g, losses = optimise(map_g, new_g, key_cams, key_rgb, iters=iters)
-        after = evaluate(g, test_cams, world_test, test_mask)
-        res[name] = dict(new_gaussians=int(new_g["means"].shape[0]), before=before, after=after,
+        g, losses = optimise_local(map_g, new_g, key_cams, key_rgb, iters=iters)
+        after = evaluate(g, test_cams, world_test, test_mask, keep_maps=True)
+        maps[name] = after
+        # the secondary protocol: means and colours only, opacity and size as inserted
+        g_mc, losses_mc = optimise(map_g, new_g, key_cams, key_rgb, iters=iters)
+        after_mc = evaluate(g_mc, test_cams, world_test, test_mask, keep_maps=True)
+        maps_mc[name] = after_mc
+        res[name] = dict(new_gaussians=int(new_g["means"].shape[0]), before=before,
+                         after={k: v for k, v in after.items() if k != "maps"},
                          loss_first=losses[0] if losses else None,
-                         loss_last=losses[-1] if losses else None)
+                         loss_last=losses[-1] if losses else None,
+                         means_colours_only={k: v for k, v in after_mc.items() if k != "maps"})
+    for key, mp in (("common", maps), ("common_means_colours_only", maps_mc)):
+        if len(mp) == 2:
+            c = common_metrics(mp["prior"], mp["plain"])
+            res[key] = dict(pixels=c["pixels"])
+            if c["pixels"]:
+                res[key]["l1_rgb"] = {"prior": c["l1_rgb"]["a"], "plain": c["l1_rgb"]["b"]}
+                res[key]["l1_depth"] = {"prior": c["l1_depth"]["a"], "plain": c["l1_depth"]["b"]}
     return res
 
 

@@ -98,11 +98,28 @@ def test_belief_propagation_on_the_plane_cost_volume():
     np.testing.assert_array_equal(lab[clear], lab_ref[clear])
 
 
-def test_prior_judge_reduced_protocol_runs_and_optimises():
-    res = prior_judge.run(n=120_000, n_train=128, epochs=3, iters=15, total_new=8_000)
+def test_prior_judge_depth_gain_at_equal_iterations():
+    """The learned prior against the plain initialisation (Eq. 1 + belief
+    propagation) on the 500k room with a 50k-Gaussian box held out, both
+    optimised by the same 100 local-stage iterations (Eq. 2).  What the trained
+    network gains: its depths start ~50x closer to the truth, and after the
+    optimisation its new Gaussians' depth error is still below plain's, over
+    all covered new-region pixels and over the pixels both cover.  Its colour
+    error after the optimisation is higher than plain's (the synthetic room is a
+    volume of small random splats: splats from eight keyframes at the true depth
+    land on top of one another and cover fewer test pixels than plain's
+    scattered ones); the test records it without asserting an order."""
+    res = prior_judge.run()
+    assert res["train"]["losses"][-1] < 0.15, res["train"]["losses"]   # left the plateau
+    ini = res["init_depth_l1"]
+    assert ini["prior"] < 0.1 * ini["plain"], ini
     for name in ("prior", "plain"):
         r = res[name]
-        assert r["new_gaussians"] > 4_000
-        assert np.isfinite(r["after"]["l1_rgb"]) and np.isfinite(r["after"]["l1_depth"])
-        assert r["loss_last"] < r["loss_first"]
-    print("judge (reduced):", res["init_depth_l1"], {k: res[k]["after"] for k in ("prior", "plain")})
+        assert r["new_gaussians"] >= 40_000
+        assert r["loss_last"] < 0.5 * r["loss_first"]
+        assert np.isfinite(r["after"]["l1_rgb"])
+    assert res["prior"]["after"]["l1_depth"] < res["plain"]["after"]["l1_depth"]
+    c = res["common"]
+    assert c["pixels"] > 100_000
+    assert c["l1_depth"]["prior"] < c["l1_depth"]["plain"], c
+    print("judge:", ini, {k: res[k]["after"] for k in ("prior", "plain")}, c)
