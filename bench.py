@@ -400,10 +400,10 @@ def main():
     dom = "render_bwd"   # the largest share of the step in the ncu launch list
     roof = dict(roofs[dom])
     # DRAM bytes of one reverse-walk launch: ncu (dram__bytes_read.sum + write) of the
-    # current kernel on the 4-view case (`bench.py --case render`), 51.51 MB
-    # for 245.15M walked entries, scaled by entries to this launch (same scene, same
-    # resolution)
-    roof.update({"traffic": 51.51e6 * E_bwd / 245.15e6,
+    # current kernel (32 threads per tile) on the 4-view case
+    # (`bench.py --case render --threads-bwd 32`), 51.46 MB for 245.15M walked
+    # entries, scaled by entries to this launch (same scene, same resolution)
+    roof.update({"traffic": 51.46e6 * E_bwd / 245.15e6,
                  "traffic_source": "ncu dram bytes of the 4-view case, scaled by walked entries",
                  "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {clk_peak:.0f} MHz"})
 

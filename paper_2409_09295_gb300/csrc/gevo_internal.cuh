@@ -121,14 +121,14 @@ __device__ __forceinline__ f2 f2_make(float a, float b)
 __device__ __forceinline__ f2 f2_splat(float a) { return f2_make(a, a); }
 __device__ __forceinline__ float f2_lo(f2 x)
 {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+    float a;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {%0, t}, %1;\n\t}" : "=f"(a) : "l"(x.v));
     return a;
 }
 __device__ __forceinline__ float f2_hi(f2 x)
 {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+    float b;
+    asm("{\n\t.reg .f32 t;\n\tmov.b64 {t, %0}, %1;\n\t}" : "=f"(b) : "l"(x.v));
     return b;
 }
 __device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)

@@ -34,7 +34,9 @@ from paper_2409_09295_gb300 import raster  # noqa: E402
 TUNINGS = [dict(threads_per_tile=256, persistent=0, blocks_per_sm=0),
            dict(threads_per_tile=128, persistent=1, blocks_per_sm=0),
            dict(threads_per_tile=64, persistent=1, blocks_per_sm=2),
-           dict(threads_per_tile=32, persistent=0, blocks_per_sm=0)]
+           dict(threads_per_tile=32, persistent=0, blocks_per_sm=0),
+           dict(threads_per_tile=32, persistent=1, blocks_per_sm=12)]
+TUNING_IDS = ["ppt1", "ppt2_persistent", "ppt4_persistent", "ppt8", "ppt8_persistent12"]
 
 
 def _np(t):
@@ -147,7 +149,7 @@ def _staged(sizes, n, seed, sigma_px=(0.5, 12.0), opacity=(0.02, 1.0)):
     return rec, ref_bins, pipe
 
 
-@pytest.mark.parametrize("tuning", TUNINGS, ids=["ppt1", "ppt2_persistent", "ppt4_persistent", "ppt8"])
+@pytest.mark.parametrize("tuning", TUNINGS, ids=TUNING_IDS)
 def test_render_fwd_staged_1e5(tuning):
     sizes = [(96, 80), (53, 37)]
     rec, b, pipe = _staged(sizes, 2500, seed=50)
@@ -214,7 +216,7 @@ def test_render_tunings_bitwise_identical():
             np.testing.assert_array_equal(a, c)
 
 
-@pytest.mark.parametrize("tuning", TUNINGS, ids=["ppt1", "ppt2_persistent", "ppt4_persistent", "ppt8"])
+@pytest.mark.parametrize("tuning", TUNINGS, ids=TUNING_IDS)
 def test_render_bwd_staged(tuning):
     sizes = [(96, 80), (53, 37)]
     rec, b, pipe = _staged(sizes, 2000, seed=52)
