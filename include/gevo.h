@@ -196,14 +196,17 @@ gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,
  * empty tile.  *d_n_dup (DEVICE uint64) receives D.
  * If D > dup_capacity: the error word gets GEVO_ERR_CAPACITY, *d_n_dup still
  * receives the true D, every range is (0, 0) and keys / vals are undefined.
- * keys: [dup_capacity] uint64, vals: [dup_capacity] uint32, ranges:
- * [total_tiles][2] uint32 (DEVICE). */
+ * keys: [dup_capacity] uint64 or NULL, vals: [dup_capacity] uint32, ranges:
+ * [total_tiles][2] uint32 (DEVICE).  With keys NULL only vals is written: the
+ * key of position i is implied (its tile is the range holding i, its depth bits
+ * those of entry (v, vals[i])), and the blending and backward stages read only
+ * vals and ranges. */
 gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
                           uint64_t dup_capacity, uint64_t* keys, uint32_t* vals,
                           uint32_t* ranges, uint64_t* d_n_dup, void* workspace, void* stream);
 
-/* Same operation and outputs as gevo_bin_sort, for callers that cannot
- * allocate device memory: no workspace argument, and the call itself allocates
+/* Same operation and outputs as gevo_bin_sort (keys may be NULL there too),
+ * for callers that cannot allocate device memory: no workspace argument, and the call itself allocates
  * nothing (no cudaMalloc, no allocating library routine).  Such callers include
  * plug-ins hosted by a renderer or an inference server that owns every device
  * allocation, and real-time loops where an allocator call, with its latency

@@ -23,6 +23,24 @@ WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap)
     w.core = o;
     const size_t nbx = ((size_t)(n > 0 ? n : 0) + kBinChunk - 1) / kBinChunk;
     w.blk_off = o;      o = align256(o + 4 * nbx * T);
+    const size_t V = (size_t)L.n_views, VN = V * (size_t)(n > 0 ? n : 0);
+    const size_t S = V * kDepthBins;
+    w.ord_stat = o;     o = align256(o + 16 * V);
+    w.ord_seg = o;      o = align256(o + 4 * (5 * S + 1) + 4 * S);
+    w.ord_total = o;    o = align256(o + 16);
+    w.ord_b1 = o;       o = align256(o + 16 * VN);   // later the uint4 records
+    w.ord_b2 = o;       o = align256(o + 8 * VN);
+    w.ord_vals = o;     o = align256(o + 4 * VN);
+    w.ord_dkeys = o;    o = align256(o + 8 * VN);
+    w.ord_pre = o;      o = align256(o + 8 * (VN + V + 1));
+    w.ord_bsum = o;     o = align256(o + 8 * V * ((size_t)(n > 0 ? n : 0) / kOrdScanItems + 1));
+    w.ord_units = o;    o = align256(o + 8 * 4 * (GEVO_MAX_VIEWS + 1));
+    size_t max_tiles = 0;
+    for (int v = 0; v < L.n_views; v++)
+        max_tiles = std::max(max_tiles, (size_t)L.tiles_x[v] * L.tiles_y[v]);
+    const size_t unit_rows = (size_t)(cap / kOrdUnit) + V + 1;
+    w.ord_cnt = o;      o = align256(o + 4 * unit_rows * max_tiles);
+    w.ord_wstart = o;   o = align256(o + 4 * 8 * unit_rows);
     w.total = o;
     return w;
 }

@@ -53,7 +53,8 @@ k_count(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restri
 __global__ void __launch_bounds__(1024)
 k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* __restrict__ tile_start,
        uint32_t* __restrict__ tile_cursor, uint32_t* __restrict__ tile_order,
-       uint32_t* __restrict__ ranges, uint64_t* __restrict__ d_n_dup, uint32_t* err)
+       uint32_t* __restrict__ ranges, uint64_t* __restrict__ d_n_dup, uint32_t* err,
+       const unsigned long long* __restrict__ known_total = nullptr)
 {
     constexpr int NW = 32;
     __shared__ unsigned long long s_warp[NW];
@@ -83,7 +84,9 @@ k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* _
         if (lane == 31) s_total = incl;
     }
     __syncthreads();
-    const unsigned long long D = s_total;
+    // the depth-ordered path counts no duplicate when D exceeds the capacity and
+    // passes the exact D instead
+    const unsigned long long D = known_total ? *known_total : s_total;
     const bool overflow = D > cap;
     unsigned long long carry = s_warp[warp];
     for (int b0 = w0; b0 < w1; b0 += 32) {
@@ -576,7 +579,7 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
         }
         const unsigned long long th = (unsigned long long)tile << 32;
         for (int i = tid; i < L; i += kSortThreads) {
-            keys_out[s0 + i] = th | ka[i];
+            if (keys_out) keys_out[s0 + i] = th | ka[i];
             vals_out[s0 + i] = (uint32_t)a[ia[i]];
         }
         return;
@@ -609,8 +612,104 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
     const unsigned long long th = (unsigned long long)tile << 32;
     for (int i = tid; i < L; i += kSortThreads) {
         const unsigned long long k = a[i];
-        keys_out[s0 + i] = th | (k >> 32);
+        if (keys_out) keys_out[s0 + i] = th | (k >> 32);
         vals_out[s0 + i] = (uint32_t)k;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Depth-ordered binning.  Every tile list is the tile's duplicates in (depth
+// bits, id) order, and the depth of a (view, Gaussian) entry is the same in
+// every tile it touches.  So each view's visible entries are first sorted by
+// (depth bits, id) once -- a few million items: one duplicate per entry into
+// one of kDepthBins depth segments of its view (a monotone quantisation of the
+// depth bits between the view's least and greatest), then the segment sort
+// above -- and the tile duplicates are emitted in that order by an
+// order-keeping scatter.  The work is divided by duplicates, not entries: in
+// depth order the nearest Gaussians (the largest splats, hundreds of tiles
+// each) sit together, so equal runs of entries would carry very unequal work.
+// Each view's entries get a record (Gaussian, depth bits, tile rectangle) and
+// the exclusive prefix of their rectangle areas -- the index of each entry's
+// first duplicate.  A unit is kOrdUnit consecutive duplicates of one view
+// (one block, eight warps of kOrdWarpDups); the prefix pass also writes, for
+// every warp boundary, the entry holding that duplicate, so a warp starts
+// without a search and may begin or end inside an entry.  Per tile, a unit's
+// run starts at the sum of the earlier units' counts (a counting pass and a
+// scan over units), a warp's run inside it at the earlier warps' counts (a
+// counting pass inside the block), and a duplicate's place inside its warp's
+// run at the number of earlier lanes of its round with the same tile
+// (match-any) plus the earlier rounds' count.  The lists come out sorted: no
+// per-tile sort runs at all.
+// ---------------------------------------------------------------------------
+constexpr int kOrdWarpDups = kOrdUnit / 8;       // duplicates per warp of a unit (8 warps)
+// Words of the unit table (uint64), filled once the per-view totals are known.
+constexpr int kUnitFirst = 0;                      // [V + 1]: first unit of view v; [V]: all units
+constexpr int kUnitDv = GEVO_MAX_VIEWS + 1;        // [V]: duplicates of view v
+constexpr int kUnitVs = 2 * (GEVO_MAX_VIEWS + 1);  // [V]: first sorted position of view v
+constexpr int kUnitD = 3 * (GEVO_MAX_VIEWS + 1);   // [0]: D over all views
+
+// Duplicates [d0, d1) of one view in order.  rec and pre are the view's records
+// (Gaussian, depth bits, x0 | y0 << 16, width | height << 16) and the exclusive
+// prefix of their rectangle areas (pre[M] = the view's duplicate count), in
+// (depth bits, id) order; p is the entry holding duplicate d0.  The warp walks
+// 32 entries per round, lays their duplicates end to end and deals them to the
+// lanes 32 at a time; the round's first entry may have started before d0 and
+// its last may run past d1.  f(g, local tile, depth bits, valid) is called by
+// every lane once per 32 duplicates (valid false past the range), so f may use
+// warp collectives.
+template <typename F>
+__device__ __forceinline__ void walk_dups(int tx, const uint4* __restrict__ rec,
+                                          const unsigned long long* __restrict__ pre, int M,
+                                          int p, unsigned long long d0, unsigned long long d1,
+                                          F&& f)
+{
+    __shared__ int4 s_rect[8][32];     // x0, y0, width, first duplicate (from the round's start)
+    __shared__ uint2 s_gd[8][32];      // Gaussian, depth bits
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    unsigned long long cur = d0;
+    for (; cur < d1 && p < M; p += 32) {
+        const int q = p + lane;
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        unsigned long long a;
+        if (q < M) { r = rec[q]; a = pre[q]; }
+        else a = pre[M];
+        const int w = (int)(r.w & 0xffffu);
+        const int area = w * (int)(r.w >> 16);
+        const int excl = (int)(long long)(a - cur);   // negative only for a partial first entry
+        const unsigned long long rend =
+            min(d1, __shfl_sync(0xffffffffu, a + (unsigned long long)area, 31));
+        const int total = (int)(rend - cur);
+        const uint32_t nz = __ballot_sync(0xffffffffu, area > 0);
+        __syncwarp();   // the previous round's readers are done
+        if (area > 0) {
+            const int c = __popc(nz & lt);
+            s_rect[warp][c] = make_int4((int)(r.z & 0xffffu), (int)(r.z >> 16), w, excl);
+            s_gd[warp][c] = make_uint2(r.x, r.y);
+        }
+        __syncwarp();
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            const bool starts = area > 0 && excl >= k0 && excl < k0 + 32;
+            const uint32_t Ms = __reduce_or_sync(0xffffffffu, starts ? 1u << (excl - k0) : 0u);
+            const int before = __popc(__ballot_sync(0xffffffffu, area > 0 && excl < k0));
+            int tl = -1, gg = 0;
+            uint32_t db = 0u;
+            if (k < total) {
+                const int own = before + __popc(Ms & (0xffffffffu >> (31 - lane))) - 1;
+                const int4 rc = s_rect[warp][own];
+                const uint2 gd = s_gd[warp][own];
+                const int local = k - rc.w;
+                int qy = (int)((float)local * rcp_approx((float)rc.z));
+                if (qy * rc.z > local) qy--;
+                else if ((qy + 1) * rc.z <= local) qy++;
+                tl = (rc.y + qy) * tx + rc.x + (local - qy * rc.z);
+                gg = (int)gd.x;
+                db = gd.y;
+            }
+            f(gg, tl, db, k < total);
+        }
+        cur = rend;
     }
 }
 
@@ -618,6 +717,435 @@ k_segsort(const uint32_t* __restrict__ tile_order, const uint32_t* __restrict__ 
 // device (the attribute belongs to the device's context) and only upwards.
 // Host threads may sort concurrently, so the record sits behind a mutex.
 static std::mutex g_attr_mu;
+
+// Per view: max(~depth bits) (so the least depth is its complement), max(depth
+// bits) and the count of visible entries (radius > 0); per entry its depth bits
+// dk (kInvisible when radius <= 0: the bits of a positive depth are below it)
+// and, when visible, its tile rectangle rect (x0 | y0 << 16, width | height <<
+// 16).  Block (x, v) reduces 1024 entries of view v.
+constexpr uint32_t kInvisible = 0xffffffffu;
+__global__ void __launch_bounds__(256)
+k_ord_stat(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restrict__ radius,
+           const float4* __restrict__ rgbz, uint32_t* __restrict__ stat,
+           uint32_t* __restrict__ dk, uint2* __restrict__ rect)
+{
+    __shared__ uint32_t s_r[3][8];
+    const int v = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t vb = (size_t)v * n;
+    const int tx = L.tiles_x[v], ty = L.tiles_y[v];
+    uint32_t nmin = 0u, mx = 0u, cnt = 0u;
+    for (int g = blockIdx.x * 1024 + threadIdx.x; g < min(n, (int)(blockIdx.x + 1) * 1024); g += 256) {
+        const int r = radius[vb + g];
+        if (r <= 0) { dk[vb + g] = kInvisible; continue; }
+        const uint32_t d = __float_as_uint(__ldg(reinterpret_cast<const float*>(rgbz + vb + g) + 3));
+        const float2 m = xy[vb + g];
+        int x0, y0, x1, y1;
+        tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
+        dk[vb + g] = d;
+        rect[vb + g] = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16),
+                                  (uint32_t)(x1 - x0) | ((uint32_t)(y1 - y0) << 16));
+        nmin = max(nmin, ~d);
+        mx = max(mx, d);
+        cnt++;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nmin = max(nmin, __shfl_xor_sync(0xffffffffu, nmin, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) { s_r[0][warp] = nmin; s_r[1][warp] = mx; s_r[2][warp] = cnt; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) {
+            nmin = max(nmin, s_r[0][w]); mx = max(mx, s_r[1][w]); cnt += s_r[2][w];
+        }
+        if (cnt) {
+            atomicMax(stat + 4 * v, nmin);
+            atomicMax(stat + 4 * v + 1, mx);
+            atomicAdd(stat + 4 * v + 2, cnt);
+        }
+    }
+}
+
+// Depth segment of depth bits d in view v: a monotone map of [least, greatest]
+// onto 0 .. kDepthBins - 1.
+__device__ __forceinline__ int depth_segment(const uint32_t* stat, int v, uint32_t d)
+{
+    const uint32_t lo = ~stat[4 * v], hi = stat[4 * v + 1];
+    return v * kDepthBins +
+           (int)(((unsigned long long)(d - lo) * kDepthBins) / ((unsigned long long)(hi - lo) + 1ull));
+}
+
+// Count (SCATTER false) or place (SCATTER true) each visible entry in its depth
+// segment; block (x, v) takes kBinChunk entries of view v, kBinChunk / 256 per
+// thread.  The block counts its entries per segment in shared memory (the
+// shared atomic's old value ranks an entry inside the block's share); placing,
+// it reserves one run per (block, segment) with a single global atomic.  The
+// order inside a segment is left to the segment sort.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256)
+k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ stat,
+          uint32_t* __restrict__ seg_count, const uint32_t* __restrict__ seg_start,
+          uint32_t* __restrict__ seg_cursor, unsigned long long* __restrict__ b1)
+{
+    constexpr int PER = kBinChunk / 256;
+    __shared__ uint32_t s_h[kDepthBins];
+    const int v = blockIdx.y;
+    const size_t vb = (size_t)v * n;
+    for (int i = threadIdx.x; i < kDepthBins; i += blockDim.x) s_h[i] = 0u;
+    __syncthreads();
+    uint32_t d[PER];
+    int rank[PER];
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int g = blockIdx.x * kBinChunk + i * 256 + threadIdx.x;
+        d[i] = g < n ? dk[vb + g] : kInvisible;
+        rank[i] = d[i] != kInvisible
+                      ? (int)atomicAdd(s_h + (depth_segment(stat, v, d[i]) - v * kDepthBins), 1u)
+                      : 0;
+    }
+    __syncthreads();
+    if (!SCATTER) {
+        for (int i = threadIdx.x; i < kDepthBins; i += blockDim.x)
+            if (s_h[i]) atomicAdd(seg_count + v * kDepthBins + i, s_h[i]);
+        return;
+    }
+    for (int i = threadIdx.x; i < kDepthBins; i += blockDim.x)
+        if (s_h[i]) s_h[i] = seg_start[v * kDepthBins + i] +
+                             atomicAdd(seg_cursor + v * kDepthBins + i, s_h[i]);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        if (d[i] == kInvisible) continue;
+        const int g = blockIdx.x * kBinChunk + i * 256 + threadIdx.x;
+        const int sg = depth_segment(stat, v, d[i]) - v * kDepthBins;
+        b1[s_h[sg] + rank[i]] = ((unsigned long long)d[i] << 32) | (uint32_t)g;
+    }
+}
+
+// First sorted position of view v (the visible entries of earlier views).
+__device__ __forceinline__ uint32_t view_start(const uint32_t* stat, int v)
+{
+    uint32_t s = 0u;
+    for (int u = 0; u < v; u++) s += stat[4 * u + 2];
+    return s;
+}
+
+// Exclusive scan over the NT threads of the block; total gets the block's sum.
+// Every thread of the block must call it (it holds two barriers).
+template <int NT>
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long x,
+                                                              unsigned long long& total)
+{
+    __shared__ unsigned long long s_w[NT / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long y = lane < NT / 32 ? s_w[lane] : 0ull;
+        unsigned long long wi = y;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long z = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += z;
+        }
+        if (lane < NT / 32) s_w[lane] = wi - y;
+        if (lane == 31) s_w[NT / 32] = wi;
+    }
+    __syncthreads();
+    const unsigned long long r = s_w[warp] + incl - x;
+    total = s_w[NT / 32];
+    __syncthreads();   // s_w is free for the next call
+    return r;
+}
+
+// Per sorted entry p of view v: its record (Gaussian, depth bits,
+// x0 | y0 << 16, width | height << 16 of its tile rectangle) -- the depth bits
+// from the depth sort's keys, the rectangle gathered from the stat pass's; per
+// block of kOrdScanItems entries the sum of the rectangle areas, at
+// bsum[v gridDim.x + blockIdx.x].
+__global__ void __launch_bounds__(256)
+k_ord_rec(int n, const uint32_t* __restrict__ stat, const uint32_t* __restrict__ sorted,
+          const unsigned long long* __restrict__ dkeys, const uint2* __restrict__ rect,
+          uint4* __restrict__ rec, unsigned long long* __restrict__ bsum)
+{
+    const int v = blockIdx.y;
+    const int M = (int)stat[4 * v + 2];
+    const int p0 = blockIdx.x * kOrdScanItems;
+    if (p0 >= M) return;   // the whole block: before any barrier
+    const uint32_t vs = view_start(stat, v);
+    const size_t vb = (size_t)v * n;
+    const int p1 = min(M, p0 + kOrdScanItems);
+    unsigned long long sum = 0ull;
+    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const uint32_t g = sorted[vs + p];
+        const uint2 rc = rect[vb + g];
+        rec[vs + p] = make_uint4(g, (uint32_t)dkeys[vs + p], rc.x, rc.y);
+        sum += (unsigned long long)((rc.y & 0xffffu) * (rc.y >> 16));
+    }
+    unsigned long long total;
+    block_excl_scan<256>(sum, total);
+    if (threadIdx.x == 0) bsum[(size_t)v * gridDim.x + blockIdx.x] = total;
+}
+
+// One block.  Per view: the block sums become their exclusive running sums (in
+// place), the total is the view's duplicate count D_v, and the view's prefix
+// gets its end, pre[vs + v + M_v] = D_v.  Then the unit table: first unit of
+// each view (ceil(D_v / kOrdUnit) units each), D_v, the view's first sorted
+// position and D.  When D exceeds the capacity no unit is made, so the counting
+// and scatter passes do nothing and only D is reported.
+__global__ void __launch_bounds__(1024)
+k_ord_bscan(int V, int nbs, uint64_t cap, const uint32_t* __restrict__ stat,
+            unsigned long long* __restrict__ bsum, unsigned long long* __restrict__ units,
+            unsigned long long* __restrict__ pre)
+{
+    __shared__ unsigned long long s_dv[GEVO_MAX_VIEWS];
+    unsigned long long vs = 0ull;
+    for (int v = 0; v < V; v++) {
+        const uint32_t M = stat[4 * v + 2];
+        const int nb = (int)((M + kOrdScanItems - 1) / kOrdScanItems);
+        unsigned long long carry = 0ull;
+        for (int c0 = 0; c0 < nb; c0 += 1024) {   // the same trip count in every thread
+            const int i = c0 + threadIdx.x;
+            const unsigned long long x = i < nb ? bsum[(size_t)v * nbs + i] : 0ull;
+            unsigned long long tot;
+            const unsigned long long e = block_excl_scan<1024>(x, tot);
+            if (i < nb) bsum[(size_t)v * nbs + i] = carry + e;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) {
+            s_dv[v] = carry;
+            units[kUnitDv + v] = carry;
+            units[kUnitVs + v] = vs;
+            pre[vs + v + M] = carry;
+        }
+        vs += M;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long D = 0ull;
+        for (int v = 0; v < V; v++) D += s_dv[v];
+        const bool overflow = D > cap;
+        unsigned long long u = 0ull;
+        for (int v = 0; v < V; v++) {
+            units[kUnitFirst + v] = u;
+            if (!overflow) u += (s_dv[v] + kOrdUnit - 1) / kOrdUnit;
+        }
+        units[kUnitFirst + V] = u;
+        units[kUnitD] = D;
+    }
+}
+
+// Per sorted entry p of view v: pre[vs + v + p] = the index of its first
+// duplicate among the view's duplicates (the exclusive prefix of the areas in
+// (depth bits, id) order); and for every warp boundary j kOrdWarpDups that
+// falls inside its duplicates, wstart[8 (first unit of v) + j] = p.  Thread i
+// of block (x, v) takes the kOrdScanItems / 256 consecutive entries from
+// x kOrdScanItems + i kOrdScanItems / 256.
+__global__ void __launch_bounds__(256)
+k_ord_pre(const uint32_t* __restrict__ stat, const unsigned long long* __restrict__ units,
+          const uint4* __restrict__ rec, const unsigned long long* __restrict__ bsum,
+          uint64_t cap, unsigned long long* __restrict__ pre, uint32_t* __restrict__ wstart)
+{
+    constexpr int PER = kOrdScanItems / 256;
+    const int v = blockIdx.y;
+    const int M = (int)stat[4 * v + 2];
+    const int p0 = blockIdx.x * kOrdScanItems;
+    if (p0 >= M) return;   // the whole block: before any barrier
+    const unsigned long long vs = units[kUnitVs + v];
+    const bool keep = units[kUnitD] <= cap;
+    uint32_t* ws = wstart + units[kUnitFirst + v] * 8ull;
+    const uint32_t* wh = reinterpret_cast<const uint32_t*>(rec + vs) + 3;   // .w of each record
+    const int q0 = p0 + threadIdx.x * PER;
+    uint32_t area[PER];
+    unsigned long long sum = 0ull;
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int q = q0 + i;
+        uint32_t a = 0u;
+        if (q < M) {
+            const uint32_t x = wh[4 * (size_t)q];
+            a = (x & 0xffffu) * (x >> 16);
+        }
+        area[i] = a;
+        sum += a;
+    }
+    unsigned long long tot;
+    unsigned long long run =
+        bsum[(size_t)v * gridDim.x + blockIdx.x] + block_excl_scan<256>(sum, tot);
+    unsigned long long* pv = pre + vs + v;
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int q = q0 + i;
+        if (q < M) {
+            pv[q] = run;
+            if (keep && area[i] > 0u)
+                for (unsigned long long j = (run + kOrdWarpDups - 1) / kOrdWarpDups;
+                     j * kOrdWarpDups < run + area[i]; j++)
+                    ws[j] = (uint32_t)q;
+        }
+        run += area[i];
+    }
+}
+
+// View of unit u: first[v] <= u < first[v + 1] (the table's end is the unit count).
+__device__ __forceinline__ int view_of_unit(const unsigned long long* units, int u)
+{
+    int v = 0;
+    while (units[kUnitFirst + v + 1] <= (unsigned long long)u) v++;
+    return v;
+}
+
+// Per unit u and tile t of its view: the unit's duplicate count, at
+// cnt[u max_tiles + t].  A persistent grid walks the units.
+__global__ void __launch_bounds__(256)
+k_ord_count(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
+            const unsigned long long* __restrict__ units, const uint4* __restrict__ rec,
+            const unsigned long long* __restrict__ pre, const uint32_t* __restrict__ wstart,
+            uint32_t* __restrict__ cnt)
+{
+    extern __shared__ uint32_t s_hist[];
+    const int warp = threadIdx.x >> 5;
+    const int n_units = (int)units[kUnitFirst + L.n_views];
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int v = view_of_unit(units, u);
+        const int nt = L.tiles_x[v] * L.tiles_y[v];
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) s_hist[t] = 0u;
+        __syncthreads();
+        const unsigned long long Dv = units[kUnitDv + v];
+        const unsigned long long w0 =
+            (unsigned long long)(u - (int)units[kUnitFirst + v]) * kOrdUnit +
+            (unsigned long long)warp * kOrdWarpDups;
+        if (w0 < Dv) {
+            const unsigned long long vs = units[kUnitVs + v];
+            walk_dups(L.tiles_x[v], rec + vs, pre + vs + v, (int)stat[4 * v + 2],
+                      (int)wstart[(size_t)u * 8 + warp], w0, min(Dv, w0 + kOrdWarpDups),
+                      [&](int, int t, uint32_t, bool ok) {
+                          if (ok) atomicAdd(s_hist + t, 1u);
+                      });
+        }
+        __syncthreads();
+        uint32_t* dst = cnt + (size_t)u * max_tiles;
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) dst[t] = s_hist[t];
+        __syncthreads();
+    }
+}
+
+// Per global tile: its view's unit counts become their exclusive running sums
+// (in unit order, in place) and the total is the tile's count.
+__global__ void __launch_bounds__(256)
+k_ord_scan(gevo_layout L, int max_tiles, const unsigned long long* __restrict__ units,
+           uint32_t* __restrict__ cnt, uint32_t* __restrict__ tile_count)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.total_tiles) return;
+    const int v = view_of_tile(L, t);
+    uint32_t* c = cnt + (t - L.tile_base[v]);
+    const int u1 = (int)units[kUnitFirst + v + 1];
+    int u = (int)units[kUnitFirst + v];
+    uint32_t run = 0u;
+    for (; u + 8 <= u1; u += 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) x[i] = c[(size_t)(u + i) * max_tiles];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            c[(size_t)(u + i) * max_tiles] = run;
+            run += x[i];
+        }
+    }
+    for (; u < u1; u++) {
+        const uint32_t x = c[(size_t)u * max_tiles];
+        c[(size_t)u * max_tiles] = run;
+        run += x;
+    }
+    tile_count[t] = run;
+}
+
+// The order-keeping scatter, one unit per block at a time.  Shared memory: the
+// unit's first slot per tile [T_v], then per warp and tile a 16-bit running
+// offset (two tiles to a 32-bit word): a warp's kOrdWarpDups duplicates hold at
+// most that many of one tile and the unit's run of a tile at most kOrdUnit, so
+// 16 bits hold every count and offset.
+__global__ void __launch_bounds__(256)
+k_ord_scatter(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
+              const unsigned long long* __restrict__ units, const uint4* __restrict__ rec,
+              const unsigned long long* __restrict__ pre, const uint32_t* __restrict__ wstart,
+              const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ tile_start,
+              unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    extern __shared__ uint32_t s_dyn[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int n_units = (int)units[kUnitFirst + L.n_views];
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int v = view_of_unit(units, u);
+        const int nt = L.tiles_x[v] * L.tiles_y[v];
+        const int rw = (nt + 1) / 2;   // words per warp row
+        uint32_t* s_base = s_dyn;
+        uint32_t* s_rel = s_dyn + 2 * rw;
+        for (int i = threadIdx.x; i < 8 * rw; i += blockDim.x) s_rel[i] = 0u;
+        __syncthreads();
+        const unsigned long long Dv = units[kUnitDv + v];
+        const unsigned long long w0 =
+            (unsigned long long)(u - (int)units[kUnitFirst + v]) * kOrdUnit +
+            (unsigned long long)warp * kOrdWarpDups;
+        const unsigned long long w1 = min(Dv, w0 + kOrdWarpDups);
+        const unsigned long long vs = units[kUnitVs + v];
+        const uint4* rv = rec + vs;
+        const unsigned long long* pv = pre + vs + v;
+        const int M = (int)stat[4 * v + 2];
+        const int p = w0 < Dv ? (int)wstart[(size_t)u * 8 + warp] : 0;
+        const int tx = L.tiles_x[v];
+        uint32_t* my = s_rel + warp * rw;
+        if (w0 < Dv)
+            walk_dups(tx, rv, pv, M, p, w0, w1, [&](int, int t, uint32_t, bool ok) {
+                if (ok) atomicAdd(my + (t >> 1), 1u << ((t & 1) * 16));
+            });
+        __syncthreads();
+        // the unit's first slot per tile, and the warps' running offsets in warp order
+        const int tb = L.tile_base[v];
+        const uint32_t* off = cnt + (size_t)u * max_tiles;
+        for (int q = threadIdx.x; q < rw; q += blockDim.x) {
+            for (int h = 0; h < 2; h++) {
+                const int t = 2 * q + h;
+                if (t < nt) s_base[t] = tile_start[tb + t] + off[t];
+            }
+            uint32_t r0 = 0u, r1 = 0u;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                const uint32_t c = s_rel[w * rw + q];
+                s_rel[w * rw + q] = r0 | (r1 << 16);
+                r0 += c & 0xffffu;
+                r1 += c >> 16;
+            }
+        }
+        __syncthreads();
+        if (w0 < Dv)
+            walk_dups(tx, rv, pv, M, p, w0, w1, [&](int g, int t, uint32_t dbits, bool ok) {
+                const uint32_t peers =
+                    __match_any_sync(0xffffffffu, ok ? (uint32_t)t : 0xffffffffu);
+                if (ok) {
+                    const uint32_t o = (my[t >> 1] >> ((t & 1) * 16)) & 0xffffu;
+                    const uint32_t slot = s_base[t] + o + __popc(peers & lt);
+                    if (keys) keys[slot] = ((unsigned long long)(tb + t) << 32) | dbits;
+                    vals[slot] = (uint32_t)g;
+                }
+                __syncwarp();
+                if (ok && lane == __ffs(peers) - 1)
+                    atomicAdd(my + (t >> 1), (uint32_t)__popc(peers) << ((t & 1) * 16));
+                __syncwarp();
+            });
+        __syncthreads();
+    }
+}
 
 static void bin_attributes(size_t bin_smem)
 {
@@ -647,6 +1175,117 @@ static void segsort_attributes(size_t smem)
     }
 }
 
+static void ord_attributes(size_t smem)
+{
+    static size_t done[256] = {0};
+    int dev = 0;
+    if (smem <= 48 * 1024 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (smem > done[dev]) {
+        cudaFuncSetAttribute(k_ord_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_ord_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        done[dev] = smem;
+    }
+}
+
+// gevo_bin_sort on layouts whose views have at most kOrdMaxTiles tiles: the
+// per-view depth sort, then the order-keeping scatter (see above).
+static gevo_status bin_sort_ordered(const gevo_layout& L, int32_t n, const gevo_proj& proj,
+                                    uint64_t cap, uint64_t* keys, uint32_t* vals,
+                                    uint32_t* ranges, uint64_t* d_n_dup, char* ws,
+                                    const WsLayout& w, cudaStream_t st)
+{
+    const int V = L.n_views, T = L.total_tiles, S = V * kDepthBins;
+    uint32_t* err = reinterpret_cast<uint32_t*>(ws + w.err);
+    uint32_t* tile_count = reinterpret_cast<uint32_t*>(ws + w.tile_count);
+    uint32_t* tile_cursor = reinterpret_cast<uint32_t*>(ws + w.tile_cursor);
+    uint32_t* tile_order = reinterpret_cast<uint32_t*>(ws + w.tile_order);
+    uint32_t* tile_start = reinterpret_cast<uint32_t*>(ws + w.tile_start);
+    uint32_t* stat = reinterpret_cast<uint32_t*>(ws + w.ord_stat);
+    uint32_t* seg = reinterpret_cast<uint32_t*>(ws + w.ord_seg);
+    uint32_t* seg_count = seg;
+    uint32_t* seg_start = seg + S;
+    uint32_t* seg_cursor = seg + 2 * S + 1;
+    uint32_t* seg_order = seg + 3 * S + 1;
+    uint32_t* seg_ranges = seg + 4 * S + 1;
+    uint64_t* n_vis = reinterpret_cast<uint64_t*>(ws + w.ord_total);
+    uint32_t* err1 = reinterpret_cast<uint32_t*>(ws + w.ord_total + 8);
+    auto* b1 = reinterpret_cast<unsigned long long*>(ws + w.ord_b1);
+    auto* b2 = reinterpret_cast<unsigned long long*>(ws + w.ord_b2);
+    uint32_t* sorted = reinterpret_cast<uint32_t*>(ws + w.ord_vals);
+    auto* rec = reinterpret_cast<uint4*>(ws + w.ord_b1);   // b1 is free once the depth sort ends
+    uint32_t* dk = reinterpret_cast<uint32_t*>(ws + w.ord_vals);   // read before the sort writes ids
+    auto* rect = reinterpret_cast<uint2*>(ws + w.ord_pre);         // read before the prefix is written
+    auto* dkeys = reinterpret_cast<unsigned long long*>(ws + w.ord_dkeys);
+    auto* pre = reinterpret_cast<unsigned long long*>(ws + w.ord_pre);
+    auto* bsum = reinterpret_cast<unsigned long long*>(ws + w.ord_bsum);
+    auto* units = reinterpret_cast<unsigned long long*>(ws + w.ord_units);
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(ws + w.ord_cnt);
+    uint32_t* wstart = reinterpret_cast<uint32_t*>(ws + w.ord_wstart);
+    const auto* xy = reinterpret_cast<const float2*>(proj.xy);
+    const auto* rgbz = reinterpret_cast<const float4*>(proj.rgb_depth);
+    const uint64_t cap1 = (uint64_t)V * (uint64_t)n;
+    int max_tiles = 0;
+    for (int v = 0; v < V; v++) max_tiles = std::max(max_tiles, L.tiles_x[v] * L.tiles_y[v]);
+    const int nbx = (n + kBinChunk - 1) / kBinChunk;
+    const int nbs = (n + kOrdScanItems - 1) / kOrdScanItems;
+
+    if (cudaMemsetAsync(stat, 0, 16 * (size_t)V, st) != cudaSuccess) return GEVO_ERR_CUDA;
+    if (n > 0) {
+        // 1. each view's visible entries in (depth bits, id) order
+        if (cudaMemsetAsync(seg_count, 0, 4 * (size_t)S, st) != cudaSuccess) return GEVO_ERR_CUDA;
+        k_ord_stat<<<dim3((n + 1023) / 1024, V), 256, 0, st>>>(L, n, xy, proj.radius, rgbz, stat,
+                                                                dk, rect);
+        GEVO_CHECK_LAUNCH();
+        k_ord_seg<false><<<dim3(nbx, V), 256, 0, st>>>(n, dk, stat, seg_count, nullptr, nullptr,
+                                                        nullptr);
+        GEVO_CHECK_LAUNCH();
+        k_scan<<<1, 1024, 0, st>>>(S, cap1, seg_count, seg_start, seg_cursor, seg_order,
+                                   seg_ranges, n_vis, err1);
+        GEVO_CHECK_LAUNCH();
+        k_ord_seg<true><<<dim3(nbx, V), 256, 0, st>>>(n, dk, stat, nullptr, seg_start, seg_cursor,
+                                                       b1);
+        GEVO_CHECK_LAUNCH();
+        const size_t ssmem = (sizeof(uint32_t) + sizeof(uint16_t)) * 2 * kSortSmemItems;
+        segsort_attributes(ssmem);
+        k_segsort<<<S, kSortThreads, ssmem, st>>>(seg_order, seg_start, seg_count, n_vis, cap1,
+                                                  b1, b2, dkeys, sorted);
+        GEVO_CHECK_LAUNCH();
+        // 2. records and the block sums of their areas
+        k_ord_rec<<<dim3(nbs, V), 256, 0, st>>>(n, stat, sorted, dkeys, rect, rec, bsum);
+        GEVO_CHECK_LAUNCH();
+    }
+    // 3. per-view totals, the unit table, the duplicate prefix and warp starts
+    k_ord_bscan<<<1, 1024, 0, st>>>(V, nbs, cap, stat, bsum, units, pre);
+    GEVO_CHECK_LAUNCH();
+    if (n > 0) {
+        k_ord_pre<<<dim3(nbs, V), 256, 0, st>>>(stat, units, rec, bsum, cap, pre, wstart);
+        GEVO_CHECK_LAUNCH();
+    }
+    // 4. per (unit, tile) counts, their running sums over units, the tile totals
+    const size_t osmem = sizeof(uint32_t) * 10 * (size_t)((max_tiles + 1) / 2);
+    ord_attributes(osmem);
+    const uint64_t unit_rows = cap / kOrdUnit + (uint64_t)V + 1;
+    const int ugrid = (int)std::max<uint64_t>(1, std::min<uint64_t>(unit_rows, (uint64_t)sm_count() * 8));
+    k_ord_count<<<ugrid, 256, sizeof(uint32_t) * (size_t)max_tiles, st>>>(
+        L, max_tiles, stat, units, rec, pre, wstart, cnt);
+    GEVO_CHECK_LAUNCH();
+    k_ord_scan<<<(T + 255) / 256, 256, 0, st>>>(L, max_tiles, units, cnt, tile_count);
+    GEVO_CHECK_LAUNCH();
+    // 5. tile starts, ranges, D, heaviest-first order, the capacity check
+    k_scan<<<1, 1024, 0, st>>>(T, cap, tile_count, tile_start, tile_cursor, tile_order, ranges,
+                               d_n_dup, err, units + kUnitD);
+    GEVO_CHECK_LAUNCH();
+    // 6. the duplicates, emitted in order
+    if (cap > 0) {
+        k_ord_scatter<<<ugrid, 256, osmem, st>>>(L, max_tiles, stat, units, rec, pre, wstart, cnt,
+                                                 tile_start,
+                                                 reinterpret_cast<unsigned long long*>(keys), vals);
+        GEVO_CHECK_LAUNCH();
+    }
+    return GEVO_OK;
+}
+
 }  // namespace gevo
 
 using namespace gevo;
@@ -658,7 +1297,7 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
 {
     if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->radius ||
         !proj->rgb_depth || !ranges || !d_n_dup || !workspace || !gevo_aligned(workspace, 256) ||
-        (dup_capacity > 0 && (!keys || !vals)) || dup_capacity > 0xffffffffull)
+        (dup_capacity > 0 && !vals) || dup_capacity > 0xffffffffull)
         return GEVO_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     const WsLayout w = ws_layout(*layout, n, dup_capacity);
@@ -672,6 +1311,14 @@ extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const
     auto* bucket2 = reinterpret_cast<unsigned long long*>(ws + w.dup_tmp2);
     uint32_t* blk_off = reinterpret_cast<uint32_t*>(ws + w.blk_off);
     const int T = layout->total_tiles;
+    {
+        int mt = 0;
+        for (int v = 0; v < layout->n_views; v++)
+            mt = std::max(mt, layout->tiles_x[v] * layout->tiles_y[v]);
+        if (mt <= kOrdMaxTiles)
+            return bin_sort_ordered(*layout, n, *proj, dup_capacity, keys, vals, ranges, d_n_dup,
+                                    ws, w, st);
+    }
 
     if (cudaMemsetAsync(tile_count, 0, sizeof(uint32_t) * T, st) != cudaSuccess) return GEVO_ERR_CUDA;
     const size_t total = (size_t)layout->n_views * n;
@@ -755,7 +1402,7 @@ extern "C" gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t 
                                              uint64_t* d_n_dup, void* stream)
 {
     if (!layout || !gevo::layout_valid(*layout) || n < 0 || !proj || !proj->xy || !proj->radius ||
-        !proj->rgb_depth || !ranges || !d_n_dup || (dup_capacity > 0 && (!keys || !vals)))
+        !proj->rgb_depth || !ranges || !d_n_dup || (dup_capacity > 0 && !vals))
         return GEVO_ERR_INVALID;
     if (dup_capacity > GEVO_NOALLOC_MAX_DUPS || layout->total_tiles > GEVO_NOALLOC_MAX_TILES)
         return GEVO_ERR_SCRATCH_LIMIT;

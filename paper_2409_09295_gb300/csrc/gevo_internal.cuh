@@ -39,8 +39,32 @@ struct WsLayout {
     size_t dxi_acc;      // float [V][6]
     size_t core;         // bytes up to here (the no-allocation sort uses only these)
     size_t blk_off;      // uint32 [ceil(n / 2048)][T]: each binning block's run offset per tile
+    // depth-ordered binning (gevo_bin_sort on views of at most kOrdMaxTiles tiles)
+    size_t ord_stat;     // uint32 [V][4]: max(~depth bits), max(depth bits), visible count
+    size_t ord_seg;      // uint32 [5][V * kDepthBins (+1)]: count, start, cursor, order, and
+                         // ranges [V * kDepthBins][2] of the depth segments
+    size_t ord_total;    // uint64 visible entries + uint32 scratch error word
+    size_t ord_b1;       // uint64 [V * n] (depth bits << 32 | id), by depth segment; once
+                         // the depth sort is done, uint4 [V * n] records (id, depth bits,
+                         // tile rectangle) in sorted order
+    size_t ord_b2;       // uint64 [V * n] ping-pong of long segments
+    size_t ord_vals;     // uint32 [V * n]: each entry's depth bits (id order) until the depth
+                         // sort writes each view's visible ids in (depth bits, id) order
+    size_t ord_dkeys;    // uint64 [V * n]: the depth sort's keys (segment << 32 | depth bits)
+    size_t ord_pre;      // uint64 [V * n + V + 1]: first the uint2 tile rectangle of each
+                         // visible entry (id order), then per view the exclusive prefix of
+                         // the rectangle areas (first duplicate of each entry) and its end
+    size_t ord_bsum;     // uint64 [V * (n / kOrdScanItems + 1)]: block sums of that scan
+    size_t ord_units;    // uint64 [4 * (GEVO_MAX_VIEWS + 1)]: the unit table
+    size_t ord_cnt;      // uint32 [(cap / kOrdUnit + V + 1) * max tiles]: per (unit, tile)
+                         // counts, then their running sums over units
+    size_t ord_wstart;   // uint32 [(cap / kOrdUnit + V + 1) * 8]: first entry of each warp
     size_t total;
 };
+constexpr int kDepthBins = 512;     // depth segments per view of the per-view depth sort
+constexpr int kOrdMaxTiles = 8192;  // views with more tiles take the bucket-and-sort path
+constexpr int kOrdUnit = 16384;     // duplicates per block of the order-keeping passes
+constexpr int kOrdScanItems = 4096; // entries per block of the prefix scan
 WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap);
 
 // Gaussians per binning block of one view (the binning kernels' chunk).

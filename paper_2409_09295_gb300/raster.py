@@ -44,11 +44,13 @@ class Pipeline:
     """Device buffers + the stage calls for one configuration.
 
     sizes: list of (W, H) per view.  colour: "rgb" or "sh" (with sh_degree).
-    dup_capacity: (Gaussian, tile) pairs the sort may hold."""
+    dup_capacity: (Gaussian, tile) pairs the sort may hold.  keep_keys: also
+    write the sorted 64-bit keys (the renderers read only the ids and ranges)."""
 
     def __init__(self, n: int, sizes, dup_capacity: int, colour: str = "rgb", sh_degree: int = 0,
-                 device="cuda", tuning=None):
+                 device="cuda", tuning=None, keep_keys: bool = False):
         self.n = int(n)
+        self.keep_keys = bool(keep_keys)
         self.sizes = [(int(w), int(h)) for w, h in sizes]
         self.V = len(self.sizes)
         self.device = torch.device(device)
@@ -96,7 +98,8 @@ class Pipeline:
         self.capacity = max(int(dup_capacity), 1)
         nbytes = abi.gevo_workspace_bytes(self.layout, self.n, self.capacity)
         self.ws = torch.zeros(nbytes, dtype=torch.uint8, device=self.device)
-        self.keys = torch.zeros(self.capacity, dtype=torch.int64, device=self.device)
+        self.keys = (torch.zeros(self.capacity, dtype=torch.int64, device=self.device)
+                     if self.keep_keys else None)
         self.vals = torch.zeros(self.capacity, dtype=torch.int32, device=self.device)
 
     # ---- per-view views of the planar outputs -------------------------------------------

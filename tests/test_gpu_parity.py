@@ -29,7 +29,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_2409_09295_gb300 import raster  # noqa: E402
+from paper_2409_09295_gb300 import _abi, raster  # noqa: E402
 
 TUNINGS = [dict(threads_per_tile=256, persistent=0, blocks_per_sm=0),
            dict(threads_per_tile=128, persistent=1, blocks_per_sm=0),
@@ -102,7 +102,7 @@ def test_bin_sort_bit_exact(case):
             rec["opacity"] = np.zeros(0, np.float32)
     ref = oracle.bin_f32(sizes, rec["xy"], rec["radius"], rec["depth"])
     D = ref["n_dup"]
-    pipe = raster.Pipeline(n, sizes, max(D, 1))
+    pipe = raster.Pipeline(n, sizes, max(D, 1), keep_keys=True)
     if n > 0:
         upload_records(pipe, rec)
     pipe.bin_sort()
@@ -112,6 +112,14 @@ def test_bin_sort_bit_exact(case):
     np.testing.assert_array_equal(_np(pipe.ranges).view(np.uint32), ref["ranges"])
     np.testing.assert_array_equal(_np(pipe.keys)[:D].view(np.uint64), ref["keys"])
     np.testing.assert_array_equal(_np(pipe.vals)[:D].view(np.uint32), ref["vals"])
+    # without keys (what the renderers need): the same ids and ranges
+    vals2, ranges2 = torch.zeros_like(pipe.vals), torch.ones_like(pipe.ranges)
+    n_dup2 = torch.zeros_like(pipe.n_dup)
+    _abi.gevo_bin_sort(pipe.layout, n, pipe.proj, pipe.capacity, None, vals2, ranges2, n_dup2,
+                       pipe.ws)
+    torch.cuda.synchronize()
+    assert pipe.last_error() == 0 and int(n_dup2.item()) == D
+    assert torch.equal(ranges2, pipe.ranges) and torch.equal(vals2[:D], pipe.vals[:D])
     lens = np.diff(ref["ranges"].astype(np.int64), axis=1)
     if case == "crowded_tile":
         assert lens.max() > 4096  # global-memory path

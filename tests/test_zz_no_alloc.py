@@ -34,7 +34,7 @@ def test_noalloc_sort_matches_workspace_sort_on_consecutive_calls():
              ([(96, 64)], 2500, 62, (0.5, 40.0))]   # second call: fewer tiles, fewer duplicates
     for sizes, n, seed, sig in cases:
         rec = scenes.random_records(sizes, n, seed=seed, sigma_px=sig)
-        pipe = raster.Pipeline(n, sizes, 400_000)
+        pipe = raster.Pipeline(n, sizes, 400_000, keep_keys=True)
         _upload(pipe, rec)
         pipe.bin_sort()
         D = int(pipe.n_dup.item())
@@ -50,6 +50,11 @@ def test_noalloc_sort_matches_workspace_sort_on_consecutive_calls():
         assert torch.equal(ranges, pipe.ranges)
         assert torch.equal(keys[:D], pipe.keys[:D])
         assert torch.equal(vals[:D], pipe.vals[:D])
+        vals_only = torch.zeros_like(pipe.vals)   # keys left out: the same ids
+        _abi.gevo_bin_sort_noalloc(pipe.layout, n, pipe.proj, pipe.capacity, None, vals_only,
+                                   ranges, n_dup)
+        torch.cuda.synchronize()
+        assert torch.equal(vals_only[:D], pipe.vals[:D])
         # and, since it runs other binning kernels, bit for bit against the oracle
         ref = oracle.bin_f32(sizes, rec["xy"], rec["radius"], rec["depth"])
         assert ref["n_dup"] == D
@@ -61,7 +66,7 @@ def test_noalloc_sort_matches_workspace_sort_on_consecutive_calls():
 def test_noalloc_sort_reports_overflow_through_the_count():
     sizes = [(64, 48)]
     rec = scenes.random_records(sizes, 500, seed=63)
-    pipe = raster.Pipeline(500, sizes, 100_000)
+    pipe = raster.Pipeline(500, sizes, 100_000, keep_keys=True)
     _upload(pipe, rec)
     pipe.bin_sort()
     D = int(pipe.n_dup.item())
