@@ -379,13 +379,16 @@ def main():
     param_b = 4 * (3 + 3 + 4 + 1 + 3 * K)
     work = {  # (bound, algorithmic amount per launch, unit)
         "project": ("hbm", param_b * N + 48 * vis + 8 * (VN - vis), "GB/s"),
-        "bin_sort": ("hbm", 24 * VN + 4 * vis + 28 * D + 16 * rep.pipe.T, "GB/s"),
+        "bin_sort": ("hbm", sort_bytes(rep, VN, vis, D), "GB/s"),
         "render_fwd": ("alu", FLOP_EXAMINE * E_fwd + FLOP_BLEND_FWD * B, "TFLOP/s"),
         "loss": ("hbm", 48 * P + 4 * VN + 40 * vis, "GB/s"),
         "render_bwd": ("alu", FLOP_EXAMINE * E_bwd + FLOP_BLEND_BWD * B, "TFLOP/s"),
         "project_bwd": ("hbm", 2 * param_b * N + 4 * VN + 40 * vis, "GB/s"),
     }
-    kernels = {"project": "k_project_fwd", "bin_sort": "k_count_off+k_scan+k_scatter_off+k_segsort",
+    n_sort = _abi.gevo_bin_sort_launches(rep.pipe.layout, rep.pipe.n, rep.pipe.capacity)
+    kernels = {"project": "k_project_fwd",
+               "bin_sort": ("depth-ordered path, 12 kernels (k_ord_scatter the longest)"
+                            if n_sort == 12 else "k_count_off+k_scan+k_scatter_off+k_segsort"),
                "render_fwd": "k_render_fwd", "loss": "k_loss_l1+k_zero_grad2d",
                "render_bwd": "k_render_bwd", "project_bwd": "k_project_bwd_geo+k_project_bwd_col"}
     roofs = {}
@@ -612,10 +615,29 @@ def mapping_section():
 
 
 def launches_per_step(rep) -> int:
-    """Kernels of ours launched per step: project (1), bin_sort (count, scan,
-    scatter, segsort = 4), render_fwd (1), loss (1), grad2d_zero (1), render_bwd
-    (1), project_bwd (geometry, plus the SH-colour kernel when colours are SH)."""
-    return 1 + 4 + 1 + 1 + 1 + 1 + (1 if rep.pipe.colour == "rgb" else 2)
+    """Kernels of ours launched per step: project (1), bin_sort (as the library
+    reports for these sizes: 12 on the depth-ordered path), render_fwd (1), loss
+    (1), grad2d_zero (1), render_bwd (1), project_bwd (geometry, plus the
+    SH-colour kernel when colours are SH)."""
+    from paper_2409_09295_gb300 import _abi
+    p = rep.pipe
+    sort = _abi.gevo_bin_sort_launches(p.layout, p.n, p.capacity)
+    return 1 + sort + 1 + 1 + 1 + 1 + (1 if p.colour == "rgb" else 2)
+
+
+def sort_bytes(rep, VN: int, vis: int, D: int) -> int:
+    """Bytes the depth-ordered sort's passes move (model): per (view, Gaussian)
+    entry the radius read and the depth-bits word written once and read twice
+    (16 B); per visible entry 168 B (depth and mean read, rectangle written, the
+    depth-segment scatter, the per-view depth sort's read and two writes, the
+    record gather and write, the area prefix, three walks over records and
+    prefixes); per duplicate the 4-byte id written; per (unit of 8192
+    duplicates, tile) 16 B of counts (written, scanned in place, read); per tile
+    the range and its start."""
+    T = rep.pipe.T
+    units = -(-D // 8192) + rep.pipe.V
+    max_tiles = max(-(-w // 16) * -(-h // 16) for w, h in rep.pipe.sizes)
+    return 16 * VN + 168 * vis + 4 * D + 16 * units * max_tiles + 12 * T
 
 
 if __name__ == "__main__":

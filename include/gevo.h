@@ -205,6 +205,14 @@ gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const gevo_proj*
                           uint64_t dup_capacity, uint64_t* keys, uint32_t* vals,
                           uint32_t* ranges, uint64_t* d_n_dup, void* workspace, void* stream);
 
+/* Number of kernels gevo_bin_sort launches for these sizes (for sizing CUDA
+ * graphs and accounting launches): the views' largest tile count picks the
+ * implementation -- up to 8192 tiles per view, each view's visible entries are
+ * sorted by depth once and the duplicates emitted in order (12 kernels); above
+ * that, duplicates are bucketed by tile and each bucket sorted (4 kernels).
+ * Fewer when n or dup_capacity is 0.  -1 for an invalid layout or n < 0. */
+int32_t gevo_bin_sort_launches(const gevo_layout* layout, int32_t n, uint64_t dup_capacity);
+
 /* Same operation and outputs as gevo_bin_sort (keys may be NULL there too),
  * for callers that cannot allocate device memory: no workspace argument, and the call itself allocates
  * nothing (no cudaMalloc, no allocating library routine).  Such callers include

@@ -88,7 +88,7 @@ EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin
            "gevo_last_error", "gevo_status_str", "gevo_version", "gevo_bin_sort_noalloc",
            "gevo_grad2d_zero", "gevo_gemm_bf16", "gevo_loss_l1_err", "gevo_render_bwd_active",
            "gevo_active_set", "gevo_project_bwd_active", "gevo_render_fwd_active",
-           "gevo_render_fwd_counts"]
+           "gevo_render_fwd_counts", "gevo_bin_sort_launches"]
 
 # Every symbol include/gevo_prior.h declares, with its argument kinds
 # (i: int32, u: uint32, I: int64, f: float, p: pointer; the last p is the stream).
@@ -151,6 +151,8 @@ def load(build_if_missing: bool = True):
     L.gevo_workspace_bytes.restype = ctypes.c_size_t
     L.gevo_project.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), vp, vp]
     L.gevo_bin_sort.argtypes = [P(Layout), i32, P(Proj), u64, vp, vp, vp, vp, vp, vp]
+    L.gevo_bin_sort_launches.argtypes = [P(Layout), i32, u64]
+    L.gevo_bin_sort_launches.restype = i32
     L.gevo_bin_sort_noalloc.argtypes = [P(Layout), i32, P(Proj), u64, vp, vp, vp, vp, vp]
     L.gevo_bin_sort_noalloc.restype = ctypes.c_int
     L.gevo_render_fwd.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp, vp,
@@ -233,6 +235,11 @@ def gevo_layout_init(widths, heights) -> Layout:
 
 def gevo_workspace_bytes(layout: Layout, n: int, dup_capacity: int) -> int:
     return int(load().gevo_workspace_bytes(ctypes.byref(layout), int(n), int(dup_capacity)))
+
+
+def gevo_bin_sort_launches(layout: Layout, n: int, dup_capacity: int) -> int:
+    """Kernels gevo_bin_sort launches for these sizes (-1: invalid arguments)."""
+    return int(load().gevo_bin_sort_launches(ctypes.byref(layout), int(n), int(dup_capacity)))
 
 
 def gaussians_struct(g: dict) -> Gaussians:

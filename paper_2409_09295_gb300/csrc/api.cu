@@ -41,6 +41,7 @@ WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap)
     const size_t unit_rows = (size_t)(cap / kOrdUnit) + V + 1;
     w.ord_cnt = o;      o = align256(o + 4 * unit_rows * max_tiles);
     w.ord_wstart = o;   o = align256(o + 4 * 8 * unit_rows);
+    w.ord_wofs = o;     o = align256(o + 4 * 8 * ((max_tiles + 1) / 2) * unit_rows);
     w.total = o;
     return w;
 }

@@ -734,8 +734,17 @@ k_ord_stat(gevo_layout L, int n, const float2* __restrict__ xy, const int* __res
     const size_t vb = (size_t)v * n;
     const int tx = L.tiles_x[v], ty = L.tiles_y[v];
     uint32_t nmin = 0u, mx = 0u, cnt = 0u;
-    for (int g = blockIdx.x * 1024 + threadIdx.x; g < min(n, (int)(blockIdx.x + 1) * 1024); g += 256) {
-        const int r = radius[vb + g];
+    int rr[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {   // the four radii in flight together
+        const int g = blockIdx.x * 1024 + i * 256 + threadIdx.x;
+        rr[i] = g < n ? radius[vb + g] : 0;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int g = blockIdx.x * 1024 + i * 256 + threadIdx.x;
+        if (g >= n) break;
+        const int r = rr[i];
         if (r <= 0) { dk[vb + g] = kInvisible; continue; }
         const uint32_t d = __float_as_uint(__ldg(reinterpret_cast<const float*>(rgbz + vb + g) + 3));
         const float2 m = xy[vb + g];
@@ -768,13 +777,19 @@ k_ord_stat(gevo_layout L, int n, const float2* __restrict__ xy, const int* __res
     }
 }
 
-// Depth segment of depth bits d in view v: a monotone map of [least, greatest]
-// onto 0 .. kDepthBins - 1.
-__device__ __forceinline__ int depth_segment(const uint32_t* stat, int v, uint32_t d)
+// Depth segments of view v: d -> ((d - least) mul) >> 32 with
+// mul = floor(2^32 kDepthBins / (greatest - least + 1)), a monotone map of the
+// view's depth bits onto 0 .. kDepthBins - 1 (the product stays below
+// kDepthBins 2^32) with one division per block instead of one per entry.
+__device__ __forceinline__ unsigned long long depth_mul(const uint32_t* stat, int v)
 {
     const uint32_t lo = ~stat[4 * v], hi = stat[4 * v + 1];
-    return v * kDepthBins +
-           (int)(((unsigned long long)(d - lo) * kDepthBins) / ((unsigned long long)(hi - lo) + 1ull));
+    return ((unsigned long long)kDepthBins << 32) / ((unsigned long long)(hi - lo) + 1ull);
+}
+
+__device__ __forceinline__ int depth_segment(uint32_t lo, unsigned long long mul, uint32_t d)
+{
+    return (int)(((unsigned long long)(d - lo) * mul) >> 32);
 }
 
 // Count (SCATTER false) or place (SCATTER true) each visible entry in its depth
@@ -791,18 +806,25 @@ k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ s
 {
     constexpr int PER = kBinChunk / 256;
     __shared__ uint32_t s_h[kDepthBins];
+    __shared__ unsigned long long s_mul;
     const int v = blockIdx.y;
     const size_t vb = (size_t)v * n;
     for (int i = threadIdx.x; i < kDepthBins; i += blockDim.x) s_h[i] = 0u;
+    if (threadIdx.x == 0) s_mul = depth_mul(stat, v);
     __syncthreads();
+    const uint32_t lo = ~stat[4 * v];
+    const unsigned long long mul = s_mul;
     uint32_t d[PER];
     int rank[PER];
 #pragma unroll
-    for (int i = 0; i < PER; i++) {
+    for (int i = 0; i < PER; i++) {   // every load in flight before the first atomic
         const int g = blockIdx.x * kBinChunk + i * 256 + threadIdx.x;
         d[i] = g < n ? dk[vb + g] : kInvisible;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
         rank[i] = d[i] != kInvisible
-                      ? (int)atomicAdd(s_h + (depth_segment(stat, v, d[i]) - v * kDepthBins), 1u)
+                      ? (int)atomicAdd(s_h + depth_segment(lo, mul, d[i]), 1u)
                       : 0;
     }
     __syncthreads();
@@ -819,7 +841,7 @@ k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ s
     for (int i = 0; i < PER; i++) {
         if (d[i] == kInvisible) continue;
         const int g = blockIdx.x * kBinChunk + i * 256 + threadIdx.x;
-        const int sg = depth_segment(stat, v, d[i]) - v * kDepthBins;
+        const int sg = depth_segment(lo, mul, d[i]);
         b1[s_h[sg] + rank[i]] = ((unsigned long long)d[i] << 32) | (uint32_t)g;
     }
 }
@@ -895,48 +917,52 @@ k_ord_rec(int n, const uint32_t* __restrict__ stat, const uint32_t* __restrict__
     if (threadIdx.x == 0) bsum[(size_t)v * gridDim.x + blockIdx.x] = total;
 }
 
-// One block.  Per view: the block sums become their exclusive running sums (in
-// place), the total is the view's duplicate count D_v, and the view's prefix
-// gets its end, pre[vs + v + M_v] = D_v.  Then the unit table: first unit of
-// each view (ceil(D_v / kOrdUnit) units each), D_v, the view's first sorted
-// position and D.  When D exceeds the capacity no unit is made, so the counting
-// and scatter passes do nothing and only D is reported.
+// One block.  Per view (one warp each): the block sums become their exclusive
+// running sums (in place) and the total is the view's duplicate count D_v.
+// Then, in one thread, the unit table -- first unit of each view
+// (ceil(D_v / kOrdUnit) units each), D_v, the view's first sorted position and D
+// -- and each view's prefix end pre[vs + v + M_v] = D_v.  When D exceeds the
+// capacity no unit is made, so the counting and scatter passes do nothing and
+// only D is reported.
 __global__ void __launch_bounds__(1024)
 k_ord_bscan(int V, int nbs, uint64_t cap, const uint32_t* __restrict__ stat,
             unsigned long long* __restrict__ bsum, unsigned long long* __restrict__ units,
             unsigned long long* __restrict__ pre)
 {
     __shared__ unsigned long long s_dv[GEVO_MAX_VIEWS];
-    unsigned long long vs = 0ull;
-    for (int v = 0; v < V; v++) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int v = warp; v < V; v += 32) {
         const uint32_t M = stat[4 * v + 2];
         const int nb = (int)((M + kOrdScanItems - 1) / kOrdScanItems);
         unsigned long long carry = 0ull;
-        for (int c0 = 0; c0 < nb; c0 += 1024) {   // the same trip count in every thread
-            const int i = c0 + threadIdx.x;
+        for (int c0 = 0; c0 < nb; c0 += 32) {
+            const int i = c0 + lane;
             const unsigned long long x = i < nb ? bsum[(size_t)v * nbs + i] : 0ull;
-            unsigned long long tot;
-            const unsigned long long e = block_excl_scan<1024>(x, tot);
-            if (i < nb) bsum[(size_t)v * nbs + i] = carry + e;
-            carry += tot;
+            unsigned long long incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (i < nb) bsum[(size_t)v * nbs + i] = carry + incl - x;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
         }
-        if (threadIdx.x == 0) {
-            s_dv[v] = carry;
-            units[kUnitDv + v] = carry;
-            units[kUnitVs + v] = vs;
-            pre[vs + v + M] = carry;
-        }
-        vs += M;
+        if (lane == 0) s_dv[v] = carry;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long D = 0ull;
+        unsigned long long D = 0ull, vs = 0ull;
         for (int v = 0; v < V; v++) D += s_dv[v];
         const bool overflow = D > cap;
         unsigned long long u = 0ull;
         for (int v = 0; v < V; v++) {
+            const uint32_t M = stat[4 * v + 2];
             units[kUnitFirst + v] = u;
+            units[kUnitDv + v] = s_dv[v];
+            units[kUnitVs + v] = vs;
+            pre[vs + v + M] = s_dv[v];
             if (!overflow) u += (s_dv[v] + kOrdUnit - 1) / kOrdUnit;
+            vs += M;
         }
         units[kUnitFirst + V] = u;
         units[kUnitD] = D;
@@ -1004,20 +1030,27 @@ __device__ __forceinline__ int view_of_unit(const unsigned long long* units, int
 }
 
 // Per unit u and tile t of its view: the unit's duplicate count, at
-// cnt[u max_tiles + t].  A persistent grid walks the units.
+// cnt[u max_tiles + t], and per warp w of the unit the number of the unit's
+// duplicates of tile t that earlier warps hold -- 16 bits, two tiles to a word,
+// at wofs[(8u + w) rwm + t / 2] with rwm = ceil(max_tiles / 2).  A warp's
+// kOrdWarpDups duplicates hold at most that many of one tile and the unit at
+// most kOrdUnit, so 16 bits hold every count and offset.  A persistent grid
+// walks the units.
 __global__ void __launch_bounds__(256)
 k_ord_count(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
             const unsigned long long* __restrict__ units, const uint4* __restrict__ rec,
             const unsigned long long* __restrict__ pre, const uint32_t* __restrict__ wstart,
-            uint32_t* __restrict__ cnt)
+            uint32_t* __restrict__ cnt, uint32_t* __restrict__ wofs)
 {
-    extern __shared__ uint32_t s_hist[];
+    extern __shared__ uint32_t s_rel[];   // [8][rw] per-warp counts, 16 bits per tile
     const int warp = threadIdx.x >> 5;
+    const int rwm = (max_tiles + 1) / 2;
     const int n_units = (int)units[kUnitFirst + L.n_views];
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int v = view_of_unit(units, u);
         const int nt = L.tiles_x[v] * L.tiles_y[v];
-        for (int t = threadIdx.x; t < nt; t += blockDim.x) s_hist[t] = 0u;
+        const int rw = (nt + 1) / 2;
+        for (int i = threadIdx.x; i < 8 * rw; i += blockDim.x) s_rel[i] = 0u;
         __syncthreads();
         const unsigned long long Dv = units[kUnitDv + v];
         const unsigned long long w0 =
@@ -1025,65 +1058,82 @@ k_ord_count(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
             (unsigned long long)warp * kOrdWarpDups;
         if (w0 < Dv) {
             const unsigned long long vs = units[kUnitVs + v];
+            uint32_t* my = s_rel + warp * rw;
             walk_dups(L.tiles_x[v], rec + vs, pre + vs + v, (int)stat[4 * v + 2],
                       (int)wstart[(size_t)u * 8 + warp], w0, min(Dv, w0 + kOrdWarpDups),
                       [&](int, int t, uint32_t, bool ok) {
-                          if (ok) atomicAdd(s_hist + t, 1u);
+                          if (ok) atomicAdd(my + (t >> 1), 1u << ((t & 1) * 16));
                       });
         }
         __syncthreads();
+        uint32_t* wo = wofs + (size_t)u * 8 * rwm;
         uint32_t* dst = cnt + (size_t)u * max_tiles;
-        for (int t = threadIdx.x; t < nt; t += blockDim.x) dst[t] = s_hist[t];
+        for (int q = threadIdx.x; q < rw; q += blockDim.x) {
+            uint32_t r0 = 0u, r1 = 0u;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                const uint32_t c = s_rel[w * rw + q];
+                wo[(size_t)w * rwm + q] = r0 | (r1 << 16);
+                r0 += c & 0xffffu;
+                r1 += c >> 16;
+            }
+            dst[2 * q] = r0;
+            if (2 * q + 1 < nt) dst[2 * q + 1] = r1;
+        }
         __syncthreads();
     }
 }
 
-// Per global tile: its view's unit counts become their exclusive running sums
-// (in unit order, in place) and the total is the tile's count.
+// Per tile of a view: its unit counts become their exclusive running sums (in
+// unit order, in place) and the total is the tile's count.  Block (x, v) takes
+// the 32 tiles 32x .. 32x + 31 of view v, one per lane; its eight warps split
+// the view's units into eight runs, sum their run per tile, and after the
+// warps' sums are scanned in shared memory write the running sums.
 __global__ void __launch_bounds__(256)
 k_ord_scan(gevo_layout L, int max_tiles, const unsigned long long* __restrict__ units,
            uint32_t* __restrict__ cnt, uint32_t* __restrict__ tile_count)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L.total_tiles) return;
-    const int v = view_of_tile(L, t);
-    uint32_t* c = cnt + (t - L.tile_base[v]);
-    const int u1 = (int)units[kUnitFirst + v + 1];
-    int u = (int)units[kUnitFirst + v];
+    __shared__ uint32_t s_sum[8][32];
+    const int v = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = L.tiles_x[v] * L.tiles_y[v];
+    const int t = blockIdx.x * 32 + lane;
+    if (blockIdx.x * 32 >= nt) return;   // the whole block: before any barrier
+    const int u0 = (int)units[kUnitFirst + v], nu = (int)units[kUnitFirst + v + 1] - u0;
+    const int a = u0 + (int)((long long)nu * warp / 8), b = u0 + (int)((long long)nu * (warp + 1) / 8);
+    uint32_t* c = cnt + t;
+    uint32_t sum = 0u;
+    if (t < nt)
+        for (int u = a; u < b; u++) sum += c[(size_t)u * max_tiles];
+    s_sum[warp][lane] = sum;
+    __syncthreads();
     uint32_t run = 0u;
-    for (; u + 8 <= u1; u += 8) {
-        uint32_t x[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) x[i] = c[(size_t)(u + i) * max_tiles];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            c[(size_t)(u + i) * max_tiles] = run;
-            run += x[i];
+    for (int w = 0; w < warp; w++) run += s_sum[w][lane];
+    if (t < nt) {
+        for (int u = a; u < b; u++) {
+            const uint32_t x = c[(size_t)u * max_tiles];
+            c[(size_t)u * max_tiles] = run;
+            run += x;
         }
+        if (warp == 7) tile_count[L.tile_base[v] + t] = run;
     }
-    for (; u < u1; u++) {
-        const uint32_t x = c[(size_t)u * max_tiles];
-        c[(size_t)u * max_tiles] = run;
-        run += x;
-    }
-    tile_count[t] = run;
 }
 
 // The order-keeping scatter, one unit per block at a time.  Shared memory: the
-// unit's first slot per tile [T_v], then per warp and tile a 16-bit running
-// offset (two tiles to a 32-bit word): a warp's kOrdWarpDups duplicates hold at
-// most that many of one tile and the unit's run of a tile at most kOrdUnit, so
-// 16 bits hold every count and offset.
+// unit's first slot per tile [T_v], then per warp and tile the 16-bit running
+// offset (two tiles to a 32-bit word) that starts as the counting pass's count
+// of the earlier warps' duplicates and grows by each round's.
 __global__ void __launch_bounds__(256)
 k_ord_scatter(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
               const unsigned long long* __restrict__ units, const uint4* __restrict__ rec,
               const unsigned long long* __restrict__ pre, const uint32_t* __restrict__ wstart,
-              const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ tile_start,
-              unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals)
+              const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ wofs,
+              const uint32_t* __restrict__ tile_start, unsigned long long* __restrict__ keys,
+              uint32_t* __restrict__ vals)
 {
     extern __shared__ uint32_t s_dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
+    const int rwm = (max_tiles + 1) / 2;
     const int n_units = (int)units[kUnitFirst + L.n_views];
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
         const int v = view_of_unit(units, u);
@@ -1091,58 +1141,41 @@ k_ord_scatter(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
         const int rw = (nt + 1) / 2;   // words per warp row
         uint32_t* s_base = s_dyn;
         uint32_t* s_rel = s_dyn + 2 * rw;
-        for (int i = threadIdx.x; i < 8 * rw; i += blockDim.x) s_rel[i] = 0u;
+        // the unit's first slot per tile and the warps' running offsets
+        const int tb = L.tile_base[v];
+        const uint32_t* off = cnt + (size_t)u * max_tiles;
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) s_base[t] = tile_start[tb + t] + off[t];
+        // each warp its own row of running offsets
+        const uint32_t* wo = wofs + ((size_t)u * 8 + warp) * rwm;
+        for (int q = lane; q < rw; q += 32) s_rel[warp * rw + q] = wo[q];
         __syncthreads();
         const unsigned long long Dv = units[kUnitDv + v];
         const unsigned long long w0 =
             (unsigned long long)(u - (int)units[kUnitFirst + v]) * kOrdUnit +
             (unsigned long long)warp * kOrdWarpDups;
-        const unsigned long long w1 = min(Dv, w0 + kOrdWarpDups);
-        const unsigned long long vs = units[kUnitVs + v];
-        const uint4* rv = rec + vs;
-        const unsigned long long* pv = pre + vs + v;
-        const int M = (int)stat[4 * v + 2];
-        const int p = w0 < Dv ? (int)wstart[(size_t)u * 8 + warp] : 0;
-        const int tx = L.tiles_x[v];
-        uint32_t* my = s_rel + warp * rw;
-        if (w0 < Dv)
-            walk_dups(tx, rv, pv, M, p, w0, w1, [&](int, int t, uint32_t, bool ok) {
-                if (ok) atomicAdd(my + (t >> 1), 1u << ((t & 1) * 16));
-            });
-        __syncthreads();
-        // the unit's first slot per tile, and the warps' running offsets in warp order
-        const int tb = L.tile_base[v];
-        const uint32_t* off = cnt + (size_t)u * max_tiles;
-        for (int q = threadIdx.x; q < rw; q += blockDim.x) {
-            for (int h = 0; h < 2; h++) {
-                const int t = 2 * q + h;
-                if (t < nt) s_base[t] = tile_start[tb + t] + off[t];
-            }
-            uint32_t r0 = 0u, r1 = 0u;
-#pragma unroll
-            for (int w = 0; w < 8; w++) {
-                const uint32_t c = s_rel[w * rw + q];
-                s_rel[w * rw + q] = r0 | (r1 << 16);
-                r0 += c & 0xffffu;
-                r1 += c >> 16;
-            }
-        }
-        __syncthreads();
-        if (w0 < Dv)
-            walk_dups(tx, rv, pv, M, p, w0, w1, [&](int g, int t, uint32_t dbits, bool ok) {
+        if (w0 < Dv) {
+            const unsigned long long vs = units[kUnitVs + v];
+            // the warp's offsets, one 16-bit word per tile (tile t is the half of
+            // word t / 2 that the packing puts it in: little-endian)
+            uint16_t* my = reinterpret_cast<uint16_t*>(s_rel + warp * rw);
+            walk_dups(L.tiles_x[v], rec + vs, pre + vs + v, (int)stat[4 * v + 2],
+                      (int)wstart[(size_t)u * 8 + warp], w0, min(Dv, w0 + kOrdWarpDups),
+                      [&](int g, int t, uint32_t dbits, bool ok) {
                 const uint32_t peers =
                     __match_any_sync(0xffffffffu, ok ? (uint32_t)t : 0xffffffffu);
+                const uint32_t rank = __popc(peers & lt);
+                uint32_t o = 0u;
                 if (ok) {
-                    const uint32_t o = (my[t >> 1] >> ((t & 1) * 16)) & 0xffffu;
-                    const uint32_t slot = s_base[t] + o + __popc(peers & lt);
+                    o = my[t];
+                    const uint32_t slot = s_base[t] + o + rank;
                     if (keys) keys[slot] = ((unsigned long long)(tb + t) << 32) | dbits;
                     vals[slot] = (uint32_t)g;
                 }
-                __syncwarp();
-                if (ok && lane == __ffs(peers) - 1)
-                    atomicAdd(my + (t >> 1), (uint32_t)__popc(peers) << ((t & 1) * 16));
+                __syncwarp();   // every peer has read the tile's offset
+                if (ok && (peers >> lane) == 1u) my[t] = (uint16_t)(o + rank + 1u);   // last peer
                 __syncwarp();
             });
+        }
         __syncthreads();
     }
 }
@@ -1222,6 +1255,7 @@ static gevo_status bin_sort_ordered(const gevo_layout& L, int32_t n, const gevo_
     auto* units = reinterpret_cast<unsigned long long*>(ws + w.ord_units);
     uint32_t* cnt = reinterpret_cast<uint32_t*>(ws + w.ord_cnt);
     uint32_t* wstart = reinterpret_cast<uint32_t*>(ws + w.ord_wstart);
+    uint32_t* wofs = reinterpret_cast<uint32_t*>(ws + w.ord_wofs);
     const auto* xy = reinterpret_cast<const float2*>(proj.xy);
     const auto* rgbz = reinterpret_cast<const float4*>(proj.rgb_depth);
     const uint64_t cap1 = (uint64_t)V * (uint64_t)n;
@@ -1266,11 +1300,12 @@ static gevo_status bin_sort_ordered(const gevo_layout& L, int32_t n, const gevo_
     const size_t osmem = sizeof(uint32_t) * 10 * (size_t)((max_tiles + 1) / 2);
     ord_attributes(osmem);
     const uint64_t unit_rows = cap / kOrdUnit + (uint64_t)V + 1;
-    const int ugrid = (int)std::max<uint64_t>(1, std::min<uint64_t>(unit_rows, (uint64_t)sm_count() * 8));
-    k_ord_count<<<ugrid, 256, sizeof(uint32_t) * (size_t)max_tiles, st>>>(
-        L, max_tiles, stat, units, rec, pre, wstart, cnt);
+    const int ugrid = (int)std::max<uint64_t>(1, std::min<uint64_t>(unit_rows, (uint64_t)sm_count() * 32));
+    k_ord_count<<<ugrid, 256, sizeof(uint32_t) * 8 * (size_t)((max_tiles + 1) / 2), st>>>(
+        L, max_tiles, stat, units, rec, pre, wstart, cnt, wofs);
     GEVO_CHECK_LAUNCH();
-    k_ord_scan<<<(T + 255) / 256, 256, 0, st>>>(L, max_tiles, units, cnt, tile_count);
+    k_ord_scan<<<dim3((max_tiles + 31) / 32, V), 256, 0, st>>>(L, max_tiles, units, cnt,
+                                                                tile_count);
     GEVO_CHECK_LAUNCH();
     // 5. tile starts, ranges, D, heaviest-first order, the capacity check
     k_scan<<<1, 1024, 0, st>>>(T, cap, tile_count, tile_start, tile_cursor, tile_order, ranges,
@@ -1279,7 +1314,7 @@ static gevo_status bin_sort_ordered(const gevo_layout& L, int32_t n, const gevo_
     // 6. the duplicates, emitted in order
     if (cap > 0) {
         k_ord_scatter<<<ugrid, 256, osmem, st>>>(L, max_tiles, stat, units, rec, pre, wstart, cnt,
-                                                 tile_start,
+                                                 wofs, tile_start,
                                                  reinterpret_cast<unsigned long long*>(keys), vals);
         GEVO_CHECK_LAUNCH();
     }
@@ -1289,6 +1324,19 @@ static gevo_status bin_sort_ordered(const gevo_layout& L, int32_t n, const gevo_
 }  // namespace gevo
 
 using namespace gevo;
+
+extern "C" int32_t gevo_bin_sort_launches(const gevo_layout* layout, int32_t n,
+                                          uint64_t dup_capacity)
+{
+    if (!layout || !gevo::layout_valid(*layout) || n < 0) return -1;
+    int mt = 0;
+    for (int v = 0; v < layout->n_views; v++)
+        mt = std::max(mt, layout->tiles_x[v] * layout->tiles_y[v]);
+    const bool work = n > 0, room = dup_capacity > 0;
+    if (mt <= kOrdMaxTiles)   // the launches of bin_sort_ordered
+        return (work ? 6 : 0) + 1 + (work ? 1 : 0) + 3 + (room ? 1 : 0);
+    return (work ? 1 : 0) + 1 + (work && room ? 2 : 0);
+}
 
 extern "C" gevo_status gevo_bin_sort(const gevo_layout* layout, int32_t n, const gevo_proj* proj,
                                      uint64_t dup_capacity, uint64_t* keys, uint32_t* vals,

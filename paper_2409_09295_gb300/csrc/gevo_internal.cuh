@@ -59,11 +59,13 @@ struct WsLayout {
     size_t ord_cnt;      // uint32 [(cap / kOrdUnit + V + 1) * max tiles]: per (unit, tile)
                          // counts, then their running sums over units
     size_t ord_wstart;   // uint32 [(cap / kOrdUnit + V + 1) * 8]: first entry of each warp
+    size_t ord_wofs;     // uint32 [(cap / kOrdUnit + V + 1) * 8 * ceil(max tiles / 2)]: per
+                         // (unit, warp, tile) the earlier warps' count, 16 bits per tile
     size_t total;
 };
 constexpr int kDepthBins = 512;     // depth segments per view of the per-view depth sort
 constexpr int kOrdMaxTiles = 8192;  // views with more tiles take the bucket-and-sort path
-constexpr int kOrdUnit = 16384;     // duplicates per block of the order-keeping passes
+constexpr int kOrdUnit = 8192;      // duplicates per block of the order-keeping passes
 constexpr int kOrdScanItems = 4096; // entries per block of the prefix scan
 WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap);
 
