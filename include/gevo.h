@@ -183,6 +183,26 @@ gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,
                          const gevo_camera* cams, gevo_proj* out, void* workspace,
                          void* stream);
 
+/* Parts of gevo_project_part and gevo_project_bwd_part. */
+#define GEVO_PART_ALL 0       /* the whole call, as gevo_project / gevo_project_bwd */
+#define GEVO_PART_GEOMETRY 1  /* everything but the colour                          */
+#define GEVO_PART_COLOUR 2    /* the colour only                                    */
+
+/* gevo_project in two parts, so that a caller whose colour parameters arrive
+ * later (a host-to-device copy of the SH coefficients, most of the bytes) can
+ * start the sort meanwhile: the sort reads no colour.
+ * GEVO_PART_GEOMETRY writes xy, conic_opacity, radius, tiles_touched and the
+ * depth (w) of rgb_depth, with rgb_depth x, y, z = 0; it reads means, scales,
+ * quats and opacities only (sh / rgb may still be in flight, but one of them
+ * must be non-NULL).  GEVO_PART_COLOUR, after it on the stream (or after an
+ * event recorded after it), writes x, y, z of rgb_depth for every entry with
+ * radius > 0 and nothing else -- so gevo_bin_sort, which reads only w, may run
+ * concurrently.  The two parts give bit for bit what GEVO_PART_ALL gives.
+ * part outside 0..2: GEVO_ERR_INVALID. */
+gevo_status gevo_project_part(const gevo_layout* layout, const gevo_gaussians* g,
+                              const gevo_camera* cams, gevo_proj* out, int32_t part,
+                              void* workspace, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Stages a2-a4: keys, bit-exact sort, tile ranges                          */
 /* ---------------------------------------------------------------------- */
@@ -316,6 +336,21 @@ gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
                              const gevo_camera* cams, const gevo_proj* proj,
                              const gevo_grad2d* grad2d, gevo_gaussian_grads* out, float* dxi,
                              void* workspace, void* stream);
+
+/* gevo_project_bwd in two parts, so that a caller copying the gradients to the
+ * host can start with the SH gradients (most of the bytes) while the geometry
+ * part still runs.  GEVO_PART_COLOUR zeroes dxi and, for SH colours, writes
+ * out->sh and the view-direction share of out->means (and adds the camera
+ * centre's share to dxi); for rgb colours it only zeroes dxi.
+ * GEVO_PART_GEOMETRY, after it on the stream, writes out->scales, quats,
+ * opacities and rgb, adds the rest of out->means (writes it for rgb colours)
+ * and adds to dxi.  out->sh is final once the colour part has run.  The two
+ * parts give what GEVO_PART_ALL gives (dxi sums in another order; every other
+ * output bit for bit).  part outside 0..2: GEVO_ERR_INVALID. */
+gevo_status gevo_project_bwd_part(const gevo_layout* layout, const gevo_gaussians* g,
+                                  const gevo_camera* cams, const gevo_proj* proj,
+                                  const gevo_grad2d* grad2d, gevo_gaussian_grads* out,
+                                  float* dxi, int32_t part, void* workspace, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Stage a8: L1 loss with stop-gradient targets (E_pho of Eq. 2, E_pc of Eq. 6) */

@@ -82,6 +82,7 @@ class BatchedReplay:
             self.autotune(fwd=tuning_fwd is None, bwd=tuning_bwd is None)
         self.graph = None
         self.stage_graphs = None
+        self.zero_stream = None
         self.bwd_graph = None
 
     # ---- stages with the chosen shapes ------------------------------------------------
@@ -104,6 +105,9 @@ class BatchedReplay:
         self.pipe.loss_l1(self.target_rgb, self.target_depth, self.lambda_depth)
         self.pipe.grad2d_zero()
 
+    def _loss_only(self):
+        self.pipe.loss_l1(self.target_rgb, self.target_depth, self.lambda_depth)
+
     def _render_bwd(self):
         p = self.pipe
         p.render_bwd(p.dL_drgb, p.dL_ddepth if self.lambda_depth else None, None, self.bg,
@@ -120,8 +124,29 @@ class BatchedReplay:
                 ("render_bwd", self._render_bwd), ("project_bwd", self._project_bwd)]
 
     def step_eager(self):
-        for _, f in self.stages():
-            f()
+        """One step.  Zeroing the 2-D gradient rows reads only the projection's
+        radii and writes only rows that nothing reads before the reverse walk,
+        so it runs on a side stream beside the sort, blend and loss: its HBM
+        writes overlap their compute (inside a graph, a parallel branch)."""
+        self._project()
+        self._fork_zero()
+        self._bin_sort()
+        self._render_fwd()
+        self._loss_only()
+        self._join_zero()
+        self._render_bwd()
+        self._project_bwd()
+
+    def _fork_zero(self):
+        """Zero the 2-D gradient rows on the side stream (after the projection)."""
+        if self.zero_stream is None:
+            self.zero_stream = torch.cuda.Stream(device=self.pipe.device)
+        self.zero_stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(self.zero_stream):
+            self.pipe.grad2d_zero()
+
+    def _join_zero(self):
+        torch.cuda.current_stream().wait_stream(self.zero_stream)
 
     # ---- autotuner ---------------------------------------------------------------------
     def _search(self, name, run, reps):
@@ -258,11 +283,16 @@ class HostStep:
     call step(), synchronise, and read `host_out` (loss per view, dL/dxi per
     view, and the parameter gradients).
 
-    One graph per step: the parameters and cameras are copied up first (the
-    projection reads them); the targets, first read by the loss, are copied up
-    on a second stream while projection, sort and blend run; after the
-    projection backward the loss, the pose gradients and the 59 N parameter
-    gradients are copied back."""
+    One graph per step, its copies overlapped with the kernels: the geometry
+    parameters and cameras are copied up first and projected (the geometry
+    part); the colour parameters (the SH coefficients, most of the input bytes)
+    follow on a second stream and get their colour part there, beside the
+    sort; the targets, first read by the loss, follow on a third.  After the
+    colour part of the projection backward the SH gradients go down on the
+    second stream while the geometry part runs; then the loss, the pose
+    gradients and the other parameter gradients.  The 2-D gradient rows are
+    zeroed on a fourth stream beside the sort and blend, as in
+    BatchedReplay.step_eager."""
 
     def __init__(self, rep: BatchedReplay):
         self.rep = rep
@@ -291,28 +321,55 @@ class HostStep:
     def _body(self):
         rep, p = self.rep, self.rep.pipe
         main = torch.cuda.current_stream()
+        side, side2 = self.side, self.side2
+        col = "sh" if "sh" in rep.g else "rgb"
+        # geometry and cameras first: the geometry part of the projection and
+        # the sort read nothing else
         for k, t in self.host_in.items():
-            (rep.camt if k == "cams" else rep.g[k]).copy_(t, non_blocking=True)
-        side = self.side
+            if k != col:
+                (rep.camt if k == "cams" else rep.g[k]).copy_(t, non_blocking=True)
         side.wait_stream(main)
         with torch.cuda.stream(side):
+            rep.g[col].copy_(self.host_in[col], non_blocking=True)
+            ev_col_in = torch.cuda.Event()
+            ev_col_in.record(side)
+        p.project(rep.g, rep.camt, part=_abi.PART_GEOMETRY)
+        ev_geo = torch.cuda.Event()
+        ev_geo.record(main)
+        with torch.cuda.stream(side):      # colours once they are in, beside the sort
+            side.wait_event(ev_geo)
+            p.project(rep.g, rep.camt, part=_abi.PART_COLOUR)
+            ev_col = torch.cuda.Event()
+            ev_col.record(side)
+        side2.wait_event(ev_col_in)        # then the targets, first read by the loss
+        with torch.cuda.stream(side2):
             rep.target_rgb.copy_(self.host_targets["rgb"], non_blocking=True)
             if "depth" in self.host_targets:
                 rep.target_depth.copy_(self.host_targets["depth"], non_blocking=True)
-        rep._project()
+        rep._fork_zero()
         rep._bin_sort()
+        main.wait_event(ev_col)
         rep._render_fwd()
-        main.wait_stream(side)
-        rep._loss()
+        main.wait_stream(side2)
+        rep._loss_only()
+        rep._join_zero()
         rep._render_bwd()
-        rep._project_bwd()
+        p.project_bwd(rep.g, rep.camt, rep.want_dxi, part=_abi.PART_COLOUR)
+        if col == "sh":                    # the SH gradients go down during the geometry part
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                self.host_out["sh"].copy_(p.grads["sh"], non_blocking=True)
+        p.project_bwd(rep.g, rep.camt, rep.want_dxi, part=_abi.PART_GEOMETRY)
         self.host_out["loss"].copy_(p.loss, non_blocking=True)
         self.host_out["dxi"].copy_(p.dxi, non_blocking=True)
         for k, v in p.grads.items():
-            self.host_out[k].copy_(v, non_blocking=True)
+            if not (k == "sh" and col == "sh"):
+                self.host_out[k].copy_(v, non_blocking=True)
+        main.wait_stream(side)
 
     def capture(self):
         self.side = torch.cuda.Stream()
+        self.side2 = torch.cuda.Stream()
         self.rep._warm()
         for _ in range(2):
             self._body()

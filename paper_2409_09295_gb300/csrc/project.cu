@@ -191,7 +191,34 @@ __device__ __forceinline__ void geometry(const CamS& cam, const float mu[3], con
     G.det = (cx_ * cx_ + cy_ * cy_ + cz_ * cz_) + kDilation * (n0 + n1) + kDilation * kDilation;
 }
 
+// Colour of a Gaussian with mean mu seen from camera centre c: its rgb, or
+// max(0, sum_k Y_k(d) k_k + 0.5) with d the unit direction from c to mu.
 template <int DEG, bool HAS_RGB>
+__device__ __forceinline__ void colour_of(const float mu[3], const float c[3],
+                                          const float k[16][3], float rgb[3])
+{
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    if (HAS_RGB) {
+        rgb[0] = k[0][0]; rgb[1] = k[0][1]; rgb[2] = k[0][2];
+    } else {
+        float dx = mu[0] - c[0], dy = mu[1] - c[1], dz = mu[2] - c[2];
+        const float inl = rsqrtf(dx * dx + dy * dy + dz * dz);
+        dx *= inl; dy *= inl; dz *= inl;
+        float Y[16];
+        sh_eval<DEG>(dx, dy, dz, Y);
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            float acc = 0.5f;
+#pragma unroll
+            for (int i = 0; i < K; i++) acc += Y[i] * k[i][ch];
+            rgb[ch] = fmaxf(acc, 0.f);
+        }
+    }
+}
+
+// COLOUR false: the geometry part alone (colours left 0, the colour part writes
+// them); the colour parameters are not read.
+template <int DEG, bool HAS_RGB, bool COLOUR>
 __global__ void __launch_bounds__(128)
 k_project_fwd(gevo_layout L, int n, const float* __restrict__ means, const float* __restrict__ scales,
               const float4* __restrict__ quats, const float* __restrict__ opac,
@@ -216,8 +243,7 @@ k_project_fwd(gevo_layout L, int n, const float* __restrict__ means, const float
 #pragma unroll
         for (int k = 0; k < 3; k++) N[3 * i + k] = Rq[3 * i + k] * s[k];
     float k[16][3];
-    load_colour<DEG, HAS_RGB>(coef, g, k);
-    constexpr int K = (DEG + 1) * (DEG + 1);
+    if (COLOUR) load_colour<DEG, HAS_RGB>(coef, g, k);
 
     bool nonfinite = false;
     for (int v = 0; v < L.n_views; v++) {
@@ -247,23 +273,8 @@ k_project_fwd(gevo_layout L, int n, const float* __restrict__ means, const float
                 if (area == 0) {
                     r = 0;
                 } else {
-                    float rgb[3];
-                    if (HAS_RGB) {
-                        rgb[0] = k[0][0]; rgb[1] = k[0][1]; rgb[2] = k[0][2];
-                    } else {
-                        float dx = mu[0] - cam.c[0], dy = mu[1] - cam.c[1], dz = mu[2] - cam.c[2];
-                        const float inl = rsqrtf(dx * dx + dy * dy + dz * dz);
-                        dx *= inl; dy *= inl; dz *= inl;
-                        float Y[16];
-                        sh_eval<DEG>(dx, dy, dz, Y);
-#pragma unroll
-                        for (int ch = 0; ch < 3; ch++) {
-                            float acc = 0.5f;
-#pragma unroll
-                            for (int i = 0; i < K; i++) acc += Y[i] * k[i][ch];
-                            rgb[ch] = fmaxf(acc, 0.f);
-                        }
-                    }
+                    float rgb[3] = {0.f, 0.f, 0.f};
+                    if (COLOUR) colour_of<DEG, HAS_RGB>(mu, cam.c, k, rgb);
                     out_xy[idx] = make_float2(mx, my);
                     out_co[idx] = make_float4(ca, cb, cc, o);
                     out_rz[idx] = make_float4(rgb[0], rgb[1], rgb[2], G.p[2]);
@@ -291,6 +302,36 @@ __device__ __forceinline__ unsigned long long visible_views(const gevo_layout& L
     return m;
 }
 
+// Colour part of the projection: for every entry the geometry part left
+// visible (radius > 0) the colour, written to x, y, z of rgb_depth only -- its
+// w (the depth) may be read meanwhile, by the sort.
+template <int DEG, bool HAS_RGB>
+__global__ void __launch_bounds__(128)
+k_project_colour(gevo_layout L, int n, const float* __restrict__ means,
+                 const float* __restrict__ coef, const gevo_camera* __restrict__ cams,
+                 const int* __restrict__ radius, float4* __restrict__ out_rz)
+{
+    __shared__ CamS s_cam[GEVO_MAX_VIEWS];
+    load_cams(L, cams, s_cam);
+    __syncthreads();
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    unsigned long long vis = visible_views(L, n, g, radius);
+    if (!vis) return;
+    const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
+    float k[16][3];
+    load_colour<DEG, HAS_RGB>(coef, g, k);
+    while (vis) {
+        const int v = __ffsll((long long)vis) - 1;
+        vis &= vis - 1;
+        float rgb[3];
+        colour_of<DEG, HAS_RGB>(mu, s_cam[v].c, k, rgb);
+        float* rz = reinterpret_cast<float*>(out_rz + (size_t)v * n + g);
+        *reinterpret_cast<float2*>(rz) = make_float2(rgb[0], rgb[1]);
+        rz[2] = rgb[2];
+    }
+}
+
 // Per-view pose-gradient sums are kept in shared memory in kDxiCopies copies,
 // lane l adding into copy l % kDxiCopies: lanes of a warp that reach the same
 // view at once would otherwise serialise on one address.
@@ -302,7 +343,7 @@ constexpr int kDxiCopies = 16;
 // its colour term.  Each lane walks only its own visible views, so a warp does
 // max-over-lanes rather than all-views iterations; the per-view twist sums go
 // through shared-memory atomics.
-template <bool HAS_RGB>
+template <bool HAS_RGB, bool ADD_MEANS>
 __global__ void __launch_bounds__(128)
 k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
                   const float* __restrict__ scales, const float4* __restrict__ quats,
@@ -445,7 +486,11 @@ k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
         const float dot = w * dq[0] + x * dq[1] + y * dq[2] + z * dq[3];
         d_quats[g] = make_float4((dq[0] - w * dot) * qinv, (dq[1] - x * dot) * qinv,
                                  (dq[2] - y * dot) * qinv, (dq[3] - z * dot) * qinv);
-        d_means[3 * g] = dmu[0]; d_means[3 * g + 1] = dmu[1]; d_means[3 * g + 2] = dmu[2];
+        if (ADD_MEANS) {   // onto the SH colour kernel's share
+            d_means[3 * g] += dmu[0]; d_means[3 * g + 1] += dmu[1]; d_means[3 * g + 2] += dmu[2];
+        } else {
+            d_means[3 * g] = dmu[0]; d_means[3 * g + 1] = dmu[1]; d_means[3 * g + 2] = dmu[2];
+        }
         d_opac[g] = dop;
         if (HAS_RGB) { d_rgb[3 * g] = drgb[0]; d_rgb[3 * g + 1] = drgb[1]; d_rgb[3 * g + 2] = drgb[2]; }
     }
@@ -461,9 +506,11 @@ k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
 }
 
 // SH colour part: colour = max(0, sum_k Y_k(d) k_k + 0.5), d the unit direction
-// from the camera centre.  Writes dL/dSH, adds the direction's share to
-// dL/dmean (after k_project_bwd_geo has written it) and the camera centre's to
-// the translation part of the pose twist.
+// from the camera centre.  Writes dL/dSH and the direction's share of dL/dmean
+// (k_project_bwd_geo, launched after it, adds the rest) and adds the camera
+// centre's share to the translation part of the pose twist.  It runs first so
+// that the SH gradients, most of the bytes, are final while the geometry part
+// still runs.
 template <int DEG>
 __global__ void __launch_bounds__(128)
 k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
@@ -531,7 +578,7 @@ k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
                 }
             }
         }
-        d_means[3 * g] += dmu[0]; d_means[3 * g + 1] += dmu[1]; d_means[3 * g + 2] += dmu[2];
+        d_means[3 * g] = dmu[0]; d_means[3 * g + 1] = dmu[1]; d_means[3 * g + 2] = dmu[2];
         if ((K * 3) % 4 == 0) {
             float4* p = reinterpret_cast<float4*>(d_coef + (size_t)g * K * 3);
             float tmp[K * 3];
@@ -561,34 +608,48 @@ k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
 
 template <int DEG, bool RGB>
 static void launch_fwd(const gevo_layout& L, const gevo_gaussians& g, const gevo_camera* cams,
-                       const gevo_proj& o, uint32_t* err, cudaStream_t st)
+                       const gevo_proj& o, int part, uint32_t* err, cudaStream_t st)
 {
     const int threads = 128;
     const int blocks = (g.n + threads - 1) / threads;
-    k_project_fwd<DEG, RGB><<<blocks, threads, 0, st>>>(
-        L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), g.opacities,
-        RGB ? g.rgb : g.sh, cams, reinterpret_cast<float2*>(o.xy),
-        reinterpret_cast<float4*>(o.conic_opacity), reinterpret_cast<float4*>(o.rgb_depth),
-        o.radius, o.tiles_touched, err);
+    const float* coef = RGB ? g.rgb : g.sh;
+    if (part == GEVO_PART_ALL)
+        k_project_fwd<DEG, RGB, true><<<blocks, threads, 0, st>>>(
+            L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), g.opacities, coef,
+            cams, reinterpret_cast<float2*>(o.xy), reinterpret_cast<float4*>(o.conic_opacity),
+            reinterpret_cast<float4*>(o.rgb_depth), o.radius, o.tiles_touched, err);
+    else if (part == GEVO_PART_GEOMETRY)
+        k_project_fwd<0, true, false><<<blocks, threads, 0, st>>>(
+            L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), g.opacities,
+            nullptr, cams, reinterpret_cast<float2*>(o.xy),
+            reinterpret_cast<float4*>(o.conic_opacity), reinterpret_cast<float4*>(o.rgb_depth),
+            o.radius, o.tiles_touched, err);
+    else
+        k_project_colour<DEG, RGB><<<blocks, threads, 0, st>>>(
+            L, g.n, g.means, coef, cams, o.radius, reinterpret_cast<float4*>(o.rgb_depth));
 }
 
+// SH colour kernel first (it writes the means' gradient, the geometry kernel
+// adds to it), then the geometry kernel; part selects one of the two.
 template <int DEG, bool RGB>
 static void launch_bwd(const gevo_layout& L, const gevo_gaussians& g, const gevo_camera* cams,
                        const gevo_proj& o, const gevo_grad2d& gr, const gevo_gaussian_grads& out,
-                       float* dxi, cudaStream_t st, const uint32_t* list = nullptr,
+                       float* dxi, int part, cudaStream_t st, const uint32_t* list = nullptr,
                        const uint32_t* list_count = nullptr)
 {
     const int threads = 128;
     const int blocks = (g.n + threads - 1) / threads;
-    k_project_bwd_geo<RGB><<<blocks, threads, 0, st>>>(
+    if (!RGB && part != GEVO_PART_GEOMETRY)
+        k_project_bwd_col<DEG><<<blocks, threads, 0, st>>>(
+            L, g.n, g.means, g.sh, cams, o.radius, reinterpret_cast<const float4*>(gr.rgb_depth),
+            out.means, out.sh, dxi, list, list_count);
+    if (part == GEVO_PART_COLOUR) return;
+    const auto geo = RGB ? k_project_bwd_geo<true, false> : k_project_bwd_geo<false, true>;
+    geo<<<blocks, threads, 0, st>>>(
         L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), cams, o.radius,
         reinterpret_cast<const float2*>(gr.xy), reinterpret_cast<const float4*>(gr.conic_opacity),
         reinterpret_cast<const float4*>(gr.rgb_depth), out.means, out.scales,
         reinterpret_cast<float4*>(out.quats), out.opacities, out.rgb, dxi, list, list_count);
-    if (!RGB)
-        k_project_bwd_col<DEG><<<blocks, threads, 0, st>>>(
-            L, g.n, g.means, g.sh, cams, o.radius, reinterpret_cast<const float4*>(gr.rgb_depth),
-            out.means, out.sh, dxi, list, list_count);
 }
 
 static bool valid_gaussians(const gevo_gaussians* g)
@@ -612,36 +673,45 @@ static bool valid_proj(const gevo_proj* p)
 
 using namespace gevo;
 
-extern "C" gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,
-                                    const gevo_camera* cams, gevo_proj* out, void* workspace,
-                                    void* stream)
+extern "C" gevo_status gevo_project_part(const gevo_layout* layout, const gevo_gaussians* g,
+                                         const gevo_camera* cams, gevo_proj* out, int32_t part,
+                                         void* workspace, void* stream)
 {
     if (!layout || !gevo::layout_valid(*layout) || !valid_gaussians(g) || !cams || !valid_proj(out) ||
-        !workspace || !gevo_aligned(workspace, 256))
+        !workspace || !gevo_aligned(workspace, 256) || part < GEVO_PART_ALL ||
+        part > GEVO_PART_COLOUR)
         return GEVO_ERR_INVALID;
     if (g->n == 0) return GEVO_OK;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t* err = reinterpret_cast<uint32_t*>(workspace);
     if (g->rgb) {
-        launch_fwd<0, true>(*layout, *g, cams, *out, err, st);
+        launch_fwd<0, true>(*layout, *g, cams, *out, part, err, st);
     } else {
         switch (g->sh_degree) {
-        case 0: launch_fwd<0, false>(*layout, *g, cams, *out, err, st); break;
-        case 1: launch_fwd<1, false>(*layout, *g, cams, *out, err, st); break;
-        case 2: launch_fwd<2, false>(*layout, *g, cams, *out, err, st); break;
-        default: launch_fwd<3, false>(*layout, *g, cams, *out, err, st); break;
+        case 0: launch_fwd<0, false>(*layout, *g, cams, *out, part, err, st); break;
+        case 1: launch_fwd<1, false>(*layout, *g, cams, *out, part, err, st); break;
+        case 2: launch_fwd<2, false>(*layout, *g, cams, *out, part, err, st); break;
+        default: launch_fwd<3, false>(*layout, *g, cams, *out, part, err, st); break;
         }
     }
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
 }
 
+extern "C" gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,
+                                    const gevo_camera* cams, gevo_proj* out, void* workspace,
+                                    void* stream)
+{
+    return gevo_project_part(layout, g, cams, out, GEVO_PART_ALL, workspace, stream);
+}
+
 static gevo_status project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
                                const gevo_camera* cams, const gevo_proj* proj,
                                const gevo_grad2d* grad2d, gevo_gaussian_grads* out, float* dxi,
                                void* workspace, void* stream, const uint32_t* list,
-                               const uint32_t* list_count)
+                               const uint32_t* list_count, int part = GEVO_PART_ALL)
 {
+    if (part < GEVO_PART_ALL || part > GEVO_PART_COLOUR) return GEVO_ERR_INVALID;
     if (!layout || !gevo::layout_valid(*layout) || !valid_gaussians(g) || !cams || !proj || !proj->radius ||
         !grad2d || !grad2d->xy || !grad2d->conic_opacity || !grad2d->rgb_depth || !out ||
         !out->means || !out->scales || !out->quats || !out->opacities || !workspace)
@@ -654,18 +724,20 @@ static gevo_status project_bwd(const gevo_layout* layout, const gevo_gaussians* 
     if (out->sh && (g->sh_degree == 1 || g->sh_degree == 3) && !gevo_aligned(out->sh, 16))
         return GEVO_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
-    if (dxi && cudaMemsetAsync(dxi, 0, sizeof(float) * 6 * layout->n_views, st) != cudaSuccess)
+    // the colour part (alone, or first of the two) starts the pose twist at zero
+    if (dxi && part != GEVO_PART_GEOMETRY &&
+        cudaMemsetAsync(dxi, 0, sizeof(float) * 6 * layout->n_views, st) != cudaSuccess)
         return GEVO_ERR_CUDA;
     if (g->n == 0) return GEVO_OK;
     const gevo_layout& L = *layout;
     if (g->rgb) {
-        launch_bwd<0, true>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count);
+        launch_bwd<0, true>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count);
     } else {
         switch (g->sh_degree) {
-        case 0: launch_bwd<0, false>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count); break;
-        case 1: launch_bwd<1, false>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count); break;
-        case 2: launch_bwd<2, false>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count); break;
-        default: launch_bwd<3, false>(L, *g, cams, *proj, *grad2d, *out, dxi, st, list, list_count); break;
+        case 0: launch_bwd<0, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count); break;
+        case 1: launch_bwd<1, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count); break;
+        case 2: launch_bwd<2, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count); break;
+        default: launch_bwd<3, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count); break;
         }
     }
     GEVO_CHECK_LAUNCH();
@@ -678,6 +750,16 @@ extern "C" gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_ga
                                         float* dxi, void* workspace, void* stream)
 {
     return project_bwd(layout, g, cams, proj, grad2d, out, dxi, workspace, stream, nullptr, nullptr);
+}
+
+extern "C" gevo_status gevo_project_bwd_part(const gevo_layout* layout, const gevo_gaussians* g,
+                                             const gevo_camera* cams, const gevo_proj* proj,
+                                             const gevo_grad2d* grad2d, gevo_gaussian_grads* out,
+                                             float* dxi, int32_t part, void* workspace,
+                                             void* stream)
+{
+    return project_bwd(layout, g, cams, proj, grad2d, out, dxi, workspace, stream, nullptr, nullptr,
+                       part);
 }
 
 extern "C" gevo_status gevo_project_bwd_active(const gevo_layout* layout, const gevo_gaussians* g,

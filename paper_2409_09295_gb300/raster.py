@@ -112,8 +112,13 @@ class Pipeline:
         return buf[self.pix_base[v]:self.pix_base[v + 1]].view(H, W)
 
     # ---- stages ----------------------------------------------------------------------
-    def project(self, g, cams):
-        abi.gevo_project(self.layout, g, cams, self.proj, self.ws)
+    def project(self, g, cams, part=None):
+        """The projection; part = abi.PART_GEOMETRY or abi.PART_COLOUR runs one
+        of its two parts (geometry first)."""
+        if part is None:
+            abi.gevo_project(self.layout, g, cams, self.proj, self.ws)
+        else:
+            abi.gevo_project_part(self.layout, g, cams, self.proj, part, self.ws)
 
     def bin_sort(self):
         abi.gevo_bin_sort(self.layout, self.n, self.proj, self.capacity, self.keys, self.vals,
@@ -143,9 +148,17 @@ class Pipeline:
                             self.T_final, self.n_contrib, dL_drgb, dL_ddepth, dL_dT, self.grad2d,
                             self.ws, tuning or self.tuning)
 
-    def project_bwd(self, g, cams, want_dxi=True):
-        abi.gevo_project_bwd(self.layout, g, cams, self.proj, self.grad2d, self.grads,
-                             self.dxi if want_dxi else None, self.ws)
+    def project_bwd(self, g, cams, want_dxi=True, part=None):
+        """The projection derivative; part = abi.PART_COLOUR then
+        abi.PART_GEOMETRY runs it in two parts (the SH gradients final after
+        the first)."""
+        dxi = self.dxi if want_dxi else None
+        if part is None:
+            abi.gevo_project_bwd(self.layout, g, cams, self.proj, self.grad2d, self.grads, dxi,
+                                 self.ws)
+        else:
+            abi.gevo_project_bwd_part(self.layout, g, cams, self.proj, self.grad2d, self.grads,
+                                      dxi, part, self.ws)
 
     # ---- active set of the global stage (Section III-B2, Eq. 5) --------------------
     def alloc_active(self):
