@@ -390,7 +390,7 @@ def main():
                "bin_sort": ("depth-ordered path, 12 kernels (k_ord_scatter the longest)"
                             if n_sort == 12 else "k_count_off+k_scan+k_scatter_off+k_segsort"),
                "render_fwd": "k_render_fwd", "loss": "k_loss_l1+k_zero_grad2d",
-               "render_bwd": "k_render_bwd", "project_bwd": "k_project_bwd_geo+k_project_bwd_col"}
+               "render_bwd": "k_render_bwd", "project_bwd": "k_pbwd_order+k_project_bwd_col+k_project_bwd_geo"}
     roofs = {}
     for name, (bound, amount, unit) in work.items():
         sec = stage_ms[name] / 1e3
@@ -617,12 +617,12 @@ def mapping_section():
 def launches_per_step(rep) -> int:
     """Kernels of ours launched per step: project (1), bin_sort (as the library
     reports for these sizes: 12 on the depth-ordered path), render_fwd (1), loss
-    (1), grad2d_zero (1), render_bwd (1), project_bwd (geometry, plus the
-    SH-colour kernel when colours are SH)."""
+    (1), grad2d_zero (1), render_bwd (1), project_bwd (the Gaussian order, the
+    geometry kernel, and the SH-colour kernel when colours are SH)."""
     from paper_2409_09295_gb300 import _abi
     p = rep.pipe
     sort = _abi.gevo_bin_sort_launches(p.layout, p.n, p.capacity)
-    return 1 + sort + 1 + 1 + 1 + 1 + (1 if p.colour == "rgb" else 2)
+    return 1 + sort + 1 + 1 + 1 + 1 + (2 if p.colour == "rgb" else 3)
 
 
 def sort_bytes(rep, VN: int, vis: int, D: int) -> int:

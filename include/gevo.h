@@ -342,9 +342,10 @@ gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
  * part still runs.  GEVO_PART_COLOUR zeroes dxi and, for SH colours, writes
  * out->sh and the view-direction share of out->means (and adds the camera
  * centre's share to dxi); for rgb colours it only zeroes dxi.
- * GEVO_PART_GEOMETRY, after it on the stream, writes out->scales, quats,
- * opacities and rgb, adds the rest of out->means (writes it for rgb colours)
- * and adds to dxi.  out->sh is final once the colour part has run.  The two
+ * GEVO_PART_GEOMETRY, after it on the stream and with the same workspace (it
+ * walks the Gaussians in the order the colour part stored there), writes
+ * out->scales, quats, opacities and rgb, adds the rest of out->means (writes it
+ * for rgb colours) and adds to dxi.  out->sh is final once the colour part has run.  The two
  * parts give what GEVO_PART_ALL gives (dxi sums in another order; every other
  * output bit for bit).  part outside 0..2: GEVO_ERR_INVALID. */
 gevo_status gevo_project_bwd_part(const gevo_layout* layout, const gevo_gaussians* g,

@@ -7,7 +7,7 @@ namespace gevo {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap)
+WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap, bool pbwd)
 {
     WsLayout w;
     size_t T = (size_t)L.total_tiles;
@@ -17,6 +17,9 @@ WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap)
     w.tile_cursor = o;  o = align256(o + 4 * T);
     w.tile_order = o;   o = align256(o + 4 * T);
     w.tile_start = o;   o = align256(o + 4 * (T + 1));
+    const size_t nn = pbwd ? (size_t)(n > 0 ? n : 0) : 0;
+    w.pb_perm = o;      o = align256(o + 4 * nn);
+    w.pb_mask = o;      o = align256(o + 8 * nn);
     w.dup_tmp = o;      o = align256(o + 8 * (size_t)cap);
     w.dup_tmp2 = o;     o = align256(o + 8 * (size_t)cap);
     w.dxi_acc = o;      o = align256(o + 4 * 6 * (size_t)GEVO_MAX_VIEWS);

@@ -1454,7 +1454,7 @@ extern "C" gevo_status gevo_bin_sort_noalloc(const gevo_layout* layout, int32_t 
         return GEVO_ERR_INVALID;
     if (dup_capacity > GEVO_NOALLOC_MAX_DUPS || layout->total_tiles > GEVO_NOALLOC_MAX_TILES)
         return GEVO_ERR_SCRATCH_LIMIT;
-    const WsLayout w = ws_layout(*layout, n, dup_capacity);
+    const WsLayout w = ws_layout(*layout, n, dup_capacity, false);
     if (w.core > GEVO_NOALLOC_SCRATCH_BYTES) return GEVO_ERR_SCRATCH_LIMIT;
     char* ws = reinterpret_cast<char*>(noalloc_scratch_address());
     if (!ws) return GEVO_ERR_CUDA;

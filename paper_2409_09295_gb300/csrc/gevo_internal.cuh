@@ -37,6 +37,8 @@ struct WsLayout {
     size_t dup_tmp;      // uint64 [cap]  (depth bits << 32 | id), bucketed by tile
     size_t dup_tmp2;     // uint64 [cap]  ping-pong for long tiles
     size_t dxi_acc;      // float [V][6]
+    size_t pb_perm;      // uint32 [n]: the projection backward's Gaussian order
+    size_t pb_mask;      // uint64 [n]: visible-view mask of each, in that order
     size_t core;         // bytes up to here (the no-allocation sort uses only these)
     size_t blk_off;      // uint32 [ceil(n / 2048)][T]: each binning block's run offset per tile
     // depth-ordered binning (gevo_bin_sort on views of at most kOrdMaxTiles tiles)
@@ -67,7 +69,11 @@ constexpr int kDepthBins = 512;     // depth segments per view of the per-view d
 constexpr int kOrdMaxTiles = 8192;  // views with more tiles take the bucket-and-sort path
 constexpr int kOrdUnit = 8192;      // duplicates per block of the order-keeping passes
 constexpr int kOrdScanItems = 4096; // entries per block of the prefix scan
-WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap);
+// pbwd false leaves out the projection backward's order (the no-allocation
+// sort's scratch holds only what the sort uses); every field before dup_tmp has
+// an offset that does not depend on cap, so calls that do not know the
+// capacity (render, projection backward) pass 0.
+WsLayout ws_layout(const gevo_layout& L, int32_t n, uint64_t cap, bool pbwd = true);
 
 // Gaussians per binning block of one view (the binning kernels' chunk).
 constexpr int kBinChunk = 2048;
