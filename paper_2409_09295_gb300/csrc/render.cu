@@ -833,12 +833,22 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 const float vals[12] = {m0, S1, dx * S1, m1, dx * m1, m2, a_r, a_g, a_b, a_z,
                                         DT ? a_o : a_e, a_e};
                 int slot;
+                // one warp per block: an entry's sums come from this warp alone,
+                // so they are stored; several warps add theirs
                 if (NG == 10) {
                     const float tot = warp_reduce10(vals, slot);
-                    if (slot >= 0 && tot != 0.f) atomicAdd(&s_g[j][slot], tot);
+                    if (NW == 1) {
+                        if (slot >= 0) s_g[j][slot] = tot;
+                    } else if (slot >= 0 && tot != 0.f) {
+                        atomicAdd(&s_g[j][slot], tot);
+                    }
                 } else {
                     const float tot = warp_reduce12(vals, slot);
-                    if (slot >= 0 && slot < NG && tot != 0.f) atomicAdd(&s_g[j][slot], tot);
+                    if (NW == 1) {
+                        if (slot >= 0 && slot < NG) s_g[j][slot] = tot;
+                    } else if (slot >= 0 && slot < NG && tot != 0.f) {
+                        atomicAdd(&s_g[j][slot], tot);
+                    }
                 }
             }
             __syncthreads();
