@@ -836,9 +836,12 @@ k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ s
             if (s_h[i]) atomicAdd(seg_count + v * kDepthBins + i, s_h[i]);
         return;
     }
-    for (int i = threadIdx.x; i < kDepthBins; i += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < kDepthBins / 256; q++) {   // the block's reservations in flight together
+        const int i = q * 256 + threadIdx.x;
         if (s_h[i]) s_h[i] = seg_start[v * kDepthBins + i] +
                              atomicAdd(seg_cursor + v * kDepthBins + i, s_h[i]);
+    }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < PER; i++) {
@@ -907,13 +910,22 @@ k_ord_rec(int n, const uint32_t* __restrict__ stat, const uint32_t* __restrict__
     if (p0 >= M) return;   // the whole block: before any barrier
     const uint32_t vs = view_start(stat, v);
     const size_t vb = (size_t)v * n;
-    const int p1 = min(M, p0 + kOrdScanItems);
+    constexpr int PER = kOrdScanItems / 256;
     unsigned long long sum = 0ull;
-    for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const uint32_t g = sorted[vs + p];
-        const uint2 rc = rect[vb + g];
-        rec[vs + p] = make_uint4(g, (uint32_t)dkeys[vs + p], rc.x, rc.y);
-        sum += (unsigned long long)((rc.y & 0xffffu) * (rc.y >> 16));
+    uint32_t g[PER];
+#pragma unroll
+    for (int i = 0; i < PER; i++) {   // the ids, then the gathers, all in flight together
+        const int p = p0 + i * 256 + threadIdx.x;
+        g[i] = p < M ? sorted[vs + p] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int p = p0 + i * 256 + threadIdx.x;
+        if (p < M) {
+            const uint2 rc = rect[vb + g[i]];
+            rec[vs + p] = make_uint4(g[i], (uint32_t)dkeys[vs + p], rc.x, rc.y);
+            sum += (unsigned long long)((rc.y & 0xffffu) * (rc.y >> 16));
+        }
     }
     unsigned long long total;
     block_excl_scan<256>(sum, total);

@@ -68,7 +68,7 @@ struct WsLayout {
 constexpr int kDepthBins = 512;     // depth segments per view of the per-view depth sort
 constexpr int kOrdMaxTiles = 8192;  // views with more tiles take the bucket-and-sort path
 constexpr int kOrdUnit = 8192;      // duplicates per block of the order-keeping passes
-constexpr int kOrdScanItems = 4096; // entries per block of the prefix scan
+constexpr int kOrdScanItems = 1024; // entries per block of the prefix scan (4 per thread)
 // pbwd false leaves out the projection backward's order (the no-allocation
 // sort's scratch holds only what the sort uses); every field before dup_tmp has
 // an offset that does not depend on cap, so calls that do not know the
