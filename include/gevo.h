@@ -188,20 +188,27 @@ gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,
 #define GEVO_PART_GEOMETRY 1  /* everything but the colour                          */
 #define GEVO_PART_COLOUR 2    /* the colour only                                    */
 
-/* gevo_project in two parts, so that a caller whose colour parameters arrive
- * later (a host-to-device copy of the SH coefficients, most of the bytes) can
- * start the sort meanwhile: the sort reads no colour.
+/* Range unit of gevo_project_bwd_part (see there). */
+#define GEVO_PART_RANGE 512
+
+/* gevo_project in two parts and over Gaussian ranges, so that a caller whose
+ * parameters arrive in pieces (host-to-device copies) can project each piece
+ * as it lands, and start the sort while the colour parameters (the SH
+ * coefficients, most of the bytes) are still in flight: the sort reads no
+ * colour.  Only Gaussians g_begin <= g < g_end (0 <= g_begin <= g_end <= n)
+ * are projected, for every view; the records of the others are untouched.
  * GEVO_PART_GEOMETRY writes xy, conic_opacity, radius, tiles_touched and the
  * depth (w) of rgb_depth, with rgb_depth x, y, z = 0; it reads means, scales,
  * quats and opacities only (sh / rgb may still be in flight, but one of them
  * must be non-NULL).  GEVO_PART_COLOUR, after it on the stream (or after an
  * event recorded after it), writes x, y, z of rgb_depth for every entry with
  * radius > 0 and nothing else -- so gevo_bin_sort, which reads only w, may run
- * concurrently.  The two parts give bit for bit what GEVO_PART_ALL gives.
- * part outside 0..2: GEVO_ERR_INVALID. */
+ * concurrently.  The parts, over any ranges covering the map, give bit for
+ * bit what gevo_project gives.  part outside 0..2 or a bad range:
+ * GEVO_ERR_INVALID. */
 gevo_status gevo_project_part(const gevo_layout* layout, const gevo_gaussians* g,
                               const gevo_camera* cams, gevo_proj* out, int32_t part,
-                              void* workspace, void* stream);
+                              int32_t g_begin, int32_t g_end, void* workspace, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Stages a2-a4: keys, bit-exact sort, tile ranges                          */
@@ -337,21 +344,26 @@ gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
                              const gevo_grad2d* grad2d, gevo_gaussian_grads* out, float* dxi,
                              void* workspace, void* stream);
 
-/* gevo_project_bwd in two parts, so that a caller copying the gradients to the
- * host can start with the SH gradients (most of the bytes) while the geometry
- * part still runs.  GEVO_PART_COLOUR zeroes dxi and, for SH colours, writes
- * out->sh and the view-direction share of out->means (and adds the camera
- * centre's share to dxi); for rgb colours it only zeroes dxi.
- * GEVO_PART_GEOMETRY, after it on the stream and with the same workspace (it
- * walks the Gaussians in the order the colour part stored there), writes
- * out->scales, quats, opacities and rgb, adds the rest of out->means (writes it
- * for rgb colours) and adds to dxi.  out->sh is final once the colour part has run.  The two
- * parts give what GEVO_PART_ALL gives (dxi sums in another order; every other
- * output bit for bit).  part outside 0..2: GEVO_ERR_INVALID. */
+/* gevo_project_bwd in two parts and over Gaussian ranges, so that a caller
+ * copying the gradients to the host can start with the SH gradients (most of
+ * the bytes) of the first range while later ranges and the geometry part
+ * still run.  Ranges [g_begin, g_end) start and end at multiples of
+ * GEVO_PART_RANGE (or end at n).  GEVO_PART_COLOUR, for SH colours, writes
+ * out->sh and the view-direction share of out->means for the range and adds
+ * the camera centre's share to dxi; on the range starting at 0 it also zeroes
+ * dxi and stores in the workspace the order in which both parts walk the
+ * Gaussians, so it runs first.  GEVO_PART_GEOMETRY, on ranges whose colour
+ * part has run (same stream, same workspace), writes out->scales, quats,
+ * opacities and rgb, adds the rest of out->means (writes it for rgb colours)
+ * and adds to dxi.  The SH gradients of a range are final once its colour part
+ * has run.  Over ranges covering the map the parts give what gevo_project_bwd
+ * gives (dxi sums in another order; every other output bit for bit).  part
+ * outside 0..2 or a bad range: GEVO_ERR_INVALID. */
 gevo_status gevo_project_bwd_part(const gevo_layout* layout, const gevo_gaussians* g,
                                   const gevo_camera* cams, const gevo_proj* proj,
                                   const gevo_grad2d* grad2d, gevo_gaussian_grads* out,
-                                  float* dxi, int32_t part, void* workspace, void* stream);
+                                  float* dxi, int32_t part, int32_t g_begin, int32_t g_end,
+                                  void* workspace, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Stage a8: L1 loss with stop-gradient targets (E_pho of Eq. 2, E_pc of Eq. 6) */

@@ -91,8 +91,10 @@ EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin
            "gevo_render_fwd_counts", "gevo_bin_sort_launches", "gevo_project_part",
            "gevo_project_bwd_part"]
 
-# Parts of gevo_project_part / gevo_project_bwd_part (include/gevo.h).
+# Parts of gevo_project_part / gevo_project_bwd_part and the backward's range
+# unit (include/gevo.h).
 PART_ALL, PART_GEOMETRY, PART_COLOUR = 0, 1, 2
+PART_RANGE = 512
 
 # Every symbol include/gevo_prior.h declares, with its argument kinds
 # (i: int32, u: uint32, I: int64, f: float, p: pointer; the last p is the stream).
@@ -154,7 +156,7 @@ def load(build_if_missing: bool = True):
     L.gevo_workspace_bytes.argtypes = [P(Layout), i32, u64]
     L.gevo_workspace_bytes.restype = ctypes.c_size_t
     L.gevo_project.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), vp, vp]
-    L.gevo_project_part.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), i32, vp, vp]
+    L.gevo_project_part.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), i32, i32, i32, vp, vp]
     L.gevo_bin_sort.argtypes = [P(Layout), i32, P(Proj), u64, vp, vp, vp, vp, vp, vp]
     L.gevo_bin_sort_launches.argtypes = [P(Layout), i32, u64]
     L.gevo_bin_sort_launches.restype = i32
@@ -171,7 +173,7 @@ def load(build_if_missing: bool = True):
     L.gevo_project_bwd.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d),
                                    P(GaussianGrads), vp, vp, vp]
     L.gevo_project_bwd_part.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d),
-                                        P(GaussianGrads), vp, i32, vp, vp]
+                                        P(GaussianGrads), vp, i32, i32, i32, vp, vp]
     L.gevo_loss_l1.argtypes = [P(Layout), vp, vp, vp, vp, f32, vp, vp, vp, vp, vp]
     L.gevo_loss_l1_err.argtypes = [P(Layout), vp, vp, vp, vp, f32, vp, vp, vp, vp, vp, vp]
     L.gevo_render_bwd_active.argtypes = [P(Layout), i32, P(Proj), vp, vp, P(f32), vp, vp, vp, vp,
@@ -295,13 +297,14 @@ def gevo_project(layout, g: dict, cams: torch.Tensor, proj: dict, ws: torch.Tens
 
 
 def gevo_project_part(layout, g: dict, cams: torch.Tensor, proj: dict, part: int,
-                      ws: torch.Tensor, stream=None):
-    """One part (PART_GEOMETRY or PART_COLOUR) of gevo_project."""
+                      ws: torch.Tensor, stream=None, g_begin=0, g_end=None):
+    """One part (PART_GEOMETRY or PART_COLOUR) of gevo_project, over the
+    Gaussians g_begin <= g < g_end (default: all)."""
     G = gaussians_struct(g)
     P_ = proj_struct(proj)
     _check("gevo_project_part", load().gevo_project_part(
-        ctypes.byref(layout), ctypes.byref(G), _p(cams), ctypes.byref(P_), int(part), _p(ws),
-        _stream(stream)))
+        ctypes.byref(layout), ctypes.byref(G), _p(cams), ctypes.byref(P_), int(part), int(g_begin),
+        int(G.n if g_end is None else g_end), _p(ws), _stream(stream)))
 
 
 def gevo_bin_sort(layout, n, proj: dict, dup_capacity, keys, vals, ranges, d_n_dup, ws,
@@ -425,8 +428,10 @@ def gevo_project_bwd(layout, g: dict, cams, proj: dict, grad2d: dict, out: dict,
 
 
 def gevo_project_bwd_part(layout, g: dict, cams, proj: dict, grad2d: dict, out: dict, dxi,
-                          part: int, ws, stream=None):
-    """One part of gevo_project_bwd: PART_COLOUR first, then PART_GEOMETRY."""
+                          part: int, ws, stream=None, g_begin=0, g_end=None):
+    """One part of gevo_project_bwd over a range of whole PART_RANGE blocks
+    (default: all): PART_COLOUR first (its range at 0 first of all), then
+    PART_GEOMETRY."""
     G = gaussians_struct(g)
     P_ = proj_struct(proj)
     G2 = grad2d_struct(grad2d)
@@ -437,7 +442,8 @@ def gevo_project_bwd_part(layout, g: dict, cams, proj: dict, grad2d: dict, out: 
     O.rgb = _p(out.get("rgb"))
     _check("gevo_project_bwd_part", load().gevo_project_bwd_part(
         ctypes.byref(layout), ctypes.byref(G), _p(cams), ctypes.byref(P_), ctypes.byref(G2),
-        ctypes.byref(O), _p(dxi), int(part), _p(ws), _stream(stream)))
+        ctypes.byref(O), _p(dxi), int(part), int(g_begin), int(G.n if g_end is None else g_end),
+        _p(ws), _stream(stream)))
 
 
 def gevo_project_bwd_active(layout, g: dict, cams, proj: dict, grad2d: dict, active_list, counts,

@@ -283,16 +283,16 @@ class HostStep:
     call step(), synchronise, and read `host_out` (loss per view, dL/dxi per
     view, and the parameter gradients).
 
-    One graph per step, its copies overlapped with the kernels: the geometry
-    parameters and cameras are copied up first and projected (the geometry
-    part); the colour parameters (the SH coefficients, most of the input bytes)
-    follow on a second stream and get their colour part there, beside the
-    sort; the targets, first read by the loss, follow on a third.  After the
-    colour part of the projection backward the SH gradients go down on the
-    second stream while the geometry part runs; then the loss, the pose
-    gradients and the other parameter gradients.  The 2-D gradient rows are
-    zeroed on a fourth stream beside the sort and blend, as in
-    BatchedReplay.step_eager."""
+    One graph per step, its copies overlapped with the kernels: the cameras
+    and the geometry parameters go up first, in CHUNKS pieces, each projected
+    (the geometry part) as soon as it has landed; the colour parameters (the SH
+    coefficients, most of the input bytes) follow and get their colour part
+    beside the sort; the targets, first read by the loss, follow on another
+    stream.  After the reverse walk the colour part of the projection backward
+    runs piece by piece, and each piece's SH gradients go down while the next
+    pieces and the geometry part run; then the loss, the pose gradients and the
+    other parameter gradients.  The 2-D gradient rows are zeroed on a side
+    stream beside the sort and blend, as in BatchedReplay.step_eager."""
 
     def __init__(self, rep: BatchedReplay):
         self.rep = rep
@@ -318,29 +318,47 @@ class HostStep:
             self.host_targets["depth"].copy_(rep.target_depth)
         self.graph = None
 
+    CHUNKS = 4   # pieces of the map the uploads and the SH-gradient read-back move in
+
+    def _chunks(self):
+        """CHUNKS Gaussian ranges in whole PART_RANGE blocks (the backward's unit)."""
+        n = self.rep.pipe.n
+        step = -(-max(n, 1) // self.CHUNKS)
+        step = -(-step // _abi.PART_RANGE) * _abi.PART_RANGE
+        return [(b, min(n, b + step)) for b in range(0, n, step)]
+
     def _body(self):
         rep, p = self.rep, self.rep.pipe
         main = torch.cuda.current_stream()
-        side, side2 = self.side, self.side2
+        up, side2, down = self.side, self.side2, self.side3
         col = "sh" if "sh" in rep.g else "rgb"
-        # geometry and cameras first: the geometry part of the projection and
-        # the sort read nothing else
-        for k, t in self.host_in.items():
-            if k != col:
-                (rep.camt if k == "cams" else rep.g[k]).copy_(t, non_blocking=True)
-        side.wait_stream(main)
-        with torch.cuda.stream(side):
+        geo_keys = [k for k in self.host_in if k not in (col, "cams")]
+        chunks = self._chunks()
+        # the cameras and the geometry parameters go up first, in pieces; each
+        # piece is projected (geometry part) as soon as it has landed
+        up.wait_stream(main)
+        ev_in = []
+        with torch.cuda.stream(up):
+            rep.camt.copy_(self.host_in["cams"], non_blocking=True)
+            for b, e in chunks:
+                for k in geo_keys:
+                    rep.g[k][b:e].copy_(self.host_in[k][b:e], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(up)
+                ev_in.append(ev)
             rep.g[col].copy_(self.host_in[col], non_blocking=True)
             ev_col_in = torch.cuda.Event()
-            ev_col_in.record(side)
-        p.project(rep.g, rep.camt, part=_abi.PART_GEOMETRY)
+            ev_col_in.record(up)
+        for (b, e), ev in zip(chunks, ev_in):
+            main.wait_event(ev)
+            p.project(rep.g, rep.camt, part=_abi.PART_GEOMETRY, g_range=(b, e))
         ev_geo = torch.cuda.Event()
         ev_geo.record(main)
-        with torch.cuda.stream(side):      # colours once they are in, beside the sort
-            side.wait_event(ev_geo)
+        with torch.cuda.stream(up):        # colours once they are in, beside the sort
+            up.wait_event(ev_geo)
             p.project(rep.g, rep.camt, part=_abi.PART_COLOUR)
             ev_col = torch.cuda.Event()
-            ev_col.record(side)
+            ev_col.record(up)
         side2.wait_event(ev_col_in)        # then the targets, first read by the loss
         with torch.cuda.stream(side2):
             rep.target_rgb.copy_(self.host_targets["rgb"], non_blocking=True)
@@ -354,22 +372,26 @@ class HostStep:
         rep._loss_only()
         rep._join_zero()
         rep._render_bwd()
-        p.project_bwd(rep.g, rep.camt, rep.want_dxi, part=_abi.PART_COLOUR)
-        if col == "sh":                    # the SH gradients go down during the geometry part
-            side.wait_stream(main)
-            with torch.cuda.stream(side):
-                self.host_out["sh"].copy_(p.grads["sh"], non_blocking=True)
+        # the SH gradients of each piece go down as soon as its colour part has run
+        for b, e in chunks:
+            p.project_bwd(rep.g, rep.camt, rep.want_dxi, part=_abi.PART_COLOUR, g_range=(b, e))
+            if col == "sh":
+                down.wait_stream(main)
+                with torch.cuda.stream(down):
+                    self.host_out["sh"][b:e].copy_(p.grads["sh"][b:e], non_blocking=True)
         p.project_bwd(rep.g, rep.camt, rep.want_dxi, part=_abi.PART_GEOMETRY)
         self.host_out["loss"].copy_(p.loss, non_blocking=True)
         self.host_out["dxi"].copy_(p.dxi, non_blocking=True)
         for k, v in p.grads.items():
             if not (k == "sh" and col == "sh"):
                 self.host_out[k].copy_(v, non_blocking=True)
-        main.wait_stream(side)
+        main.wait_stream(down)
+        main.wait_stream(up)
 
     def capture(self):
         self.side = torch.cuda.Stream()
         self.side2 = torch.cuda.Stream()
+        self.side3 = torch.cuda.Stream()
         self.rep._warm()
         for _ in range(2):
             self._body()

@@ -224,13 +224,14 @@ k_project_fwd(gevo_layout L, int n, const float* __restrict__ means, const float
               const float4* __restrict__ quats, const float* __restrict__ opac,
               const float* __restrict__ coef, const gevo_camera* __restrict__ cams,
               float2* __restrict__ out_xy, float4* __restrict__ out_co, float4* __restrict__ out_rz,
-              int* __restrict__ out_r, uint32_t* __restrict__ out_tiles, uint32_t* err)
+              int* __restrict__ out_r, uint32_t* __restrict__ out_tiles, uint32_t* err,
+              int g_begin, int g_end)
 {
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
     load_cams(L, cams, s_cam);
     __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+    const int g = g_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= g_end) return;
 
     const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
     const float s[3] = {scales[3 * g], scales[3 * g + 1], scales[3 * g + 2]};
@@ -309,13 +310,13 @@ template <int DEG, bool HAS_RGB>
 __global__ void __launch_bounds__(128)
 k_project_colour(gevo_layout L, int n, const float* __restrict__ means,
                  const float* __restrict__ coef, const gevo_camera* __restrict__ cams,
-                 const int* __restrict__ radius, float4* __restrict__ out_rz)
+                 const int* __restrict__ radius, float4* __restrict__ out_rz, int g_begin, int g_end)
 {
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
     load_cams(L, cams, s_cam);
     __syncthreads();
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n) return;
+    const int g = g_begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= g_end) return;
     unsigned long long vis = visible_views(L, n, g, radius);
     if (!vis) return;
     const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
@@ -341,7 +342,7 @@ k_project_colour(gevo_layout L, int n, const float* __restrict__ means,
 // beside it, so the kernels read one word instead of a radius per view.  The
 // order inside a count is the order of a shared-memory atomic (each Gaussian is
 // still handled once); loads stay within the range's window.
-constexpr int kPbwdRange = 512;
+constexpr int kPbwdRange = GEVO_PART_RANGE;
 __global__ void __launch_bounds__(kPbwdRange)
 k_pbwd_order(gevo_layout L, int n, const int* __restrict__ radius, uint32_t* __restrict__ perm,
              unsigned long long* __restrict__ vmask)
@@ -391,16 +392,16 @@ k_project_bwd_geo(gevo_layout L, int n, const float* __restrict__ means,
                   float* __restrict__ d_scales, float4* __restrict__ d_quats,
                   float* __restrict__ d_opac, float* __restrict__ d_rgb, float* __restrict__ dxi,
                   const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count,
-                  const unsigned long long* __restrict__ vmask)
+                  const unsigned long long* __restrict__ vmask, int t_begin, int t_end)
 {
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
     __shared__ float s_dxi[GEVO_MAX_VIEWS][kDxiCopies][6];
-    const int total = list_count ? (int)*list_count : n;
-    if ((int)(blockIdx.x * blockDim.x) >= total) return;   // whole block: before any barrier
+    const int total = list_count ? (int)*list_count : t_end;
+    if (t_begin + (int)(blockIdx.x * blockDim.x) >= total) return;   // whole block: before any barrier
     load_cams(L, cams, s_cam);
     for (int i = threadIdx.x; i < L.n_views * kDxiCopies * 6; i += blockDim.x) (&s_dxi[0][0][0])[i] = 0.f;
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = t_begin + blockIdx.x * blockDim.x + threadIdx.x;
     const int g = t < total ? (list ? (int)list[t] : t) : n;
     if (g < n) {
         const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
@@ -557,17 +558,17 @@ k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
                   const int* __restrict__ radius, const float4* __restrict__ g_rz,
                   float* __restrict__ d_means, float* __restrict__ d_coef, float* __restrict__ dxi,
                   const uint32_t* __restrict__ list, const uint32_t* __restrict__ list_count,
-                  const unsigned long long* __restrict__ vmask)
+                  const unsigned long long* __restrict__ vmask, int t_begin, int t_end)
 {
     constexpr int K = (DEG + 1) * (DEG + 1);
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
     __shared__ float s_dxi[GEVO_MAX_VIEWS][kDxiCopies][3];
-    const int total = list_count ? (int)*list_count : n;
-    if ((int)(blockIdx.x * blockDim.x) >= total) return;   // whole block: before any barrier
+    const int total = list_count ? (int)*list_count : t_end;
+    if (t_begin + (int)(blockIdx.x * blockDim.x) >= total) return;   // whole block: before any barrier
     load_cams(L, cams, s_cam);
     for (int i = threadIdx.x; i < L.n_views * kDxiCopies * 3; i += blockDim.x) (&s_dxi[0][0][0])[i] = 0.f;
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = t_begin + blockIdx.x * blockDim.x + threadIdx.x;
     const int g = t < total ? (list ? (int)list[t] : t) : n;
     if (g < n) {
         const float mu[3] = {means[3 * g], means[3 * g + 1], means[3 * g + 2]};
@@ -648,25 +649,28 @@ k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
 
 template <int DEG, bool RGB>
 static void launch_fwd(const gevo_layout& L, const gevo_gaussians& g, const gevo_camera* cams,
-                       const gevo_proj& o, int part, uint32_t* err, cudaStream_t st)
+                       const gevo_proj& o, int part, int g_begin, int g_end, uint32_t* err,
+                       cudaStream_t st)
 {
     const int threads = 128;
-    const int blocks = (g.n + threads - 1) / threads;
+    const int blocks = (g_end - g_begin + threads - 1) / threads;
+    if (blocks == 0) return;
     const float* coef = RGB ? g.rgb : g.sh;
     if (part == GEVO_PART_ALL)
         k_project_fwd<DEG, RGB, true><<<blocks, threads, 0, st>>>(
             L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), g.opacities, coef,
             cams, reinterpret_cast<float2*>(o.xy), reinterpret_cast<float4*>(o.conic_opacity),
-            reinterpret_cast<float4*>(o.rgb_depth), o.radius, o.tiles_touched, err);
+            reinterpret_cast<float4*>(o.rgb_depth), o.radius, o.tiles_touched, err, g_begin, g_end);
     else if (part == GEVO_PART_GEOMETRY)
         k_project_fwd<0, true, false><<<blocks, threads, 0, st>>>(
             L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), g.opacities,
             nullptr, cams, reinterpret_cast<float2*>(o.xy),
             reinterpret_cast<float4*>(o.conic_opacity), reinterpret_cast<float4*>(o.rgb_depth),
-            o.radius, o.tiles_touched, err);
+            o.radius, o.tiles_touched, err, g_begin, g_end);
     else
         k_project_colour<DEG, RGB><<<blocks, threads, 0, st>>>(
-            L, g.n, g.means, coef, cams, o.radius, reinterpret_cast<float4*>(o.rgb_depth));
+            L, g.n, g.means, coef, cams, o.radius, reinterpret_cast<float4*>(o.rgb_depth), g_begin,
+            g_end);
 }
 
 // SH colour kernel first (it writes the means' gradient, the geometry kernel
@@ -674,15 +678,17 @@ static void launch_fwd(const gevo_layout& L, const gevo_gaussians& g, const gevo
 template <int DEG, bool RGB>
 static void launch_bwd(const gevo_layout& L, const gevo_gaussians& g, const gevo_camera* cams,
                        const gevo_proj& o, const gevo_grad2d& gr, const gevo_gaussian_grads& out,
-                       float* dxi, int part, cudaStream_t st, const uint32_t* list,
-                       const uint32_t* list_count, const unsigned long long* vmask)
+                       float* dxi, int part, int t_begin, int t_end, cudaStream_t st,
+                       const uint32_t* list, const uint32_t* list_count,
+                       const unsigned long long* vmask)
 {
     const int threads = 128;
-    const int blocks = (g.n + threads - 1) / threads;
+    const int blocks = (t_end - t_begin + threads - 1) / threads;
+    if (blocks == 0) return;
     if (!RGB && part != GEVO_PART_GEOMETRY)
         k_project_bwd_col<DEG><<<blocks, threads, 0, st>>>(
             L, g.n, g.means, g.sh, cams, o.radius, reinterpret_cast<const float4*>(gr.rgb_depth),
-            out.means, out.sh, dxi, list, list_count, vmask);
+            out.means, out.sh, dxi, list, list_count, vmask, t_begin, t_end);
     if (part == GEVO_PART_COLOUR) return;
     const auto geo = RGB ? k_project_bwd_geo<true, false> : k_project_bwd_geo<false, true>;
     geo<<<blocks, threads, 0, st>>>(
@@ -690,7 +696,7 @@ static void launch_bwd(const gevo_layout& L, const gevo_gaussians& g, const gevo
         reinterpret_cast<const float2*>(gr.xy), reinterpret_cast<const float4*>(gr.conic_opacity),
         reinterpret_cast<const float4*>(gr.rgb_depth), out.means, out.scales,
         reinterpret_cast<float4*>(out.quats), out.opacities, out.rgb, dxi, list, list_count,
-        vmask);
+        vmask, t_begin, t_end);
 }
 
 static bool valid_gaussians(const gevo_gaussians* g)
@@ -716,23 +722,24 @@ using namespace gevo;
 
 extern "C" gevo_status gevo_project_part(const gevo_layout* layout, const gevo_gaussians* g,
                                          const gevo_camera* cams, gevo_proj* out, int32_t part,
-                                         void* workspace, void* stream)
+                                         int32_t g_begin, int32_t g_end, void* workspace,
+                                         void* stream)
 {
     if (!layout || !gevo::layout_valid(*layout) || !valid_gaussians(g) || !cams || !valid_proj(out) ||
         !workspace || !gevo_aligned(workspace, 256) || part < GEVO_PART_ALL ||
-        part > GEVO_PART_COLOUR)
+        part > GEVO_PART_COLOUR || g_begin < 0 || g_begin > g_end || g_end > g->n)
         return GEVO_ERR_INVALID;
-    if (g->n == 0) return GEVO_OK;
+    if (g_begin == g_end) return GEVO_OK;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t* err = reinterpret_cast<uint32_t*>(workspace);
     if (g->rgb) {
-        launch_fwd<0, true>(*layout, *g, cams, *out, part, err, st);
+        launch_fwd<0, true>(*layout, *g, cams, *out, part, g_begin, g_end, err, st);
     } else {
         switch (g->sh_degree) {
-        case 0: launch_fwd<0, false>(*layout, *g, cams, *out, part, err, st); break;
-        case 1: launch_fwd<1, false>(*layout, *g, cams, *out, part, err, st); break;
-        case 2: launch_fwd<2, false>(*layout, *g, cams, *out, part, err, st); break;
-        default: launch_fwd<3, false>(*layout, *g, cams, *out, part, err, st); break;
+        case 0: launch_fwd<0, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st); break;
+        case 1: launch_fwd<1, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st); break;
+        case 2: launch_fwd<2, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st); break;
+        default: launch_fwd<3, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st); break;
         }
     }
     GEVO_CHECK_LAUNCH();
@@ -743,16 +750,23 @@ extern "C" gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussi
                                     const gevo_camera* cams, gevo_proj* out, void* workspace,
                                     void* stream)
 {
-    return gevo_project_part(layout, g, cams, out, GEVO_PART_ALL, workspace, stream);
+    return gevo_project_part(layout, g, cams, out, GEVO_PART_ALL, 0, g ? g->n : 0, workspace,
+                             stream);
 }
 
 static gevo_status project_bwd(const gevo_layout* layout, const gevo_gaussians* g,
                                const gevo_camera* cams, const gevo_proj* proj,
                                const gevo_grad2d* grad2d, gevo_gaussian_grads* out, float* dxi,
                                void* workspace, void* stream, const uint32_t* list,
-                               const uint32_t* list_count, int part = GEVO_PART_ALL)
+                               const uint32_t* list_count, int part = GEVO_PART_ALL,
+                               int t_begin = 0, int t_end = -1)
 {
     if (part < GEVO_PART_ALL || part > GEVO_PART_COLOUR) return GEVO_ERR_INVALID;
+    if (g && t_end < 0) t_end = g->n;
+    // a range of the whole map: whole ranges of the walk order
+    if (!g || t_begin < 0 || t_begin > t_end || t_end > g->n || t_begin % kPbwdRange != 0 ||
+        (t_end % kPbwdRange != 0 && t_end != g->n) || (list && (t_begin != 0 || t_end != g->n)))
+        return GEVO_ERR_INVALID;
     if (!layout || !gevo::layout_valid(*layout) || !valid_gaussians(g) || !cams || !proj || !proj->radius ||
         !grad2d || !grad2d->xy || !grad2d->conic_opacity || !grad2d->rgb_depth || !out ||
         !out->means || !out->scales || !out->quats || !out->opacities || !workspace ||
@@ -766,8 +780,10 @@ static gevo_status project_bwd(const gevo_layout* layout, const gevo_gaussians* 
     if (out->sh && (g->sh_degree == 1 || g->sh_degree == 3) && !gevo_aligned(out->sh, 16))
         return GEVO_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
-    // the colour part (alone, or first of the two) starts the pose twist at zero
-    if (dxi && part != GEVO_PART_GEOMETRY &&
+    // the colour part of the range starting at 0 (alone, or first of the two)
+    // starts the pose twist at zero and builds the walk order
+    const bool first = part != GEVO_PART_GEOMETRY && t_begin == 0;
+    if (dxi && first &&
         cudaMemsetAsync(dxi, 0, sizeof(float) * 6 * layout->n_views, st) != cudaSuccess)
         return GEVO_ERR_CUDA;
     if (g->n == 0) return GEVO_OK;
@@ -778,7 +794,7 @@ static gevo_status project_bwd(const gevo_layout* layout, const gevo_gaussians* 
         char* ws = reinterpret_cast<char*>(workspace);
         uint32_t* perm = reinterpret_cast<uint32_t*>(ws + w.pb_perm);
         auto* vm = reinterpret_cast<unsigned long long*>(ws + w.pb_mask);
-        if (part != GEVO_PART_GEOMETRY) {
+        if (first) {
             k_pbwd_order<<<(g->n + kPbwdRange - 1) / kPbwdRange, kPbwdRange, 0, st>>>(
                 L, g->n, proj->radius, perm, vm);
             GEVO_CHECK_LAUNCH();
@@ -787,13 +803,13 @@ static gevo_status project_bwd(const gevo_layout* layout, const gevo_gaussians* 
         vmask = vm;
     }
     if (g->rgb) {
-        launch_bwd<0, true>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count, vmask);
+        launch_bwd<0, true>(L, *g, cams, *proj, *grad2d, *out, dxi, part, t_begin, t_end, st, list, list_count, vmask);
     } else {
         switch (g->sh_degree) {
-        case 0: launch_bwd<0, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count, vmask); break;
-        case 1: launch_bwd<1, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count, vmask); break;
-        case 2: launch_bwd<2, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count, vmask); break;
-        default: launch_bwd<3, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, st, list, list_count, vmask); break;
+        case 0: launch_bwd<0, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, t_begin, t_end, st, list, list_count, vmask); break;
+        case 1: launch_bwd<1, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, t_begin, t_end, st, list, list_count, vmask); break;
+        case 2: launch_bwd<2, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, t_begin, t_end, st, list, list_count, vmask); break;
+        default: launch_bwd<3, false>(L, *g, cams, *proj, *grad2d, *out, dxi, part, t_begin, t_end, st, list, list_count, vmask); break;
         }
     }
     GEVO_CHECK_LAUNCH();
@@ -811,11 +827,11 @@ extern "C" gevo_status gevo_project_bwd(const gevo_layout* layout, const gevo_ga
 extern "C" gevo_status gevo_project_bwd_part(const gevo_layout* layout, const gevo_gaussians* g,
                                              const gevo_camera* cams, const gevo_proj* proj,
                                              const gevo_grad2d* grad2d, gevo_gaussian_grads* out,
-                                             float* dxi, int32_t part, void* workspace,
-                                             void* stream)
+                                             float* dxi, int32_t part, int32_t g_begin,
+                                             int32_t g_end, void* workspace, void* stream)
 {
     return project_bwd(layout, g, cams, proj, grad2d, out, dxi, workspace, stream, nullptr, nullptr,
-                       part);
+                       part, g_begin, g_end);
 }
 
 extern "C" gevo_status gevo_project_bwd_active(const gevo_layout* layout, const gevo_gaussians* g,

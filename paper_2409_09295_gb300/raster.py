@@ -112,13 +112,15 @@ class Pipeline:
         return buf[self.pix_base[v]:self.pix_base[v + 1]].view(H, W)
 
     # ---- stages ----------------------------------------------------------------------
-    def project(self, g, cams, part=None):
+    def project(self, g, cams, part=None, g_range=None):
         """The projection; part = abi.PART_GEOMETRY or abi.PART_COLOUR runs one
-        of its two parts (geometry first)."""
-        if part is None:
+        of its two parts (geometry first), over g_range = (begin, end) if given."""
+        if part is None and g_range is None:
             abi.gevo_project(self.layout, g, cams, self.proj, self.ws)
         else:
-            abi.gevo_project_part(self.layout, g, cams, self.proj, part, self.ws)
+            b, e = g_range if g_range is not None else (0, None)
+            abi.gevo_project_part(self.layout, g, cams, self.proj,
+                                  abi.PART_ALL if part is None else part, self.ws, g_begin=b, g_end=e)
 
     def bin_sort(self):
         abi.gevo_bin_sort(self.layout, self.n, self.proj, self.capacity, self.keys, self.vals,
@@ -148,17 +150,20 @@ class Pipeline:
                             self.T_final, self.n_contrib, dL_drgb, dL_ddepth, dL_dT, self.grad2d,
                             self.ws, tuning or self.tuning)
 
-    def project_bwd(self, g, cams, want_dxi=True, part=None):
+    def project_bwd(self, g, cams, want_dxi=True, part=None, g_range=None):
         """The projection derivative; part = abi.PART_COLOUR then
         abi.PART_GEOMETRY runs it in two parts (the SH gradients final after
-        the first)."""
+        the first), over g_range = (begin, end) in whole abi.PART_RANGE blocks
+        if given (colour ranges in order from 0, before the geometry ones)."""
         dxi = self.dxi if want_dxi else None
-        if part is None:
+        if part is None and g_range is None:
             abi.gevo_project_bwd(self.layout, g, cams, self.proj, self.grad2d, self.grads, dxi,
                                  self.ws)
         else:
+            b, e = g_range if g_range is not None else (0, None)
             abi.gevo_project_bwd_part(self.layout, g, cams, self.proj, self.grad2d, self.grads,
-                                      dxi, part, self.ws)
+                                      dxi, abi.PART_ALL if part is None else part, self.ws,
+                                      g_begin=b, g_end=e)
 
     # ---- active set of the global stage (Section III-B2, Eq. 5) --------------------
     def alloc_active(self):

@@ -48,9 +48,25 @@ def _np(t):
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("case", ["one_view", "uneven_views", "crowded_tile", "long_tiles",
                                   "equal_depths", "one_depth", "wide_depths", "huge_view",
-                                  "empty"])
+                                  "giant_splats", "many_views", "empty"])
 def test_bin_sort_bit_exact(case):
-    if case == "huge_view":
+    if case == "giant_splats":
+        # 90 x 90 = 8100 tiles, the depth-ordered path's largest kind of view: a
+        # few splats cover every tile (8100 duplicates each, so they span several
+        # 1024-duplicate warp ranges and 8192-duplicate units and start and end
+        # inside them) among small ones
+        sizes, n = [(1440, 1440)], 3000
+        rec = scenes.random_records(sizes, n, seed=37, sigma_px=(0.5, 6.0), frac_culled=0.0)
+        big = np.arange(0, n, 500)
+        rec["xy"][0, big] = np.float32(720.0)
+        rec["radius"][0, big] = 1100
+        rec["depth"][0, big[::2]] = np.float32(0.6)   # some nearest, some among the rest
+    elif case == "many_views":
+        # 24 views of 12 tiles each: the unit table and the per-view scans
+        sizes = [(64, 48)] * 24
+        n = 400
+        rec = scenes.random_records(sizes, n, seed=38, sigma_px=(0.5, 20.0))
+    elif case == "huge_view":
         # 132 x 130 = 17160 tiles in one view: more than the 16384 per-view tile
         # counters the shared-memory binning holds, so the global-atomic count
         # and scatter kernels run
@@ -125,6 +141,8 @@ def test_bin_sort_bit_exact(case):
         assert lens.max() > 4096  # global-memory path
     if case == "long_tiles":
         assert ((lens > 2048) & (lens <= 4096)).sum() >= 2
+    if case == "giant_splats":
+        assert int(lens.min()) >= 6 and D > 6 * 8192
     if case == "wide_depths":
         k = ref["keys"] & 0xffffffff
         spans = [int(k[a:b].max()) - int(k[a:b].min()) for a, b in ref["ranges"] if 1 < b - a <= 2048]

@@ -62,6 +62,21 @@ def test_projection_parts_match_whole(deg):
     assert torch.equal(_bits(b.proj["rgb_depth"][vis]), _bits(a.proj["rgb_depth"][vis]))
     with pytest.raises(_abi.GevoError):
         b.project(g, camt, part=3)
+    # over ranges (uneven, any split): the same records
+    c = mk()
+    for t in c.proj.values():
+        t.fill_(7)
+    n = int(g["means"].shape[0])
+    for r in ((0, 777), (777, 20000), (20000, n)):
+        c.project(g, camt, part=_abi.PART_GEOMETRY, g_range=r)
+    for r in ((0, 15000), (15000, n)):
+        c.project(g, camt, part=_abi.PART_COLOUR, g_range=r)
+    torch.cuda.synchronize()
+    assert torch.equal(c.proj["radius"], a.proj["radius"])
+    for k in ("xy", "conic_opacity", "rgb_depth"):
+        assert torch.equal(_bits(c.proj[k][vis]), _bits(a.proj[k][vis])), k
+    with pytest.raises(_abi.GevoError):
+        c.project(g, camt, part=_abi.PART_GEOMETRY, g_range=(10, n + 1))
 
 
 def _random_grad2d(pipe, seed):
@@ -93,6 +108,22 @@ def test_projection_backward_parts_match_whole(deg):
         assert torch.equal(_bits(p.grads[k]), _bits(v)), k
     # the pose twist sums with atomics, in another order
     assert torch.allclose(p.dxi, dxi, rtol=1e-5, atol=1e-6 * float(dxi.abs().max()))
+    # over ranges of whole PART_RANGE blocks: colour ranges in order, then geometry
+    n = int(g["means"].shape[0])
+    R = _abi.PART_RANGE
+    for v in p.grads.values():
+        v.fill_(7)
+    p.dxi.fill_(7)
+    for r in ((0, 16 * R), (16 * R, 40 * R), (40 * R, n)):
+        p.project_bwd(g, camt, part=_abi.PART_COLOUR, g_range=r)
+    for r in ((0, 40 * R), (40 * R, n)):
+        p.project_bwd(g, camt, part=_abi.PART_GEOMETRY, g_range=r)
+    torch.cuda.synchronize()
+    for k, v in whole.items():
+        assert torch.equal(_bits(p.grads[k]), _bits(v)), k
+    assert torch.allclose(p.dxi, dxi, rtol=1e-5, atol=1e-6 * float(dxi.abs().max()))
+    with pytest.raises(_abi.GevoError):   # not a whole range of the walk order
+        p.project_bwd(g, camt, part=_abi.PART_COLOUR, g_range=(100, n))
 
 
 def _rel(a, b):
