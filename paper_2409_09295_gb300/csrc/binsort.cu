@@ -837,11 +837,9 @@ k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ s
         return;
     }
 #pragma unroll
-    for (int q = 0; q < kDepthBins / 256; q++) {   // the block's reservations in flight together
-        const int i = q * 256 + threadIdx.x;
+    for (int i = threadIdx.x; i < kDepthBins; i += 256)   // the block's reservations together
         if (s_h[i]) s_h[i] = seg_start[v * kDepthBins + i] +
                              atomicAdd(seg_cursor + v * kDepthBins + i, s_h[i]);
-    }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < PER; i++) {

@@ -65,7 +65,7 @@ struct WsLayout {
                          // (unit, warp, tile) the earlier warps' count, 16 bits per tile
     size_t total;
 };
-constexpr int kDepthBins = 512;     // depth segments per view of the per-view depth sort
+constexpr int kDepthBins = 256;     // depth segments per view of the per-view depth sort
 constexpr int kOrdMaxTiles = 8192;  // views with more tiles take the bucket-and-sort path
 constexpr int kOrdUnit = 8192;      // duplicates per block of the order-keeping passes
 constexpr int kOrdScanItems = 1024; // entries per block of the prefix scan (4 per thread)

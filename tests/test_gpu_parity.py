@@ -48,9 +48,20 @@ def _np(t):
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("case", ["one_view", "uneven_views", "crowded_tile", "long_tiles",
                                   "equal_depths", "one_depth", "wide_depths", "huge_view",
-                                  "giant_splats", "many_views", "empty"])
+                                  "giant_splats", "many_views", "deep_segment", "empty"])
 def test_bin_sort_bit_exact(case):
-    if case == "giant_splats":
+    if case == "deep_segment":
+        # 5500 of 6000 entries in a depth band narrower than one of the view's
+        # depth segments (outliers stretch the view's depth range): the per-view
+        # depth sort takes its L2 path for a segment of more than 2048 entries
+        sizes, n = [(64, 48)], 6000
+        rec = scenes.random_records(sizes, n, seed=39, sigma_px=(0.5, 3.0), frac_culled=0.0)
+        r = np.random.default_rng(6)
+        d = r.uniform(5.0, 5.001, n)
+        d[:250] = r.uniform(0.5, 0.6, 250)
+        d[250:500] = r.uniform(9.9, 10.0, 250)
+        rec["depth"][0] = d.astype(np.float32)
+    elif case == "giant_splats":
         # 90 x 90 = 8100 tiles, the depth-ordered path's largest kind of view: a
         # few splats cover every tile (8100 duplicates each, so they span several
         # 1024-duplicate warp ranges and 8192-duplicate units and start and end
