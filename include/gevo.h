@@ -189,7 +189,7 @@ gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,
 #define GEVO_PART_COLOUR 2    /* the colour only                                    */
 
 /* Range unit of gevo_project_bwd_part (see there). */
-#define GEVO_PART_RANGE 512
+#define GEVO_PART_RANGE 1024
 
 /* gevo_project in two parts and over Gaussian ranges, so that a caller whose
  * parameters arrive in pieces (host-to-device copies) can project each piece

@@ -94,7 +94,7 @@ EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin
 # Parts of gevo_project_part / gevo_project_bwd_part and the backward's range
 # unit (include/gevo.h).
 PART_ALL, PART_GEOMETRY, PART_COLOUR = 0, 1, 2
-PART_RANGE = 512
+PART_RANGE = 1024
 
 # Every symbol include/gevo_prior.h declares, with its argument kinds
 # (i: int32, u: uint32, I: int64, f: float, p: pointer; the last p is the stream).

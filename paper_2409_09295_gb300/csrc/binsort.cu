@@ -796,18 +796,21 @@ __device__ __forceinline__ int depth_segment(uint32_t lo, unsigned long long mul
 }
 
 // Count (SCATTER false) or place (SCATTER true) each visible entry in its depth
-// segment; block (x, v) takes kBinChunk entries of view v, kBinChunk / 256 per
-// thread.  The block counts its entries per segment in shared memory (the
+// segment; block (x, v) takes kOrdSegChunk entries of view v, kOrdSegChunk / 256
+// per thread.  The block counts its entries per segment in shared memory (the
 // shared atomic's old value ranks an entry inside the block's share); placing,
 // it reserves one run per (block, segment) with a single global atomic.  The
 // order inside a segment is left to the segment sort.
+constexpr int kOrdSegChunk = 4096;   // entries per block of the depth-segment passes
+                                     // (measured: 4096 a little faster than 1024 and 2048)
+
 template <bool SCATTER>
 __global__ void __launch_bounds__(256)
 k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ stat,
           uint32_t* __restrict__ seg_count, const uint32_t* __restrict__ seg_start,
           uint32_t* __restrict__ seg_cursor, unsigned long long* __restrict__ b1)
 {
-    constexpr int PER = kBinChunk / 256;
+    constexpr int PER = kOrdSegChunk / 256;
     __shared__ uint32_t s_h[kDepthBins];
     __shared__ unsigned long long s_mul;
     const int v = blockIdx.y;
@@ -821,7 +824,7 @@ k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ s
     int rank[PER];
 #pragma unroll
     for (int i = 0; i < PER; i++) {   // every load in flight before the first atomic
-        const int g = blockIdx.x * kBinChunk + i * 256 + threadIdx.x;
+        const int g = blockIdx.x * kOrdSegChunk + i * 256 + threadIdx.x;
         d[i] = g < n ? dk[vb + g] : kInvisible;
     }
 #pragma unroll
@@ -844,7 +847,7 @@ k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ s
 #pragma unroll
     for (int i = 0; i < PER; i++) {
         if (d[i] == kInvisible) continue;
-        const int g = blockIdx.x * kBinChunk + i * 256 + threadIdx.x;
+        const int g = blockIdx.x * kOrdSegChunk + i * 256 + threadIdx.x;
         const int sg = depth_segment(lo, mul, d[i]);
         b1[s_h[sg] + rank[i]] = ((unsigned long long)d[i] << 32) | (uint32_t)g;
     }
@@ -1285,7 +1288,7 @@ static gevo_status bin_sort_ordered(const gevo_layout& L, int32_t n, const gevo_
     const uint64_t cap1 = (uint64_t)V * (uint64_t)n;
     int max_tiles = 0;
     for (int v = 0; v < V; v++) max_tiles = std::max(max_tiles, L.tiles_x[v] * L.tiles_y[v]);
-    const int nbx = (n + kBinChunk - 1) / kBinChunk;
+    const int nbx = (n + kOrdSegChunk - 1) / kOrdSegChunk;
     const int nbs = (n + kOrdScanItems - 1) / kOrdScanItems;
 
     if (cudaMemsetAsync(stat, 0, 16 * (size_t)V, st) != cudaSuccess) return GEVO_ERR_CUDA;

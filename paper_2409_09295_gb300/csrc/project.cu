@@ -337,8 +337,9 @@ k_project_colour(gevo_layout L, int n, const float* __restrict__ means,
 // kernels walks its own Gaussian's visible views, so a warp takes as many
 // iterations as its busiest lane: in id order that is 2.25 times the mean on
 // the 16-view benchmark (10.3 against 4.6 views).  Here each range of
-// kPbwdRange consecutive Gaussians is put in order of decreasing visible-view
-// count (1.13 times the mean), and each Gaussian's visible-view mask is stored
+// kPbwdRange (1024) consecutive Gaussians is put in order of decreasing
+// visible-view count (1.06 times the mean; 1.13 for ranges of 512, measured
+// slower), and each Gaussian's visible-view mask is stored
 // beside it, so the kernels read one word instead of a radius per view.  The
 // order inside a count is the order of a shared-memory atomic (each Gaussian is
 // still handled once); loads stay within the range's window.

@@ -114,9 +114,12 @@ def test_projection_backward_parts_match_whole(deg):
     for v in p.grads.values():
         v.fill_(7)
     p.dxi.fill_(7)
-    for r in ((0, 16 * R), (16 * R, 40 * R), (40 * R, n)):
+    b1 = R * (n // (3 * R))
+    b2 = 2 * b1
+    assert 0 < b1 < b2 < n
+    for r in ((0, b1), (b1, b2), (b2, n)):
         p.project_bwd(g, camt, part=_abi.PART_COLOUR, g_range=r)
-    for r in ((0, 40 * R), (40 * R, n)):
+    for r in ((0, b2), (b2, n)):
         p.project_bwd(g, camt, part=_abi.PART_GEOMETRY, g_range=r)
     torch.cuda.synchronize()
     for k, v in whole.items():
