@@ -210,6 +210,17 @@ gevo_status gevo_project_part(const gevo_layout* layout, const gevo_gaussians* g
                               const gevo_camera* cams, gevo_proj* out, int32_t part,
                               int32_t g_begin, int32_t g_end, void* workspace, void* stream);
 
+/* gevo_project_part (part GEVO_PART_ALL or GEVO_PART_GEOMETRY) that also zeroes,
+ * for every entry it finds visible (radius > 0), that entry's rows of *grad2d
+ * -- the rows gevo_render_bwd then accumulates into and gevo_project_bwd reads
+ * -- in the same pass, so that a step needs no separate gevo_grad2d_zero.
+ * Rows of culled entries are left as they are.  GEVO_PART_COLOUR, a NULL or
+ * misaligned grad2d: GEVO_ERR_INVALID. */
+gevo_status gevo_project_zero(const gevo_layout* layout, const gevo_gaussians* g,
+                              const gevo_camera* cams, gevo_proj* out, gevo_grad2d* grad2d,
+                              int32_t part, int32_t g_begin, int32_t g_end, void* workspace,
+                              void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Stages a2-a4: keys, bit-exact sort, tile ranges                          */
 /* ---------------------------------------------------------------------- */

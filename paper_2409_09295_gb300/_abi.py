@@ -89,7 +89,7 @@ EXPORTS = ["gevo_layout_init", "gevo_workspace_bytes", "gevo_project", "gevo_bin
            "gevo_grad2d_zero", "gevo_gemm_bf16", "gevo_loss_l1_err", "gevo_render_bwd_active",
            "gevo_active_set", "gevo_project_bwd_active", "gevo_render_fwd_active",
            "gevo_render_fwd_counts", "gevo_bin_sort_launches", "gevo_project_part",
-           "gevo_project_bwd_part"]
+           "gevo_project_bwd_part", "gevo_project_zero"]
 
 # Parts of gevo_project_part / gevo_project_bwd_part and the backward's range
 # unit (include/gevo.h).
@@ -157,6 +157,8 @@ def load(build_if_missing: bool = True):
     L.gevo_workspace_bytes.restype = ctypes.c_size_t
     L.gevo_project.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), vp, vp]
     L.gevo_project_part.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), i32, i32, i32, vp, vp]
+    L.gevo_project_zero.argtypes = [P(Layout), P(Gaussians), vp, P(Proj), P(Grad2d), i32, i32, i32,
+                                    vp, vp]
     L.gevo_bin_sort.argtypes = [P(Layout), i32, P(Proj), u64, vp, vp, vp, vp, vp, vp]
     L.gevo_bin_sort_launches.argtypes = [P(Layout), i32, u64]
     L.gevo_bin_sort_launches.restype = i32
@@ -410,6 +412,18 @@ def gevo_grad2d_zero(layout, n, proj: dict, grad2d: dict, stream=None):
     _check("gevo_grad2d_zero", load().gevo_grad2d_zero(ctypes.byref(layout), int(n),
                                                        ctypes.byref(P_), ctypes.byref(G2),
                                                        _stream(stream)))
+
+
+def gevo_project_zero(layout, g: dict, cams: torch.Tensor, proj: dict, grad2d: dict, part: int,
+                      ws: torch.Tensor, stream=None, g_begin=0, g_end=None):
+    """gevo_project_part (PART_ALL or PART_GEOMETRY) that also zeroes the 2-D
+    gradient rows of the entries it finds visible."""
+    G = gaussians_struct(g)
+    P_ = proj_struct(proj)
+    G2 = grad2d_struct(grad2d)
+    _check("gevo_project_zero", load().gevo_project_zero(
+        ctypes.byref(layout), ctypes.byref(G), _p(cams), ctypes.byref(P_), ctypes.byref(G2),
+        int(part), int(g_begin), int(G.n if g_end is None else g_end), _p(ws), _stream(stream)))
 
 
 def gevo_project_bwd(layout, g: dict, cams, proj: dict, grad2d: dict, out: dict, dxi, ws,

@@ -82,7 +82,6 @@ class BatchedReplay:
             self.autotune(fwd=tuning_fwd is None, bwd=tuning_bwd is None)
         self.graph = None
         self.stage_graphs = None
-        self.zero_stream = None
         self.bwd_graph = None
 
     # ---- stages with the chosen shapes ------------------------------------------------
@@ -93,7 +92,9 @@ class BatchedReplay:
         self._loss()
 
     def _project(self):
-        self.pipe.project(self.g, self.camt)
+        """The projection, zeroing the 2-D gradient rows the reverse walk will
+        accumulate into (the visible entries') in the same pass."""
+        self.pipe.project(self.g, self.camt, zero_grad2d=True)
 
     def _bin_sort(self):
         self.pipe.bin_sort()
@@ -102,10 +103,6 @@ class BatchedReplay:
         self.pipe.render_fwd(self.bg, tuning=self.tuning_fwd)
 
     def _loss(self):
-        self.pipe.loss_l1(self.target_rgb, self.target_depth, self.lambda_depth)
-        self.pipe.grad2d_zero()
-
-    def _loss_only(self):
         self.pipe.loss_l1(self.target_rgb, self.target_depth, self.lambda_depth)
 
     def _render_bwd(self):
@@ -124,29 +121,11 @@ class BatchedReplay:
                 ("render_bwd", self._render_bwd), ("project_bwd", self._project_bwd)]
 
     def step_eager(self):
-        """One step.  Zeroing the 2-D gradient rows reads only the projection's
-        radii and writes only rows that nothing reads before the reverse walk,
-        so it runs on a side stream beside the sort, blend and loss: its HBM
-        writes overlap their compute (inside a graph, a parallel branch)."""
-        self._project()
-        self._fork_zero()
-        self._bin_sort()
-        self._render_fwd()
-        self._loss_only()
-        self._join_zero()
-        self._render_bwd()
-        self._project_bwd()
-
-    def _fork_zero(self):
-        """Zero the 2-D gradient rows on the side stream (after the projection)."""
-        if self.zero_stream is None:
-            self.zero_stream = torch.cuda.Stream(device=self.pipe.device)
-        self.zero_stream.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(self.zero_stream):
-            self.pipe.grad2d_zero()
-
-    def _join_zero(self):
-        torch.cuda.current_stream().wait_stream(self.zero_stream)
+        """One step: the projection (which also zeroes the 2-D gradient rows of
+        the visible entries), sort, blend, loss, reverse walk, projection
+        backward."""
+        for _, f in self.stages():
+            f()
 
     # ---- autotuner ---------------------------------------------------------------------
     def _search(self, name, run, reps):
@@ -291,8 +270,8 @@ class HostStep:
     stream.  After the reverse walk the colour part of the projection backward
     runs piece by piece, and each piece's SH gradients go down while the next
     pieces and the geometry part run; then the loss, the pose gradients and the
-    other parameter gradients.  The 2-D gradient rows are zeroed on a side
-    stream beside the sort and blend, as in BatchedReplay.step_eager."""
+    other parameter gradients.  The geometry part also zeroes the 2-D gradient
+    rows of the visible entries, as in BatchedReplay.step_eager."""
 
     def __init__(self, rep: BatchedReplay):
         self.rep = rep
@@ -351,7 +330,7 @@ class HostStep:
             ev_col_in.record(up)
         for (b, e), ev in zip(chunks, ev_in):
             main.wait_event(ev)
-            p.project(rep.g, rep.camt, part=_abi.PART_GEOMETRY, g_range=(b, e))
+            p.project(rep.g, rep.camt, part=_abi.PART_GEOMETRY, g_range=(b, e), zero_grad2d=True)
         ev_geo = torch.cuda.Event()
         ev_geo.record(main)
         with torch.cuda.stream(up):        # colours once they are in, beside the sort
@@ -364,13 +343,11 @@ class HostStep:
             rep.target_rgb.copy_(self.host_targets["rgb"], non_blocking=True)
             if "depth" in self.host_targets:
                 rep.target_depth.copy_(self.host_targets["depth"], non_blocking=True)
-        rep._fork_zero()
         rep._bin_sort()
         main.wait_event(ev_col)
         rep._render_fwd()
         main.wait_stream(side2)
-        rep._loss_only()
-        rep._join_zero()
+        rep._loss()
         rep._render_bwd()
         # the SH gradients of each piece go down as soon as its colour part has run
         for b, e in chunks:

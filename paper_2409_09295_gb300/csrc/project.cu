@@ -225,7 +225,8 @@ k_project_fwd(gevo_layout L, int n, const float* __restrict__ means, const float
               const float* __restrict__ coef, const gevo_camera* __restrict__ cams,
               float2* __restrict__ out_xy, float4* __restrict__ out_co, float4* __restrict__ out_rz,
               int* __restrict__ out_r, uint32_t* __restrict__ out_tiles, uint32_t* err,
-              int g_begin, int g_end)
+              int g_begin, int g_end, float2* __restrict__ z_xy, float4* __restrict__ z_co,
+              float4* __restrict__ z_rz)
 {
     __shared__ CamS s_cam[GEVO_MAX_VIEWS];
     load_cams(L, cams, s_cam);
@@ -279,6 +280,11 @@ k_project_fwd(gevo_layout L, int n, const float* __restrict__ means, const float
                     out_xy[idx] = make_float2(mx, my);
                     out_co[idx] = make_float4(ca, cb, cc, o);
                     out_rz[idx] = make_float4(rgb[0], rgb[1], rgb[2], G.p[2]);
+                    if (z_xy) {   // the reverse walk accumulates into exactly these rows
+                        z_xy[idx] = make_float2(0.f, 0.f);
+                        z_co[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        z_rz[idx] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 }
             }
         } else if (!(G.p[2] == G.p[2])) {
@@ -651,8 +657,11 @@ k_project_bwd_col(gevo_layout L, int n, const float* __restrict__ means,
 template <int DEG, bool RGB>
 static void launch_fwd(const gevo_layout& L, const gevo_gaussians& g, const gevo_camera* cams,
                        const gevo_proj& o, int part, int g_begin, int g_end, uint32_t* err,
-                       cudaStream_t st)
+                       cudaStream_t st, const gevo_grad2d* zero = nullptr)
 {
+    float2* z_xy = zero ? reinterpret_cast<float2*>(zero->xy) : nullptr;
+    float4* z_co = zero ? reinterpret_cast<float4*>(zero->conic_opacity) : nullptr;
+    float4* z_rz = zero ? reinterpret_cast<float4*>(zero->rgb_depth) : nullptr;
     const int threads = 128;
     const int blocks = (g_end - g_begin + threads - 1) / threads;
     if (blocks == 0) return;
@@ -661,13 +670,14 @@ static void launch_fwd(const gevo_layout& L, const gevo_gaussians& g, const gevo
         k_project_fwd<DEG, RGB, true><<<blocks, threads, 0, st>>>(
             L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), g.opacities, coef,
             cams, reinterpret_cast<float2*>(o.xy), reinterpret_cast<float4*>(o.conic_opacity),
-            reinterpret_cast<float4*>(o.rgb_depth), o.radius, o.tiles_touched, err, g_begin, g_end);
+            reinterpret_cast<float4*>(o.rgb_depth), o.radius, o.tiles_touched, err, g_begin, g_end,
+            z_xy, z_co, z_rz);
     else if (part == GEVO_PART_GEOMETRY)
         k_project_fwd<0, true, false><<<blocks, threads, 0, st>>>(
             L, g.n, g.means, g.scales, reinterpret_cast<const float4*>(g.quats), g.opacities,
             nullptr, cams, reinterpret_cast<float2*>(o.xy),
             reinterpret_cast<float4*>(o.conic_opacity), reinterpret_cast<float4*>(o.rgb_depth),
-            o.radius, o.tiles_touched, err, g_begin, g_end);
+            o.radius, o.tiles_touched, err, g_begin, g_end, z_xy, z_co, z_rz);
     else
         k_project_colour<DEG, RGB><<<blocks, threads, 0, st>>>(
             L, g.n, g.means, coef, cams, o.radius, reinterpret_cast<float4*>(o.rgb_depth), g_begin,
@@ -721,30 +731,51 @@ static bool valid_proj(const gevo_proj* p)
 
 using namespace gevo;
 
-extern "C" gevo_status gevo_project_part(const gevo_layout* layout, const gevo_gaussians* g,
-                                         const gevo_camera* cams, gevo_proj* out, int32_t part,
-                                         int32_t g_begin, int32_t g_end, void* workspace,
-                                         void* stream)
+static gevo_status project_fwd(const gevo_layout* layout, const gevo_gaussians* g,
+                               const gevo_camera* cams, gevo_proj* out, int32_t part,
+                               int32_t g_begin, int32_t g_end, void* workspace, void* stream,
+                               const gevo_grad2d* zero)
 {
     if (!layout || !gevo::layout_valid(*layout) || !valid_gaussians(g) || !cams || !valid_proj(out) ||
         !workspace || !gevo_aligned(workspace, 256) || part < GEVO_PART_ALL ||
         part > GEVO_PART_COLOUR || g_begin < 0 || g_begin > g_end || g_end > g->n)
         return GEVO_ERR_INVALID;
+    if (zero && (part == GEVO_PART_COLOUR || !zero->xy || !zero->conic_opacity ||
+                 !zero->rgb_depth || !gevo_aligned(zero->xy, 8) ||
+                 !gevo_aligned(zero->conic_opacity, 16) || !gevo_aligned(zero->rgb_depth, 16)))
+        return GEVO_ERR_INVALID;
     if (g_begin == g_end) return GEVO_OK;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t* err = reinterpret_cast<uint32_t*>(workspace);
     if (g->rgb) {
-        launch_fwd<0, true>(*layout, *g, cams, *out, part, g_begin, g_end, err, st);
+        launch_fwd<0, true>(*layout, *g, cams, *out, part, g_begin, g_end, err, st, zero);
     } else {
         switch (g->sh_degree) {
-        case 0: launch_fwd<0, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st); break;
-        case 1: launch_fwd<1, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st); break;
-        case 2: launch_fwd<2, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st); break;
-        default: launch_fwd<3, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st); break;
+        case 0: launch_fwd<0, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st, zero); break;
+        case 1: launch_fwd<1, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st, zero); break;
+        case 2: launch_fwd<2, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st, zero); break;
+        default: launch_fwd<3, false>(*layout, *g, cams, *out, part, g_begin, g_end, err, st, zero); break;
         }
     }
     GEVO_CHECK_LAUNCH();
     return GEVO_OK;
+}
+
+extern "C" gevo_status gevo_project_part(const gevo_layout* layout, const gevo_gaussians* g,
+                                         const gevo_camera* cams, gevo_proj* out, int32_t part,
+                                         int32_t g_begin, int32_t g_end, void* workspace,
+                                         void* stream)
+{
+    return project_fwd(layout, g, cams, out, part, g_begin, g_end, workspace, stream, nullptr);
+}
+
+extern "C" gevo_status gevo_project_zero(const gevo_layout* layout, const gevo_gaussians* g,
+                                         const gevo_camera* cams, gevo_proj* out,
+                                         gevo_grad2d* grad2d, int32_t part, int32_t g_begin,
+                                         int32_t g_end, void* workspace, void* stream)
+{
+    if (!grad2d) return GEVO_ERR_INVALID;
+    return project_fwd(layout, g, cams, out, part, g_begin, g_end, workspace, stream, grad2d);
 }
 
 extern "C" gevo_status gevo_project(const gevo_layout* layout, const gevo_gaussians* g,

@@ -112,10 +112,17 @@ class Pipeline:
         return buf[self.pix_base[v]:self.pix_base[v + 1]].view(H, W)
 
     # ---- stages ----------------------------------------------------------------------
-    def project(self, g, cams, part=None, g_range=None):
+    def project(self, g, cams, part=None, g_range=None, zero_grad2d=False):
         """The projection; part = abi.PART_GEOMETRY or abi.PART_COLOUR runs one
-        of its two parts (geometry first), over g_range = (begin, end) if given."""
-        if part is None and g_range is None:
+        of its two parts (geometry first), over g_range = (begin, end) if given.
+        zero_grad2d: also zero the 2-D gradient rows of the visible entries (all
+        or geometry part), in place of grad2d_zero."""
+        if zero_grad2d:
+            b, e = g_range if g_range is not None else (0, None)
+            abi.gevo_project_zero(self.layout, g, cams, self.proj, self.grad2d,
+                                  abi.PART_ALL if part is None else part, self.ws, g_begin=b,
+                                  g_end=e)
+        elif part is None and g_range is None:
             abi.gevo_project(self.layout, g, cams, self.proj, self.ws)
         else:
             b, e = g_range if g_range is not None else (0, None)

@@ -167,3 +167,35 @@ def test_host_step_matches_device_step():
         for k, v in p.grads.items():
             assert float(v.norm()) > 0, k
             assert _rel(hs.host_out[k], v.cpu()) < 1e-5, (it, k)
+
+
+@pytest.mark.parametrize("deg", [None, 3])
+def test_projection_that_zeroes_the_gradient_rows(deg):
+    g, camt, mk = _setup(deg)
+    a, b = mk(), mk()
+    a.project(g, camt)
+    for t in b.grad2d.values():
+        t.fill_(7)
+    b.project(g, camt, zero_grad2d=True)
+    torch.cuda.synchronize()
+    vis = a.proj["radius"] > 0
+    assert torch.equal(b.proj["radius"], a.proj["radius"])
+    for k in ("xy", "conic_opacity", "rgb_depth"):
+        assert torch.equal(_bits(b.proj[k][vis]), _bits(a.proj[k][vis])), k
+    for k, t in b.grad2d.items():   # the visible entries' rows zeroed, the others untouched
+        assert torch.count_nonzero(t[vis]) == 0, k
+        assert bool((t[~vis] == 7).all()), k
+    # the geometry part over ranges does the same for its Gaussians
+    c = mk()
+    for t in c.grad2d.values():
+        t.fill_(7)
+    n = int(g["means"].shape[0])
+    for r in ((0, 9999), (9999, n)):
+        c.project(g, camt, part=_abi.PART_GEOMETRY, g_range=r, zero_grad2d=True)
+    c.project(g, camt, part=_abi.PART_COLOUR)
+    torch.cuda.synchronize()
+    assert torch.equal(_bits(c.proj["rgb_depth"][vis]), _bits(a.proj["rgb_depth"][vis]))
+    for k, t in c.grad2d.items():
+        assert torch.count_nonzero(t[vis]) == 0 and bool((t[~vis] == 7).all()), k
+    with pytest.raises(_abi.GevoError):
+        c.project(g, camt, part=_abi.PART_COLOUR, zero_grad2d=True)
