@@ -1,7 +1,8 @@
 """CPU checks of the C ABI library: it builds for sm_103a, loads without a GPU,
 exports every symbol include/gevo.h declares, and its host-only set-up calls
-(layout, workspace size, status strings) behave as the header states.  No
-compute entry point is called here."""
+(layout, workspace size, status strings, the sort's launch count) behave as the
+header states.  Compute entry points are called here only with arguments they
+refuse before any launch."""
 import ctypes
 import os
 import re
@@ -120,3 +121,60 @@ def _prior_kinds():
 def test_prior_binding_signatures_match_header():
     from paper_2409_09295_gb300 import _abi
     assert _abi.PRIOR == _prior_kinds()
+
+
+def test_sort_launch_count_follows_the_dispatch():
+    """gevo_bin_sort_launches: 12 kernels on the depth-ordered path (views of at
+    most 8192 tiles), 4 on the bucket-and-sort path, fewer without entries or
+    without room; -1 for a bad layout.  Host logic only."""
+    from paper_2409_09295_gb300 import _abi
+    small = _abi.gevo_layout_init([640, 320], [480, 240])     # 1200 + 300 tiles
+    edge = _abi.gevo_layout_init([1440], [1456])              # 90 x 91 = 8190 tiles
+    big = _abi.gevo_layout_init([2112, 64], [2080, 48])       # 132 x 130 tiles in one view
+    n, cap = 1000, 10 ** 6
+    assert _abi.gevo_bin_sort_launches(small, n, cap) == 12
+    assert _abi.gevo_bin_sort_launches(edge, n, cap) == 12
+    assert _abi.gevo_bin_sort_launches(big, n, cap) == 4
+    assert _abi.gevo_bin_sort_launches(small, 0, cap) == 5    # totals, counts, scans, scatter
+    assert _abi.gevo_bin_sort_launches(small, n, 0) == 11     # no scatter
+    assert _abi.gevo_bin_sort_launches(big, 0, cap) == 1
+    bad = _abi.Layout.from_buffer_copy(small)
+    bad.n_views = 0
+    assert _abi.gevo_bin_sort_launches(bad, n, cap) == -1
+
+
+def test_part_calls_refuse_bad_parts_and_ranges(lib):
+    """The projection's part calls check part and range before any launch (the
+    pointers below are never dereferenced), so no GPU is needed."""
+    from paper_2409_09295_gb300 import _abi
+    L = _abi.load()
+    lay = _abi.gevo_layout_init([64], [48])
+    d = ctypes.c_void_p(256)
+    n = 5000
+    g = _abi.Gaussians(d, d, d, d, d, None, n, 3)
+    proj = _abi.Proj(d, d, d, d, d)
+    g2 = _abi.Grad2d(d, d, d)
+    out = _abi.GaussianGrads(d, d, d, d, d, None)
+    R = _abi.PART_RANGE
+
+    def fwd(part, b, e):
+        return L.gevo_project_part(ctypes.byref(lay), ctypes.byref(g), d, ctypes.byref(proj), part,
+                                   b, e, d, None)
+
+    def zero(part, b, e, grad=g2):
+        return L.gevo_project_zero(ctypes.byref(lay), ctypes.byref(g), d, ctypes.byref(proj),
+                                   ctypes.byref(grad) if grad is not None else None, part, b, e,
+                                   d, None)
+
+    def bwd(part, b, e):
+        return L.gevo_project_bwd_part(ctypes.byref(lay), ctypes.byref(g), d, ctypes.byref(proj),
+                                       ctypes.byref(g2), ctypes.byref(out), d, part, b, e, d, None)
+
+    for part, b, e in ((3, 0, n), (-1, 0, n), (0, 10, 5), (0, -1, n), (0, 0, n + 1)):
+        assert fwd(part, b, e) == 1
+        assert zero(part, b, e) == 1
+    assert zero(_abi.PART_COLOUR, 0, n) == 1                  # the colour part zeroes nothing
+    assert zero(_abi.PART_ALL, 0, n, grad=None) == 1
+    for part, b, e in ((3, 0, n), (0, 100, n), (0, 0, R + 1), (0, R, R - 1), (0, 0, n + R)):
+        assert bwd(part, b, e) == 1
+    assert fwd(_abi.PART_GEOMETRY, 7, 7) == 0                 # an empty range is a no-op
