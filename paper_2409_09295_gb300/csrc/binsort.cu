@@ -2,7 +2,11 @@
 // (tile, depth) key per (Gaussian, tile) pair, sort the keys bit-exactly and
 // find each tile's range.
 //
-// GB300 design (instead of one 64-bit radix sort over all duplicates):
+// Two GB300 designs instead of one 64-bit radix sort over all duplicates.
+// Views of up to kOrdMaxTiles tiles take the depth-ordered path further down:
+// each view's visible entries are sorted by depth once and every duplicate is
+// emitted straight into its sorted place (no per-tile sort).  Larger views,
+// and the no-allocation call, take the bucket-and-sort path:
 //   1. k_count   : per-tile duplicate counts (one L2 atomic per duplicate);
 //   2. k_scan    : one block scans the counts -> tile starts, the ranges, the
 //                  total D and a heaviest-first tile order for later kernels;
