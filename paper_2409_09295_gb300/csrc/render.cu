@@ -570,7 +570,7 @@ __device__ __forceinline__ float warp_reduce12(const float v[12], int& slot)
 // exact), the suffix scalar and every sum unchanged -- and the derivatives
 // through alpha are kept only where o G <= 0.99 (alpha not clamped).
 #ifndef GEVO_BWD8_MINB
-#define GEVO_BWD8_MINB 16   // 32-thread walk: at most 128 registers (measured best of 1, 16, 20)
+#define GEVO_BWD8_MINB 14   // 32-thread walk: at most 146 registers (measured best of 12, 14, 16, 18)
 #endif
 template <int PPT, bool DD, bool DT, bool EXT>
 __global__ void __launch_bounds__(256 / PPT, (PPT == 8 ? GEVO_BWD8_MINB : 1))
