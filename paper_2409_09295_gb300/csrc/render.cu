@@ -590,10 +590,12 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     constexpr int NV = PPT / W2;
     constexpr int NT = 256 / PPT;
     constexpr int NW = NT / 32;
-    // staging batch: half a record per thread (measured on the benchmark: 32
-    // entries at 64 threads beat 64, 96, 128 and 256; the walk starts near each
-    // warp's last blended position, so short batches waste less)
-    constexpr int kBatch = NT >= 64 ? NT / 2 : NT;
+    // staging batch: half a record per thread from 64 threads up (measured on
+    // the benchmark: 32 entries at 64 threads beat 64, 96, 128 and 256; the walk
+    // starts near each warp's last blended position, so short batches waste
+    // less), two records per thread for the one-warp walk (64 entries beat 16
+    // and 32 there: fewer barriers and list rounds per entry)
+    constexpr int kBatch = NT >= 64 ? NT / 2 : 2 * NT;
     __shared__ Staged s_e[kBatch];
     __shared__ uint32_t s_mask[kBatch];
     __shared__ uint32_t s_id[kBatch];
