@@ -573,7 +573,7 @@ __device__ __forceinline__ float warp_reduce12(const float v[12], int& slot)
 #define GEVO_BWD8_MINB 14   // 32-thread walk: at most 146 registers (measured best of 12, 14, 16, 18)
 #endif
 template <int PPT, bool DD, bool DT, bool EXT>
-__global__ void __launch_bounds__(256 / PPT, (PPT == 8 ? GEVO_BWD8_MINB : 1))
+__global__ void __launch_bounds__(256 / PPT, (PPT == 8 ? (EXT ? 16 : GEVO_BWD8_MINB) : 1))
 k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* __restrict__ co,
              const float4* __restrict__ rz, const uint32_t* __restrict__ vals,
              const uint2* __restrict__ ranges, float bg0, float bg1, float bg2,
@@ -594,8 +594,9 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
     // the benchmark: 32 entries at 64 threads beat 64, 96, 128 and 256; the walk
     // starts near each warp's last blended position, so short batches waste
     // less), two records per thread for the one-warp walk (64 entries beat 16
-    // and 32 there: fewer barriers and list rounds per entry)
-    constexpr int kBatch = NT >= 64 ? NT / 2 : 2 * NT;
+    // and 32 there: fewer barriers and list rounds per entry; the active-set
+    // variant keeps 32, measured faster for it)
+    constexpr int kBatch = NT >= 64 ? NT / 2 : (EXT ? NT : 2 * NT);
     __shared__ Staged s_e[kBatch];
     __shared__ uint32_t s_mask[kBatch];
     __shared__ uint32_t s_id[kBatch];
