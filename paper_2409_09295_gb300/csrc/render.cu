@@ -169,6 +169,10 @@ __device__ __forceinline__ bool window_ok(float d, float m)
     return fabsf(d) <= m;
 }
 
+// Where the window test passes, p2 <= 0 up to rounding, so G <= 1 + 2^-20 and
+// an entry of opacity o <= 0.98 has o G < 0.99: its alpha is never clamped.
+constexpr float kNoClampO = 0.98f;
+
 // A staged list entry, every value held twice (as a pair), so that the walk
 // loads its operands straight into paired registers: mean (x, y), pre-scaled
 // conic (a', b', c'), opacity o, m = log2(255 o) / 2 of the window test, and
@@ -742,6 +746,11 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 // per-thread sums over its pixels (pairs), reduced below
                 V s0 = vsplat<V>(0.f), s1 = s0, s2 = s0, so = s0, sr = s0, sg = s0, sb = s0,
                   sz = s0, se = s0;
+                // NC: the entry cannot reach the alpha clamp (o <= kNoClampO), so
+                // alpha needs no minimum and dL/dalpha no clamp select; without
+                // dL/dT_final an unused pixel's alpha = 0 already zeroes its term
+                auto pixels = [&](auto nc_tag) {
+                constexpr bool NC = decltype(nc_tag)::value;
 #pragma unroll
                 for (int h = 0; h < NV; h++) {
                     const V dy = vsub(e.my, pyv[h]);
@@ -758,8 +767,13 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                         const int k = h * W2 + i;
                         const float ogi = vlane(og, i);
                         const bool use = pos < last[k] && window_ok(vlane(dwin, i), e.m);
-                        kk[i] = use && ogi <= kAlphaMax;      // alpha not clamped
-                        al[i] = use ? fminf(kAlphaMax, ogi) : 0.f;
+                        if (NC) {
+                            kk[i] = use;
+                            al[i] = use ? ogi : 0.f;
+                        } else {
+                            kk[i] = use && ogi <= kAlphaMax;      // alpha not clamped
+                            al[i] = use ? fminf(kAlphaMax, ogi) : 0.f;
+                        }
                     }
                     const V alpha = vpack<V>(al);                    // 0 where unused
                     const V om = vsub(one, alpha);
@@ -798,15 +812,22 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                         dp = vmul(kd, alpha);
                     } else {
                         const V gw = vmul(gd, w);
+                        if (NC) {
+                            dp = gw;
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < W2; i++) dd[i] = kk[i] ? vlane(gw, i) : 0.f;
-                        dp = vpack<V>(dd);
+                            for (int i = 0; i < W2; i++) dd[i] = kk[i] ? vlane(gw, i) : 0.f;
+                            dp = vpack<V>(dd);
+                        }
                     }
                     const V t = vmul(dp, dy);
                     s0 = vadd(s0, dp);
                     s1 = vadd(s1, t);
                     s2 = vfma(t, dy, s2);
                 }
+                };
+                if (!DT && e.o <= kNoClampO) pixels(std::true_type{});
+                else pixels(std::false_type{});
                 float m0 = vlane(s0, 0), m1 = vlane(s1, 0), m2 = vlane(s2, 0);
                 float a_o = vlane(so, 0), a_r = vlane(sr, 0), a_g = vlane(sg, 0),
                       a_b = vlane(sb, 0), a_z = vlane(sz, 0), a_e = vlane(se, 0);
