@@ -53,7 +53,10 @@ k_count(gevo_layout L, int n, const float2* __restrict__ xy, const int* __restri
 // walks it 32 tiles at a time (coalesced loads, warp scans with a carry); the
 // warps' chunk totals are scanned once in shared memory.  The heaviest-first
 // order buckets tiles by floor(log2(count)); bucket counts and positions are
-// taken with one shared-memory atomic per distinct bucket per warp step.
+// taken with one shared-memory atomic per distinct bucket per warp step.  When
+// a chunk is at most kScanCache steps (T <= 16384) its counts are read once,
+// all at a time, and kept in registers for the three passes.
+constexpr int kScanCache = 16;
 __global__ void __launch_bounds__(1024)
 k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* __restrict__ tile_start,
        uint32_t* __restrict__ tile_cursor, uint32_t* __restrict__ tile_order,
@@ -69,9 +72,38 @@ k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* _
     const int chunk = ((T + NW - 1) / NW + 31) & ~31;
     const int w0 = min(T, warp * chunk), w1 = min(T, w0 + chunk);
     const uint32_t lt = (1u << lane) - 1u;
+    const bool cached = chunk <= 32 * kScanCache;   // the same in every warp
+    uint32_t cc[kScanCache];
+    // every pass visits the chunk's steps in order; step i covers tiles
+    // w0 + 32 i + lane, and f(t, valid, c) is called by the whole warp
+    auto steps = [&](auto&& f) {
+        if (cached) {
+#pragma unroll
+            for (int i = 0; i < kScanCache; i++) {
+                const int b0 = w0 + 32 * i;
+                if (b0 >= w1) break;
+                f(b0 + lane, b0 + lane < w1, cc[i]);
+            }
+        } else {
+            for (int b0 = w0; b0 < w1; b0 += 32) {
+                const int t = b0 + lane;
+                f(t, t < w1, t < w1 ? tile_count[t] : 0u);
+            }
+        }
+    };
     if (tid < 34) s_bucket[tid] = 0;
     unsigned long long sum = 0;
-    for (int t = w0 + lane; t < w1; t += 32) sum += tile_count[t];
+    if (cached) {
+#pragma unroll
+        for (int i = 0; i < kScanCache; i++) {
+            const int t = w0 + 32 * i + lane;
+            cc[i] = t < w1 ? tile_count[t] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < kScanCache; i++) sum += cc[i];
+    } else {
+        for (int t = w0 + lane; t < w1; t += 32) sum += tile_count[t];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) s_warp[warp] = sum;
@@ -93,10 +125,7 @@ k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* _
     const unsigned long long D = known_total ? *known_total : s_total;
     const bool overflow = D > cap;
     unsigned long long carry = s_warp[warp];
-    for (int b0 = w0; b0 < w1; b0 += 32) {
-        const int t = b0 + lane;
-        const bool valid = t < w1;
-        const uint32_t c = valid ? tile_count[t] : 0u;
+    steps([&](int t, bool valid, uint32_t c) {
         unsigned long long incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -115,7 +144,7 @@ k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* _
         const int b = valid ? (c == 0 ? 0 : 32 - __clz(c)) : 34;
         const uint32_t peers = __match_any_sync(0xffffffffu, b);
         if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_bucket[b], __popc(peers));
-    }
+    });
     if (tid == 0) {
         *d_n_dup = D;
         if (overflow) atomicOr(err, kErrCapacity);
@@ -126,10 +155,7 @@ k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* _
         for (int b = 33; b >= 0; b--) { s_bucket_base[b] = acc; acc += s_bucket[b]; }
     }
     __syncthreads();
-    for (int b0 = w0; b0 < w1; b0 += 32) {
-        const int t = b0 + lane;
-        const bool valid = t < w1;
-        const uint32_t c = valid ? tile_count[t] : 0u;
+    steps([&](int t, bool valid, uint32_t c) {
         const int b = valid ? (c == 0 ? 0 : 32 - __clz(c)) : 34;
         const uint32_t peers = __match_any_sync(0xffffffffu, b);
         const int leader = __ffs(peers) - 1;
@@ -137,7 +163,7 @@ k_scan(int T, uint64_t cap, const uint32_t* __restrict__ tile_count, uint32_t* _
         if (valid && lane == leader) base = atomicAdd(&s_bucket_base[b], __popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (valid) tile_order[base + __popc(peers & lt)] = (uint32_t)t;
-    }
+    });
 }
 
 __global__ void __launch_bounds__(256)
@@ -950,24 +976,38 @@ k_ord_bscan(int V, int nbs, uint64_t cap, const uint32_t* __restrict__ stat,
             unsigned long long* __restrict__ pre)
 {
     __shared__ unsigned long long s_dv[GEVO_MAX_VIEWS];
+    __shared__ uint32_t s_m[GEVO_MAX_VIEWS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int v = warp; v < V; v += 32) {
         const uint32_t M = stat[4 * v + 2];
         const int nb = (int)((M + kOrdScanItems - 1) / kOrdScanItems);
+        unsigned long long* bs = bsum + (size_t)v * nbs;
         unsigned long long carry = 0ull;
-        for (int c0 = 0; c0 < nb; c0 += 32) {
-            const int i = c0 + lane;
-            const unsigned long long x = i < nb ? bsum[(size_t)v * nbs + i] : 0ull;
-            unsigned long long incl = x;
+        for (int c0 = 0; c0 < nb; c0 += 128) {   // four steps' loads at a time
+            unsigned long long xs[4];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+            for (int k = 0; k < 4; k++) {
+                const int i = c0 + 32 * k + lane;
+                xs[k] = i < nb ? bs[i] : 0ull;
             }
-            if (i < nb) bsum[(size_t)v * nbs + i] = carry + incl - x;
-            carry += __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int i = c0 + 32 * k + lane;
+                const unsigned long long x = xs[k];
+                unsigned long long incl = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (i < nb) bs[i] = carry + incl - x;
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
         }
-        if (lane == 0) s_dv[v] = carry;
+        if (lane == 0) {
+            s_dv[v] = carry;
+            s_m[v] = M;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -976,7 +1016,7 @@ k_ord_bscan(int V, int nbs, uint64_t cap, const uint32_t* __restrict__ stat,
         const bool overflow = D > cap;
         unsigned long long u = 0ull;
         for (int v = 0; v < V; v++) {
-            const uint32_t M = stat[4 * v + 2];
+            const uint32_t M = s_m[v];
             units[kUnitFirst + v] = u;
             units[kUnitDv + v] = s_dv[v];
             units[kUnitVs + v] = vs;
@@ -1041,11 +1081,20 @@ k_ord_pre(const uint32_t* __restrict__ stat, const unsigned long long* __restric
     }
 }
 
-// View of unit u: first[v] <= u < first[v + 1] (the table's end is the unit count).
-__device__ __forceinline__ int view_of_unit(const unsigned long long* units, int u)
+// The view v of unit u, first[v] <= u < first[v + 1] (the table's end is the
+// unit count): the number of views whose successor's first unit is at or
+// below u (first units rise with the view).  Called by whole warps: the
+// lanes read the table at once and count by ballot, one memory latency instead
+// of one per view.
+__device__ __forceinline__ int view_of_unit(const unsigned long long* units, int n_views, int u)
 {
+    const int lane = threadIdx.x & 31;
     int v = 0;
-    while (units[kUnitFirst + v + 1] <= (unsigned long long)u) v++;
+    for (int k0 = 0; k0 < n_views; k0 += 32) {
+        const int k = k0 + lane;
+        const bool below = k < n_views && units[kUnitFirst + k + 1] <= (unsigned long long)u;
+        v += __popc(__ballot_sync(0xffffffffu, below));
+    }
     return v;
 }
 
@@ -1067,7 +1116,7 @@ k_ord_count(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
     const int rwm = (max_tiles + 1) / 2;
     const int n_units = (int)units[kUnitFirst + L.n_views];
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const int v = view_of_unit(units, u);
+        const int v = view_of_unit(units, L.n_views, u);
         const int nt = L.tiles_x[v] * L.tiles_y[v];
         const int rw = (nt + 1) / 2;
         for (int i = threadIdx.x; i < 8 * rw; i += blockDim.x) s_rel[i] = 0u;
@@ -1104,6 +1153,155 @@ k_ord_count(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
     }
 }
 
+// The same counts from the entries' rectangles instead of their duplicates.
+// A warp's duplicates of one entry are a run of the entry's row-major tile
+// indices, so they cover at most three rectangles of tiles (the rest of a first
+// row, whole rows, the start of a last row) -- one for an entry the warp holds
+// whole.  Each rectangle adds its four corners to a 2-D difference array
+// (per warp, th rows of stride S = tw | 1 words, odd so that the row and column
+// passes below meet no bank conflicts), and two running-sum passes (along the
+// rows, then down the columns) turn it into the per-tile counts.  A word holds
+// the +1 corners in its low half and the -1 corners in its high half: a warp's
+// at most 1025 entries make at most 6150 of either, so the halves never carry
+// and a count is low - high.  About a fifth of the instructions of the walk
+// over the duplicates; the arrays take 32 S th bytes of shared memory, so
+// larger views keep k_ord_count.
+__device__ __forceinline__ void diff_rect(uint32_t* a, int S, int tw, int th, int xa, int xb,
+                                          int ya, int yb)
+{
+    // tiles xa..xb x ya..yb (inclusive); corners past the grid change nothing
+    atomicAdd(a + ya * S + xa, 1u);
+    if (xb + 1 < tw) atomicAdd(a + ya * S + xb + 1, 0x10000u);
+    if (yb + 1 < th) {
+        atomicAdd(a + (yb + 1) * S + xa, 0x10000u);
+        if (xb + 1 < tw) atomicAdd(a + (yb + 1) * S + xb + 1, 1u);
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_ord_count_rect(gevo_layout L, int max_tiles, int cells, const uint32_t* __restrict__ stat,
+                 const unsigned long long* __restrict__ units, const uint4* __restrict__ rec,
+                 const unsigned long long* __restrict__ pre, const uint32_t* __restrict__ wstart,
+                 uint32_t* __restrict__ cnt, uint32_t* __restrict__ wofs)
+{
+    extern __shared__ uint32_t s_d[];   // [8][cells]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rwm = (max_tiles + 1) / 2;
+    const int n_units = (int)units[kUnitFirst + L.n_views];
+    for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+        const int v = view_of_unit(units, L.n_views, u);
+        const int tw = L.tiles_x[v], th = L.tiles_y[v], S = tw | 1;
+        const int nt = tw * th, rw = (nt + 1) / 2;
+        uint32_t* a = s_d + warp * cells;
+        for (int i = lane; i < th * S; i += 32) a[i] = 0u;
+        __syncwarp();
+        const unsigned long long Dv = units[kUnitDv + v];
+        const unsigned long long w0 =
+            (unsigned long long)(u - (int)units[kUnitFirst + v]) * kOrdUnit +
+            (unsigned long long)warp * kOrdWarpDups;
+        if (w0 < Dv) {
+            const unsigned long long w1 = min(Dv, w0 + kOrdWarpDups);
+            const unsigned long long vs = units[kUnitVs + v];
+            const uint4* rv = rec + vs;
+            const unsigned long long* pv = pre + vs + v;
+            const int M = (int)stat[4 * v + 2];
+            // chunks of 4 x 32 entries with every load issued before any use (one
+            // memory latency per chunk; a warp's ~116 entries are mostly one chunk)
+            constexpr int kChunk = 4;
+            for (int p = (int)wstart[(size_t)u * 8 + warp] + lane;; p += 32 * kChunk) {
+                unsigned long long pa[kChunk];
+                uint4 rr[kChunk];
+#pragma unroll
+                for (int i = 0; i < kChunk; i++) {
+                    const int q = p + 32 * i;
+                    pa[i] = q < M ? pv[q] : ~0ull;            // past the view: past the warp
+                    rr[i] = q < M ? rv[q] : make_uint4(0u, 0u, 0u, 0u);
+                }
+#pragma unroll
+                for (int i = 0; i < kChunk; i++) {
+                    if (pa[i] >= w1) continue;        // starts past the warp's duplicates
+                    const uint4 r = rr[i];
+                    const int w = (int)(r.w & 0xffffu), area = w * (int)(r.w >> 16);
+                    const int lo = pa[i] >= w0 ? 0 : (int)(w0 - pa[i]);
+                    const int hi = (int)min((unsigned long long)area, w1 - pa[i]);
+                    if (lo >= hi) continue;           // no tiles, or all before the warp's first
+                    const int x0 = (int)(r.z & 0xffffu), y0 = (int)(r.z >> 16);
+                    if (lo == 0 && hi == area) {      // the whole rectangle
+                        diff_rect(a, S, tw, th, x0, x0 + w - 1, y0, y0 + (int)(r.w >> 16) - 1);
+                        continue;
+                    }
+                    const int r0 = lo / w, c0 = lo - r0 * w, r1 = (hi - 1) / w,
+                              c1 = hi - 1 - r1 * w;
+                    if (r0 == r1) {
+                        diff_rect(a, S, tw, th, x0 + c0, x0 + c1, y0 + r0, y0 + r0);
+                    } else {
+                        diff_rect(a, S, tw, th, x0 + c0, x0 + w - 1, y0 + r0, y0 + r0);
+                        if (r1 > r0 + 1)
+                            diff_rect(a, S, tw, th, x0, x0 + w - 1, y0 + r0 + 1, y0 + r1 - 1);
+                        diff_rect(a, S, tw, th, x0, x0 + c1, y0 + r1, y0 + r1);
+                    }
+                }
+                // entries start in order: go on while the chunk's last one starts inside
+                if (__shfl_sync(0xffffffffu, pa[kChunk - 1], 31) >= w1) break;
+            }
+        }
+        __syncwarp();
+        // running sums along each row, then down each column; four loads ahead of
+        // their stores, so that they overlap
+        for (int y = lane; y < th; y += 32) {
+            uint32_t run = 0u;
+            uint32_t* row = a + y * S;
+            int x = 0;
+            for (; x + 4 <= tw; x += 4) {
+                const uint32_t c0 = row[x], c1 = row[x + 1], c2 = row[x + 2], c3 = row[x + 3];
+                row[x] = run += c0;
+                row[x + 1] = run += c1;
+                row[x + 2] = run += c2;
+                row[x + 3] = run += c3;
+            }
+            for (; x < tw; x++) row[x] = run += row[x];
+        }
+        __syncwarp();
+        for (int x = lane; x < tw; x += 32) {
+            uint32_t run = 0u;
+            uint32_t* col = a + x;
+            int y = 0;
+            for (; y + 4 <= th; y += 4) {
+                const uint32_t c0 = col[y * S], c1 = col[(y + 1) * S], c2 = col[(y + 2) * S],
+                               c3 = col[(y + 3) * S];
+                col[y * S] = run += c0;
+                col[(y + 1) * S] = run += c1;
+                col[(y + 2) * S] = run += c2;
+                col[(y + 3) * S] = run += c3;
+            }
+            for (; y < th; y++) col[y * S] = run += col[y * S];
+        }
+        __syncthreads();
+        uint32_t* wo = wofs + (size_t)u * 8 * rwm;
+        uint32_t* dst = cnt + (size_t)u * max_tiles;
+        for (int q = threadIdx.x; q < rw; q += blockDim.x) {
+            const int t0 = 2 * q, y = t0 / tw, x = t0 - y * tw;
+            const int i0 = y * S + x;
+            const bool two = t0 + 1 < nt;
+            const int i1 = x + 1 < tw ? i0 + 1 : i0 + S - x;   // the next row's first tile
+            uint32_t r0 = 0u, r1 = 0u;
+#pragma unroll
+            for (int w = 0; w < 8; w++) {
+                wo[(size_t)w * rwm + q] = r0 | (r1 << 16);
+                const uint32_t c0 = s_d[w * cells + i0];
+                r0 += (c0 & 0xffffu) - (c0 >> 16);
+                if (two) {
+                    const uint32_t c1 = s_d[w * cells + i1];
+                    r1 += (c1 & 0xffffu) - (c1 >> 16);
+                }
+            }
+            dst[t0] = r0;
+            if (two) dst[t0 + 1] = r1;
+        }
+        __syncthreads();
+    }
+}
+
 // Per tile of a view: its unit counts become their exclusive running sums (in
 // unit order, in place) and the total is the tile's count.  Block (x, v) takes
 // the 32 tiles 32x .. 32x + 31 of view v, one per lane; its eight warps split
@@ -1121,17 +1319,30 @@ k_ord_scan(gevo_layout L, int max_tiles, const unsigned long long* __restrict__ 
     const int u0 = (int)units[kUnitFirst + v], nu = (int)units[kUnitFirst + v + 1] - u0;
     const int a = u0 + (int)((long long)nu * warp / 8), b = u0 + (int)((long long)nu * (warp + 1) / 8);
     uint32_t* c = cnt + t;
+    const size_t mt = (size_t)max_tiles;
     uint32_t sum = 0u;
-    if (t < nt)
-        for (int u = a; u < b; u++) sum += c[(size_t)u * max_tiles];
+    if (t < nt) {
+#pragma unroll 4
+        for (int u = a; u < b; u++) sum += c[(size_t)u * mt];
+    }
     s_sum[warp][lane] = sum;
     __syncthreads();
     uint32_t run = 0u;
     for (int w = 0; w < warp; w++) run += s_sum[w][lane];
     if (t < nt) {
-        for (int u = a; u < b; u++) {
-            const uint32_t x = c[(size_t)u * max_tiles];
-            c[(size_t)u * max_tiles] = run;
+        int u = a;
+        for (; u + 4 <= b; u += 4) {   // four loads ahead of their stores
+            const uint32_t x0 = c[u * mt], x1 = c[(u + 1) * mt], x2 = c[(u + 2) * mt],
+                           x3 = c[(u + 3) * mt];
+            c[u * mt] = run;
+            c[(u + 1) * mt] = run += x0;
+            c[(u + 2) * mt] = run += x1;
+            c[(u + 3) * mt] = run += x2;
+            run += x3;
+        }
+        for (; u < b; u++) {
+            const uint32_t x = c[u * mt];
+            c[u * mt] = run;
             run += x;
         }
         if (warp == 7) tile_count[L.tile_base[v] + t] = run;
@@ -1156,7 +1367,7 @@ k_ord_scatter(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
     const int rwm = (max_tiles + 1) / 2;
     const int n_units = (int)units[kUnitFirst + L.n_views];
     for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-        const int v = view_of_unit(units, u);
+        const int v = view_of_unit(units, L.n_views, u);
         const int nt = L.tiles_x[v] * L.tiles_y[v];
         const int rw = (nt + 1) / 2;   // words per warp row
         uint32_t* s_base = s_dyn;
@@ -1252,6 +1463,24 @@ static void ord_attributes(size_t smem)
     }
 }
 
+// Shared memory of the rectangle count, at most; views needing more count by
+// walking their duplicates (k_ord_count).  112 KB hold the difference arrays of
+// views up to 3584 words a warp (75 x 43 tiles: 1200 x 680 pixels).
+constexpr size_t kOrdRectSmem = 112 * 1024;
+
+static void count_rect_attributes(size_t smem)
+{
+    static size_t done[256] = {0};
+    int dev = 0;
+    if (smem <= 48 * 1024 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (smem > done[dev]) {
+        cudaFuncSetAttribute(k_ord_count_rect, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        done[dev] = smem;
+    }
+}
+
 // gevo_bin_sort on layouts whose views have at most kOrdMaxTiles tiles: the
 // per-view depth sort, then the order-keeping scatter (see above).
 static gevo_status bin_sort_ordered(const gevo_layout& L, int32_t n, const gevo_proj& proj,
@@ -1332,8 +1561,17 @@ static gevo_status bin_sort_ordered(const gevo_layout& L, int32_t n, const gevo_
     ord_attributes(osmem);
     const uint64_t unit_rows = cap / kOrdUnit + (uint64_t)V + 1;
     const int ugrid = (int)std::max<uint64_t>(1, std::min<uint64_t>(unit_rows, (uint64_t)sm_count() * 32));
-    k_ord_count<<<ugrid, 256, sizeof(uint32_t) * 8 * (size_t)((max_tiles + 1) / 2), st>>>(
-        L, max_tiles, stat, units, rec, pre, wstart, cnt, wofs);
+    int cells = 0;   // the rectangle count's difference arrays: th (tw | 1) words a warp
+    for (int v = 0; v < V; v++) cells = std::max(cells, L.tiles_y[v] * (L.tiles_x[v] | 1));
+    const size_t rsmem = sizeof(uint32_t) * 8 * (size_t)cells;
+    if (rsmem <= kOrdRectSmem) {
+        count_rect_attributes(rsmem);
+        k_ord_count_rect<<<ugrid, 256, rsmem, st>>>(L, max_tiles, cells, stat, units, rec, pre,
+                                                     wstart, cnt, wofs);
+    } else {
+        k_ord_count<<<ugrid, 256, sizeof(uint32_t) * 8 * (size_t)((max_tiles + 1) / 2), st>>>(
+            L, max_tiles, stat, units, rec, pre, wstart, cnt, wofs);
+    }
     GEVO_CHECK_LAUNCH();
     k_ord_scan<<<dim3((max_tiles + 31) / 32, V), 256, 0, st>>>(L, max_tiles, units, cnt,
                                                                 tile_count);
