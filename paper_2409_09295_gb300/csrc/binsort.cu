@@ -773,14 +773,27 @@ k_ord_stat(gevo_layout L, int n, const float2* __restrict__ xy, const int* __res
         const int g = blockIdx.x * 1024 + i * 256 + threadIdx.x;
         rr[i] = g < n ? radius[vb + g] : 0;
     }
+    // then the visible entries' depths and means, all four before any use
+    uint32_t dd[4];
+    float2 mm[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int g = blockIdx.x * 1024 + i * 256 + threadIdx.x;
+        dd[i] = 0u;
+        mm[i] = make_float2(0.f, 0.f);
+        if (rr[i] > 0) {
+            dd[i] = __float_as_uint(__ldg(reinterpret_cast<const float*>(rgbz + vb + g) + 3));
+            mm[i] = xy[vb + g];
+        }
+    }
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int g = blockIdx.x * 1024 + i * 256 + threadIdx.x;
         if (g >= n) break;
         const int r = rr[i];
         if (r <= 0) { dk[vb + g] = kInvisible; continue; }
-        const uint32_t d = __float_as_uint(__ldg(reinterpret_cast<const float*>(rgbz + vb + g) + 3));
-        const float2 m = xy[vb + g];
+        const uint32_t d = dd[i];
+        const float2 m = mm[i];
         int x0, y0, x1, y1;
         tile_rect(m.x, m.y, r, tx, ty, x0, y0, x1, y1);
         dk[vb + g] = d;
@@ -884,10 +897,15 @@ k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ s
 }
 
 // First sorted position of view v (the visible entries of earlier views).
+// Called by whole warps: the lanes load the earlier views' counts at once.
 __device__ __forceinline__ uint32_t view_start(const uint32_t* stat, int v)
 {
+    const int lane = threadIdx.x & 31;
     uint32_t s = 0u;
-    for (int u = 0; u < v; u++) s += stat[4 * u + 2];
+    for (int u0 = 0; u0 < v; u0 += 32) {
+        const int u = u0 + lane;
+        s += __reduce_add_sync(0xffffffffu, u < v ? stat[4 * u + 2] : 0u);
+    }
     return s;
 }
 
@@ -1050,6 +1068,7 @@ k_ord_pre(const uint32_t* __restrict__ stat, const unsigned long long* __restric
     uint32_t* ws = wstart + units[kUnitFirst + v] * 8ull;
     const uint32_t* wh = reinterpret_cast<const uint32_t*>(rec + vs) + 3;   // .w of each record
     const int q0 = p0 + threadIdx.x * PER;
+    const unsigned long long base = bsum[(size_t)v * gridDim.x + blockIdx.x];   // before the barriers
     uint32_t area[PER];
     unsigned long long sum = 0ull;
 #pragma unroll
@@ -1064,8 +1083,7 @@ k_ord_pre(const uint32_t* __restrict__ stat, const unsigned long long* __restric
         sum += a;
     }
     unsigned long long tot;
-    unsigned long long run =
-        bsum[(size_t)v * gridDim.x + blockIdx.x] + block_excl_scan<256>(sum, tot);
+    unsigned long long run = base + block_excl_scan<256>(sum, tot);
     unsigned long long* pv = pre + vs + v;
 #pragma unroll
     for (int i = 0; i < PER; i++) {
