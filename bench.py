@@ -404,9 +404,9 @@ def main():
     roof = dict(roofs[dom])
     # DRAM bytes of one reverse-walk launch: ncu (dram__bytes_read.sum + write) of the
     # current kernel (32 threads per tile) on the 4-view case
-    # (`bench.py --case render --threads-bwd 32`), 51.36 MB for 245.15M walked
+    # (`bench.py --case render --threads-bwd 32`), 51.42 MB for 245.15M walked
     # entries, scaled by entries to this launch (same scene, same resolution)
-    roof.update({"traffic": 51.36e6 * E_bwd / 245.15e6,
+    roof.update({"traffic": 51.42e6 * E_bwd / 245.15e6,
                  "traffic_source": "ncu dram bytes of the 4-view case, scaled by walked entries",
                  "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {clk_peak:.0f} MHz"})
 
