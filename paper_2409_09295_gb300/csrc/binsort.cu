@@ -1179,11 +1179,14 @@ k_ord_count(gevo_layout L, int max_tiles, const uint32_t* __restrict__ stat,
 // (per warp, th rows of stride S = tw | 1 words, odd so that the row and column
 // passes below meet no bank conflicts), and two running-sum passes (along the
 // rows, then down the columns) turn it into the per-tile counts.  A word holds
-// the +1 corners in its low half and the -1 corners in its high half: a warp's
-// at most 1025 entries make at most 6150 of either, so the halves never carry
-// and a count is low - high.  About a fifth of the instructions of the walk
-// over the duplicates; the arrays take 32 S th bytes of shared memory, so
-// larger views keep k_ord_count.
+// the +1 corners in its low half and the -1 corners in its high half: each of a
+// warp's at most 1024 entries (every one holds at least one of its 1024
+// duplicates) adds at most three rectangles of two corners of either sign, so
+// no running sum of a half passes 6144, the halves never carry, and a count is
+// low - high.  It executes about 60% of the instructions of the walk over the
+// duplicates (9.5M against 15.8M on four 640 x 480 views of 500k Gaussians);
+// the arrays take 32 S th bytes of shared memory, so larger views keep
+// k_ord_count.
 __device__ __forceinline__ void diff_rect(uint32_t* a, int S, int tw, int th, int xa, int xb,
                                           int ya, int yb)
 {
