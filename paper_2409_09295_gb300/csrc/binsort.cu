@@ -877,22 +877,22 @@ k_ord_seg(int n, const uint32_t* __restrict__ dk, const uint32_t* __restrict__ s
                       : 0;
     }
     __syncthreads();
-    if (!SCATTER) {
+    if constexpr (!SCATTER) {
         for (int i = threadIdx.x; i < kDepthBins; i += blockDim.x)
             if (s_h[i]) atomicAdd(seg_count + v * kDepthBins + i, s_h[i]);
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int i = threadIdx.x; i < kDepthBins; i += 256)   // the block's reservations together
-        if (s_h[i]) s_h[i] = seg_start[v * kDepthBins + i] +
-                             atomicAdd(seg_cursor + v * kDepthBins + i, s_h[i]);
-    __syncthreads();
+        for (int i = threadIdx.x; i < kDepthBins; i += 256)   // the block's reservations together
+            if (s_h[i]) s_h[i] = seg_start[v * kDepthBins + i] +
+                                 atomicAdd(seg_cursor + v * kDepthBins + i, s_h[i]);
+        __syncthreads();
 #pragma unroll
-    for (int i = 0; i < PER; i++) {
-        if (d[i] == kInvisible) continue;
-        const int g = blockIdx.x * kOrdSegChunk + i * 256 + threadIdx.x;
-        const int sg = depth_segment(lo, mul, d[i]);
-        b1[s_h[sg] + rank[i]] = ((unsigned long long)d[i] << 32) | (uint32_t)g;
+        for (int i = 0; i < PER; i++) {
+            if (d[i] == kInvisible) continue;
+            const int g = blockIdx.x * kOrdSegChunk + i * 256 + threadIdx.x;
+            const int sg = depth_segment(lo, mul, d[i]);
+            b1[s_h[sg] + rank[i]] = ((unsigned long long)d[i] << 32) | (uint32_t)g;
+        }
     }
 }
 
