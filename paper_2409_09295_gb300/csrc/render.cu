@@ -750,81 +750,81 @@ k_render_bwd(gevo_layout L, int n, const float2* __restrict__ xy, const float4* 
                 // alpha needs no minimum and dL/dalpha no clamp select; without
                 // dL/dT_final an unused pixel's alpha = 0 already zeroes its term
                 auto pixels = [&](auto nc_tag) {
-                constexpr bool NC = decltype(nc_tag)::value;
+                    constexpr bool NC = decltype(nc_tag)::value;
 #pragma unroll
-                for (int h = 0; h < NV; h++) {
-                    const V dy = vsub(e.my, pyv[h]);
-                    const V p2 = vfma(vfma(e.cz, dy, e.cy), dy, e.cx);
-                    const V dwin = vadd(p2, e.mw);
-                    float g[W2], al[W2];
-                    bool kk[W2];
+                    for (int h = 0; h < NV; h++) {
+                        const V dy = vsub(e.my, pyv[h]);
+                        const V p2 = vfma(vfma(e.cz, dy, e.cy), dy, e.cx);
+                        const V dwin = vadd(p2, e.mw);
+                        float g[W2], al[W2];
+                        bool kk[W2];
 #pragma unroll
-                    for (int i = 0; i < W2; i++) g[i] = ex2_approx(vlane(p2, i));
-                    const V G = vpack<V>(g);
-                    const V og = vmul(e.cw, G);
+                        for (int i = 0; i < W2; i++) g[i] = ex2_approx(vlane(p2, i));
+                        const V G = vpack<V>(g);
+                        const V og = vmul(e.cw, G);
 #pragma unroll
-                    for (int i = 0; i < W2; i++) {
-                        const int k = h * W2 + i;
-                        const float ogi = vlane(og, i);
-                        const bool use = pos < last[k] && window_ok(vlane(dwin, i), e.m);
-                        if (NC) {
-                            kk[i] = use;
-                            al[i] = use ? ogi : 0.f;
-                        } else {
-                            kk[i] = use && ogi <= kAlphaMax;      // alpha not clamped
-                            al[i] = use ? fminf(kAlphaMax, ogi) : 0.f;
+                        for (int i = 0; i < W2; i++) {
+                            const int k = h * W2 + i;
+                            const float ogi = vlane(og, i);
+                            const bool use = pos < last[k] && window_ok(vlane(dwin, i), e.m);
+                            if (NC) {
+                                kk[i] = use;
+                                al[i] = use ? ogi : 0.f;
+                            } else {
+                                kk[i] = use && ogi <= kAlphaMax;      // alpha not clamped
+                                al[i] = use ? fminf(kAlphaMax, ogi) : 0.f;
+                            }
                         }
-                    }
-                    const V alpha = vpack<V>(al);                    // 0 where unused
-                    const V om = vsub(one, alpha);
-                    float ri[W2];
+                        const V alpha = vpack<V>(al);                    // 0 where unused
+                        const V om = vsub(one, alpha);
+                        float ri[W2];
 #pragma unroll
-                    for (int i = 0; i < W2; i++) ri[i] = rcp_approx(vlane(om, i));
-                    const V inv = vpack<V>(ri);
-                    const V Ti = vmul(T[h], inv);
-                    T[h] = Ti;
-                    const V w = vmul(alpha, Ti);
-                    // (c - S) . dL/dC, shared by dL/dalpha = T_i gd and the suffix update
-                    V qc = vmul(gC0[h], e.rx);
-                    qc = vfma(gC1[h], e.ry, qc);
-                    qc = vfma(gC2[h], e.rb, qc);
-                    if (DD) qc = vfma(gD[h], e.rw, qc);
-                    const V gd = vsub(qc, Pg[h]);
-                    Pg[h] = vfma(alpha, gd, Pg[h]);
-                    if (EXT && !act) {
-                        if (pix_err) se = vfma(w, pe[h], se);
-                        continue;
-                    }
-                    if (EXT) se = vfma(w, pe[h], se);
-                    sr = vfma(gC0[h], w, sr);
-                    sg = vfma(gC1[h], w, sg);
-                    sb = vfma(gC2[h], w, sb);
-                    if (DD) sz = vfma(gD[h], w, sz);
-                    V dp;
-                    float dd[W2];
-                    if (DT) {
-                        // dL/dalpha = gd T_i - dL/dT_final T_final / (1 - alpha)
-                        const V dLda = vsub(vmul(gd, Ti), vmul(gTT[h], inv));
-#pragma unroll
-                        for (int i = 0; i < W2; i++) dd[i] = kk[i] ? vlane(dLda, i) : 0.f;
-                        const V kd = vpack<V>(dd);
-                        so = vfma(kd, G, so);
-                        dp = vmul(kd, alpha);
-                    } else {
-                        const V gw = vmul(gd, w);
-                        if (NC) {
-                            dp = gw;
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < W2; i++) dd[i] = kk[i] ? vlane(gw, i) : 0.f;
-                            dp = vpack<V>(dd);
+                        for (int i = 0; i < W2; i++) ri[i] = rcp_approx(vlane(om, i));
+                        const V inv = vpack<V>(ri);
+                        const V Ti = vmul(T[h], inv);
+                        T[h] = Ti;
+                        const V w = vmul(alpha, Ti);
+                        // (c - S) . dL/dC, shared by dL/dalpha = T_i gd and the suffix update
+                        V qc = vmul(gC0[h], e.rx);
+                        qc = vfma(gC1[h], e.ry, qc);
+                        qc = vfma(gC2[h], e.rb, qc);
+                        if (DD) qc = vfma(gD[h], e.rw, qc);
+                        const V gd = vsub(qc, Pg[h]);
+                        Pg[h] = vfma(alpha, gd, Pg[h]);
+                        if (EXT && !act) {
+                            if (pix_err) se = vfma(w, pe[h], se);
+                            continue;
                         }
+                        if (EXT) se = vfma(w, pe[h], se);
+                        sr = vfma(gC0[h], w, sr);
+                        sg = vfma(gC1[h], w, sg);
+                        sb = vfma(gC2[h], w, sb);
+                        if (DD) sz = vfma(gD[h], w, sz);
+                        V dp;
+                        float dd[W2];
+                        if (DT) {
+                            // dL/dalpha = gd T_i - dL/dT_final T_final / (1 - alpha)
+                            const V dLda = vsub(vmul(gd, Ti), vmul(gTT[h], inv));
+#pragma unroll
+                            for (int i = 0; i < W2; i++) dd[i] = kk[i] ? vlane(dLda, i) : 0.f;
+                            const V kd = vpack<V>(dd);
+                            so = vfma(kd, G, so);
+                            dp = vmul(kd, alpha);
+                        } else {
+                            const V gw = vmul(gd, w);
+                            if (NC) {
+                                dp = gw;
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < W2; i++) dd[i] = kk[i] ? vlane(gw, i) : 0.f;
+                                dp = vpack<V>(dd);
+                            }
+                        }
+                        const V t = vmul(dp, dy);
+                        s0 = vadd(s0, dp);
+                        s1 = vadd(s1, t);
+                        s2 = vfma(t, dy, s2);
                     }
-                    const V t = vmul(dp, dy);
-                    s0 = vadd(s0, dp);
-                    s1 = vadd(s1, t);
-                    s2 = vfma(t, dy, s2);
-                }
                 };
                 if (!DT && e.o <= kNoClampO) pixels(std::true_type{});
                 else pixels(std::false_type{});
